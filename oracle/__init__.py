@@ -1,0 +1,233 @@
+"""CPU oracle for the state-vector gate-application path (complex128).
+
+TEST INFRASTRUCTURE ONLY.  Imported by the tests, by the smoke check and by
+the benchmark's CPU-baseline leg; never by the library.  The arithmetic lives
+in sv_oracle.c (plain C, fp64, Eq. 1 of Sec. 2 written out as an index loop);
+this module compiles it with gcc and marshals the seeded records from
+`workloads` into the oracle's own flat arrays.
+
+Gradients: `grad_param_shift` is the parameter-shift rule
+dE/dtheta = (E(theta + pi/2) - E(theta - pi/2)) / 2 per gate occurrence,
+which is exact for gates exp(-i theta P / 2) with P a Pauli matrix (RX, RY,
+RZ); the paper's automatic gradients (Sec. 2, the tensorflow backend) give
+the same derivative.  `grad_fd` is a plain central difference.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+from workloads import KINDS, Circuit, Gate, PauliTerm
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sv_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+_KIND_CODE = {k: i for i, k in enumerate(KINDS)}   # same order as the C enum
+
+
+def build(force: bool = False) -> str:
+    """Compile sv_oracle.c to liboracle.so (gcc, -O2, OpenMP if available)."""
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    base = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", _SRC, "-o", _LIB_PATH + ".tmp", "-lm"]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True,
+                       capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True)
+    os.replace(_LIB_PATH + ".tmp", _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB_PATH)
+        P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        L.orc_apply.argtypes = [I, P, I, P, I, P, P]
+        L.orc_run.argtypes = [I, P, I, P, P, P, P, P, P, P, P, P, P, I, D]
+        L.orc_expval.argtypes = [I, P, I, P, P, P, P, P, P, P]
+        L.orc_norm2.argtypes = [I, P]
+        L.orc_norm2.restype = D
+        L.orc_dot.argtypes = [I, P, P, P, P]
+        L.orc_init_basis.argtypes = [I, P, ctypes.c_uint64]
+        L.orc_set_threads.argtypes = [I]
+        L.orc_set_mutant.argtypes = [I]
+        L.orc_get_threads.restype = I
+        L.orc_have_openmp.restype = I
+        _lib = L
+    return _lib
+
+
+def set_threads(t: int) -> None:
+    lib().orc_set_threads(int(t))
+
+
+def get_threads() -> int:
+    return lib().orc_get_threads()
+
+
+def have_openmp() -> bool:
+    return bool(lib().orc_have_openmp())
+
+
+def set_mutant(m: int) -> None:
+    """Plant mistake m in the oracle (0 = none).  Pin-sensitivity tests only."""
+    lib().orc_set_mutant(int(m))
+
+
+def _ptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+class _Packed:
+    def __init__(self, c: Circuit):
+        ng = len(c.gates)
+        self.ng = ng
+        self.kind = np.zeros(ng, np.int32)
+        self.ntar = np.zeros(ng, np.int32)
+        self.tar = np.zeros(5 * max(ng, 1), np.int32)
+        self.nctl = np.zeros(ng, np.int32)
+        self.ctl = np.zeros(8 * max(ng, 1), np.int32)
+        self.param = np.full(ng, -1, np.int32)
+        self.angle = np.zeros(ng, np.float64)
+        self.mat_off = np.zeros(ng, np.int64)
+        pool: List[np.ndarray] = []
+        off = 0
+        for g, gate in enumerate(c.gates):
+            self.kind[g] = _KIND_CODE[gate.kind]
+            self.ntar[g] = len(gate.targets)
+            self.tar[5 * g:5 * g + len(gate.targets)] = gate.targets
+            self.nctl[g] = len(gate.controls)
+            self.ctl[8 * g:8 * g + len(gate.controls)] = gate.controls
+            self.param[g] = gate.param
+            self.angle[g] = gate.angle
+            if gate.kind == "MATRIX":
+                m = np.ascontiguousarray(gate.matrix, dtype=np.complex128).ravel()
+                self.mat_off[g] = off
+                pool.append(m)
+                off += m.size
+        self.pool = np.concatenate(pool) if pool else np.zeros(1, np.complex128)
+
+
+def basis_state(n: int, x: int = 0) -> np.ndarray:
+    psi = np.zeros(1 << n, np.complex128)
+    lib().orc_init_basis(n, _ptr(psi), ctypes.c_uint64(x))
+    return psi
+
+
+def run(c: Circuit, theta: Optional[Sequence[float]] = None,
+        psi0: Optional[np.ndarray] = None, basis: int = 0,
+        shift_gate: int = -1, shift: float = 0.0) -> np.ndarray:
+    """psi = U_N ... U_1 psi0 (psi0 = |basis> if not given)."""
+    n = c.n_qubits
+    psi = (np.array(psi0, dtype=np.complex128, copy=True) if psi0 is not None
+           else basis_state(n, basis))
+    th = np.ascontiguousarray(theta if theta is not None and len(theta) else [0.0],
+                              dtype=np.float64)
+    p = _Packed(c)
+    rc = lib().orc_run(n, _ptr(psi), p.ng, _ptr(p.kind), _ptr(p.ntar), _ptr(p.tar),
+                       _ptr(p.nctl), _ptr(p.ctl), _ptr(p.param), _ptr(p.angle),
+                       _ptr(p.mat_off), _ptr(p.pool), _ptr(th), int(shift_gate),
+                       float(shift))
+    if rc:
+        raise ValueError(f"oracle rejected the circuit (code {rc})")
+    return psi
+
+
+def apply_gate(psi: np.ndarray, n: int, targets: Sequence[int],
+               controls: Sequence[int], G: np.ndarray) -> np.ndarray:
+    """One Eq. (1) application of a dense matrix G (in place on a copy)."""
+    out = np.array(psi, dtype=np.complex128, copy=True)
+    t = np.ascontiguousarray(targets, np.int32)
+    cc = np.ascontiguousarray(controls if len(controls) else [0], np.int32)
+    g = np.ascontiguousarray(G, np.complex128)
+    rc = lib().orc_apply(n, _ptr(out), len(targets), _ptr(t), len(controls),
+                         _ptr(cc), _ptr(g))
+    if rc:
+        raise ValueError("oracle rejected the gate")
+    return out
+
+
+def norm2(psi: np.ndarray) -> float:
+    n = int(psi.size).bit_length() - 1
+    a = np.ascontiguousarray(psi, np.complex128)
+    return lib().orc_norm2(n, _ptr(a))
+
+
+def dot(a: np.ndarray, b: np.ndarray) -> complex:
+    n = int(a.size).bit_length() - 1
+    a = np.ascontiguousarray(a, np.complex128)
+    b = np.ascontiguousarray(b, np.complex128)
+    re, im = ctypes.c_double(), ctypes.c_double()
+    lib().orc_dot(n, _ptr(a), _ptr(b), ctypes.byref(re), ctypes.byref(im))
+    return complex(re.value, im.value)
+
+
+def expval(psi: np.ndarray, terms: Sequence[PauliTerm], n: Optional[int] = None,
+           per_term: bool = False):
+    """<psi|H|psi> for H = sum_k c_k P_k (P_k a Pauli string)."""
+    if n is None:
+        n = int(psi.size).bit_length() - 1
+    a = np.ascontiguousarray(psi, np.complex128)
+    nt = len(terms)
+    coeff = np.array([t[0] for t in terms] or [0.0], np.float64)
+    nops = np.array([len(t[1]) for t in terms] or [0], np.int32)
+    qubits = np.zeros(max(nt, 1) * n, np.int32)
+    letters = np.zeros(max(nt, 1) * n, np.uint8)
+    for k, (_, ops) in enumerate(terms):
+        for j, (q, L) in enumerate(ops):
+            qubits[k * n + j] = q
+            letters[k * n + j] = ord(L)
+    e = ctypes.c_double()
+    tre = np.zeros(max(nt, 1))
+    tim = np.zeros(max(nt, 1))
+    rc = lib().orc_expval(n, _ptr(a), nt, _ptr(coeff), _ptr(nops), _ptr(qubits),
+                          _ptr(letters), ctypes.byref(e), _ptr(tre), _ptr(tim))
+    if rc:
+        raise ValueError(f"oracle expval failed (code {rc})")
+    if per_term:
+        return e.value, tre[:nt] + 1j * tim[:nt]
+    return e.value
+
+
+def energy(c: Circuit, theta, terms, psi0=None, shift_gate=-1, shift=0.0) -> float:
+    return expval(run(c, theta, psi0, shift_gate=shift_gate, shift=shift), terms, c.n_qubits)
+
+
+def grad_param_shift(c: Circuit, theta, terms, params: Optional[Sequence[int]] = None,
+                     psi0=None) -> np.ndarray:
+    """Exact gradient by the parameter-shift rule, summed over every gate that
+    uses a parameter.  If `params` is given, only those entries are filled."""
+    want = set(range(c.n_params)) if params is None else set(int(p) for p in params)
+    g = np.zeros(c.n_params)
+    for idx, gate in enumerate(c.gates):
+        if gate.param >= 0 and gate.param in want:
+            if gate.kind not in ("RX", "RY", "RZ"):
+                raise ValueError("parameter shift needs exp(-i a P / 2) gates")
+            ep = energy(c, theta, terms, psi0, idx, math.pi / 2)
+            em = energy(c, theta, terms, psi0, idx, -math.pi / 2)
+            g[gate.param] += 0.5 * (ep - em)
+    return g
+
+
+def grad_fd(c: Circuit, theta, terms, h: float = 1e-3,
+            params: Optional[Sequence[int]] = None, psi0=None) -> np.ndarray:
+    """Central finite differences (E(theta + h e_j) - E(theta - h e_j)) / 2h."""
+    theta = np.asarray(theta, np.float64)
+    idx = range(c.n_params) if params is None else params
+    g = np.zeros(c.n_params)
+    for j in idx:
+        tp = theta.copy(); tp[j] += h
+        tm = theta.copy(); tm[j] -= h
+        g[j] = (energy(c, tp, terms, psi0) - energy(c, tm, terms, psi0)) / (2 * h)
+    return g
