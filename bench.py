@@ -1,0 +1,355 @@
+#!/usr/bin/env python
+"""Benchmark of the state-vector gate-application path on GB300.
+
+Workload (one step): the QFT circuit on n = 30 qubits in complex64
+(8 GiB state, larger than L2), 480 gates (30 H, 435 controlled-U1,
+15 SWAP), one kernel per gate, from a seeded basis state (sv_init + the
+circuit).  value = gate applications per second over all ranks.
+
+Also reported: the dominant kernel's achieved HBM bandwidth against the
+measured copy bandwidth (per-launch CUDA events recorded live by the
+library's profiler during the timed steps), an end-to-end figure through
+the C ABI with the state uploaded from and downloaded to pinned host
+memory every step, the adjoint gradient / forward time ratio on the
+hardware-efficient ansatz (n = 20, 10 layers, TFIM, complex64), SM clocks
+sampled during the timed region, and the CPU oracle's throughput on a
+bounded sample of the same workload.
+
+--impl reference times the CPU oracle alone (the comparison arm).
+Multi-GPU: independent replicas (the path does not shard here), one per
+rank, weak scaling; no collective on the data path.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "QFT n=30 c64 gate-apps/s & % HBM roofline; adjoint grad/forward time ratio"
+UNIT = "gate-apps/s"
+N_QFT = 30
+SEED_QFT = 1001
+
+
+def hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def algorithmic_bytes(kernel: str, n: int, amp_bytes: int) -> float:
+    """B_alg per launch for the QFT's kernels: 2 * bytes * |A|, A the
+    amplitudes the gate changes (H: 2^n, controlled-U1: 2^(n-2),
+    SWAP: 2^(n-1))."""
+    if kernel.startswith("kphase"):
+        return 2.0 * amp_bytes * 2 ** (n - 2)
+    if kernel.startswith("kswap"):
+        return 2.0 * amp_bytes * 2 ** (n - 1)
+    return 2.0 * amp_bytes * 2 ** n
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.proc = None
+        self.file = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+        try:
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                   "-lms", "200"]
+            if gpu_id:
+                cmd += ["-i", gpu_id]
+            self.proc = subprocess.Popen(cmd, stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.file.read().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.file.name)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def cpu_oracle_sample(n: int, n_gates: int, threads: int):
+    """Time the CPU oracle (as it stands) on the first `n_gates` gates of the
+    QFT at n qubits (complex128 host state).  Returns (gate-apps/s, secs,
+    description)."""
+    import oracle
+    import workloads as W
+    oracle.set_threads(threads)
+    c = W.qft(n)
+    sample = W.Circuit(n, c.gates[:n_gates], 0)
+    x = W.random_basis_index(n, SEED_QFT)
+    t0 = time.perf_counter()
+    oracle.run(sample, None, basis=x)
+    dt = time.perf_counter() - t0
+    desc = (f"first {n_gates} gates of the n={n} QFT (H + controlled-U1) on a complex128 "
+            f"2^{n} host state, {threads} OpenMP threads")
+    return n_gates / dt, dt, desc
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    threads = os.cpu_count() or 1
+    per_step = 3
+    vals = []
+    for i in range(args.warmup + args.steps):
+        v, dt, desc = cpu_oracle_sample(args.n, per_step, threads)
+        if i >= args.warmup:
+            vals.append(dt)
+    total = sum(vals)
+    value = per_step * args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"qft n={args.n}, one gate at a time, seeded basis input",
+                   "sample": desc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def adjoint_ratio(torch, reps=3):
+    """Hardware-efficient ansatz n = 20, L = 10, TFIM, complex64: forward
+    (init + circuit + energy) vs adjoint gradient (H psi + reverse sweep)."""
+    import workloads as W
+    from paper_2202_07017_gb300 import C64, pack_circuit, pack_pauli, sv_adjoint, sv_alloc
+    from paper_2202_07017_gb300 import sv_apply_circuit, sv_expval, sv_free, sv_init
+    n, L = 20, 10
+    c, theta = W.hea(n, L, 1002)
+    pc, pp = pack_circuit(c), pack_pauli(W.tfim(n), n)
+    h = sv_alloc(n, C64, torch.cuda.current_stream().cuda_stream)
+    try:
+        fw, gr = [], []
+        for i in range(reps + 1):
+            t0 = time.perf_counter()
+            sv_init(h, 0)
+            sv_apply_circuit(h, pc, theta, 0)
+            e = sv_expval(h, pp)
+            t1 = time.perf_counter()
+            e2, g = sv_adjoint(h, pc, theta, pp)
+            t2 = time.perf_counter()
+            if i:
+                fw.append(t1 - t0)
+                gr.append(t2 - t1)
+    finally:
+        sv_free(h)
+    f, gm = float(np.median(fw)), float(np.median(gr))
+    return {"workload": "hardware-efficient ansatz n=20 L=10 (200 params), TFIM, complex64",
+            "forward_ms": 1e3 * f, "grad_ms": 1e3 * gm, "grad_over_forward": gm / f,
+            "energy": e}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_QFT)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+    import workloads as W
+    from paper_2202_07017_gb300 import (C64, pack_circuit, sv_alloc, sv_apply_circuit,
+                                        sv_download, sv_free, sv_init, sv_launch_count,
+                                        sv_profile_start, sv_profile_stop, sv_upload)
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.current_stream()
+    n = args.n
+    circ = W.qft(n)
+    pc = pack_circuit(circ)
+    n_gates = len(circ.gates)
+    x = W.random_basis_index(n, SEED_QFT)
+    h = sv_alloc(n, C64, stream.cuda_stream)
+
+    def step():
+        sv_init(h, x)
+        sv_apply_circuit(h, pc, None, 0)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        gpu_id = str(local)
+    clocks = Clocks(gpu_id)
+    l0 = sv_launch_count()
+    sv_profile_start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prof = sv_profile_stop()
+    launches = sv_launch_count() - l0
+    clk = clocks.stop()
+    secs = e0.elapsed_time(e1) / 1e3
+    if world > 1:
+        t = torch.tensor([secs], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+        secs = float(t.item())
+    value = world * n_gates * args.steps / secs
+
+    # roofline of the dominant kernel, from the live per-launch events
+    peak, peak_kind = hbm_peak()
+    kernels = {}
+    for name, (cnt, ms) in prof.items():
+        b = algorithmic_bytes(name, n, 8)
+        kernels[name] = {"launches": cnt, "total_ms": ms, "avg_ms": ms / cnt,
+                         "alg_bytes_per_launch": b, "achieved_gbs": b * cnt / (ms / 1e3) / 1e9,
+                         "share": 0.0}
+    tot = sum(k["total_ms"] for k in kernels.values()) or 1.0
+    for k in kernels.values():
+        k["share"] = k["total_ms"] / tot
+    dom = max(kernels, key=lambda k: kernels[k]["total_ms"])
+    dk = kernels[dom]
+    step_bytes = sum(k["alg_bytes_per_launch"] * k["launches"] for k in kernels.values())
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            tr = json.load(f).get(dom)
+        src = os.path.join(ROOT, "paper_2202_07017_gb300", "csrc", "gate_kernels.cu")
+        import hashlib
+        if tr and tr.get("source_sha1") == hashlib.sha1(open(src, "rb").read()).hexdigest():
+            traffic = tr["dram_bytes_per_launch"]
+    except Exception:
+        traffic = None
+    roofline = {"bound": "hbm", "achieved": dk["achieved_gbs"], "peak": peak, "unit": "GB/s",
+                "frac": dk["achieved_gbs"] / peak, "traffic": traffic, "kernel": dom,
+                "peak_source": f"{peak_kind} copy bandwidth",
+                "frac_of_8000": dk["achieved_gbs"] / 8000.0}
+
+    out = None
+    if rank == 0:
+        e2e = None
+        if not args.no_e2e:
+            host = torch.empty(1 << n, dtype=torch.complex64, pin_memory=True)
+            host.zero_()
+            host[x] = 1.0
+            hv = host.numpy()
+            for i in range(1 + 2):
+                t0 = time.perf_counter()
+                sv_upload(h, hv)
+                sv_apply_circuit(h, pc, None, 0)
+                sv_download(h, hv)
+                t1 = time.perf_counter()
+                if i == 0:
+                    ts = []
+                else:
+                    ts.append(t1 - t0)
+            e2e = {"value": n_gates / float(np.median(ts)), "unit": UNIT,
+                   "h2d_bytes_per_step": 8 << n, "d2h_bytes_per_step": 8 << n,
+                   "ms_per_step": 1e3 * float(np.median(ts)),
+                   "path": "sv_upload (pinned host) + sv_apply_circuit + sv_download"}
+            del host, hv
+        adj = adjoint_ratio(torch)
+        cpu = None
+        if not args.no_cpu:
+            threads = os.cpu_count() or 1
+            try:
+                v, dt, desc = cpu_oracle_sample(n, 8, threads)
+                cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                       "sample": desc, "seconds": dt}
+            except MemoryError:
+                v, dt, desc = cpu_oracle_sample(28, 8, threads)
+                cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                       "sample": desc + " (n=30 did not fit host memory)", "seconds": dt}
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"qft n={n} complex64, unfused (one kernel per gate), "
+                                   f"seeded basis input, {n_gates} gates",
+                       "n_qubits": n, "gates": n_gates, "state_bytes": 8 << n,
+                       "l2": "inputs larger than L2 (8 GiB state)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline,
+            "step_hbm": {"alg_bytes_per_step": step_bytes / args.steps,
+                         "achieved_gbs": step_bytes / secs / 1e9,
+                         "frac": step_bytes / secs / 1e9 / peak},
+            "kernels": kernels,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk,
+            "adjoint": adj,
+        }
+    sv_free(h)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,242 @@
+/*
+ * sv.h - C ABI of the GB300 state-vector library (libsv.so).
+ *
+ * The library implements the Schroedinger approach to circuit simulation
+ * described in Sec. 2 of "An open-source modular framework for quantum
+ * computing" (Qibo 0.1.7): a state of n qubits is 2^n complex amplitudes,
+ * a gate on n_tar targets is a 2^n_tar x 2^n_tar complex matrix G, and a
+ * gate is applied by Eq. (1),
+ *     psi'(tau, q) = sum_tau' G(tau, tau') psi(tau', q),
+ * in place, for every gate of a circuit in order.  Everything runs in
+ * hand-written CUDA kernels for sm_103a on the state's stream.
+ *
+ * Conventions (the paper leaves them open; one reading, used everywhere):
+ *   - qubit q is bit p = n-1-q of the amplitude index (qubit 0 = MSB);
+ *   - for targets t_0..t_{k-1}, G's row/column index is
+ *     tau = sum_j b(t_j) 2^(k-1-j)  (t_0 is the MSB of tau), G row-major;
+ *   - a controlled gate acts where every control qubit is 1 and leaves the
+ *     rest of the state unchanged (Sec. 2: controlled and multi-target
+ *     gates by modified index generation);
+ *   - state layout: 2^n interleaved (re, im) pairs, float32 for SV_C64 and
+ *     float64 for SV_C128, contiguous, 256-byte aligned;
+ *   - Pauli masks use amplitude-index bits: bit p of xmask/zmask refers to
+ *     qubit n-1-p.  A term is X where only x is set, Z where only z is set,
+ *     Y where both are set.
+ *
+ * Ownership: a state handle either owns its device buffer (sv_alloc) or
+ * borrows one (sv_wrap); the library also owns small per-handle work buffers
+ * (reduction partials, adjoint work states, checkpoints), freed by sv_free.
+ * Matrices, circuits, parameters and Pauli sums are read from host memory
+ * during the call and not retained.
+ *
+ * Errors: every call validates all arguments before launching anything and
+ * returns SV_ERR_INVALID with the state untouched if any is bad; CUDA
+ * failures return SV_ERR_CUDA; nothing aborts.  sv_last_error() returns a
+ * message for the calling thread's last failure.
+ *
+ * Asynchrony: calls are asynchronous on the handle's stream unless they
+ * return a host value (sv_expval, sv_norm, sv_grad, sv_adjoint with host
+ * outputs, sv_download, sv_sync), which synchronise that stream.
+ */
+#ifndef SV_H
+#define SV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { SV_C64 = 0, SV_C128 = 1 } sv_dtype;
+
+typedef enum {
+  SV_OK = 0,
+  SV_ERR_INVALID = 1,     /* bad argument; nothing was launched */
+  SV_ERR_OOM = 2,         /* device allocation failed */
+  SV_ERR_CUDA = 3,        /* a CUDA call failed; see sv_last_error() */
+  SV_ERR_TIMEOUT = 4,     /* a bounded device wait gave up */
+  SV_ERR_UNSUPPORTED = 5  /* valid request this build does not implement */
+} sv_status;
+
+/* Gate kinds of a circuit record.  Controlled forms are the same kinds with
+ * controls: CZ = Z with one control, CNOT = X with one control,
+ * CU1(l) = U1(l) with one control, Toffoli = X with two controls.
+ * Matrices (c = cos(a/2), s = sin(a/2)):
+ *   H = [[1,1],[1,-1]]/sqrt2, X, Y, Z the Pauli matrices,
+ *   RX(a) = [[c,-is],[-is,c]], RY(a) = [[c,-s],[s,c]],
+ *   RZ(a) = diag(e^{-ia/2}, e^{ia/2}), U1(a) = diag(1, e^{ia}),
+ *   SWAP exchanges |01> and |10> of its two targets,
+ *   MATRIX reads 4^n_tar complex128 entries from the circuit's pool. */
+enum {
+  SV_GATE_H = 0, SV_GATE_X = 1, SV_GATE_Y = 2, SV_GATE_Z = 3,
+  SV_GATE_RX = 4, SV_GATE_RY = 5, SV_GATE_RZ = 6, SV_GATE_U1 = 7,
+  SV_GATE_SWAP = 8, SV_GATE_MATRIX = 9
+};
+
+#define SV_MAX_QUBITS 34
+#define SV_MAX_TARGETS 5
+#define SV_MAX_CONTROLS 16
+#define SV_MAX_PAULI_TERMS 4096
+
+typedef struct sv_state_s* sv_state;   /* opaque handle */
+
+/* One gate of a circuit (Sec. 3: circuits of one-, two- and three-qubit
+ * gates; here any 1..5 targets plus up to 16 controls). */
+typedef struct {
+  int32_t kind;                        /* SV_GATE_* */
+  int32_t n_tar;                       /* 1 (2 for SWAP, 1..5 for MATRIX) */
+  int32_t n_ctrl;                      /* 0..SV_MAX_CONTROLS */
+  int32_t param;                       /* index into theta[], or -1 */
+  int32_t targets[SV_MAX_TARGETS];     /* qubit numbers */
+  int32_t controls[SV_MAX_CONTROLS];   /* qubit numbers */
+  double angle;                        /* angle when param == -1 */
+  int64_t mat_off;                     /* MATRIX: offset (in complex entries) into mat_pool */
+} sv_gate;
+
+typedef struct {
+  int32_t n_qubits;
+  int32_t n_gates;
+  int32_t n_params;                    /* length of theta[] */
+  const sv_gate* gates;                /* host, n_gates records */
+  const double* mat_pool;              /* host complex128 (re, im) pairs, or NULL */
+} sv_circuit;
+
+/* H = sum_k coeff[k] P_k, P_k a Pauli string given by (xmask[k], zmask[k])
+ * (Sec. 3: Hamiltonians such as the transverse-field Ising model). */
+typedef struct {
+  int32_t n_terms;                     /* 0..SV_MAX_PAULI_TERMS */
+  const uint64_t* xmask;               /* host */
+  const uint64_t* zmask;               /* host */
+  const double* coeff;                 /* host, real coefficients */
+} sv_pauli_sum;
+
+/* ---- state handles ---------------------------------------------------- */
+
+/* Allocate a 2^n_qubits state (library-owned, contents undefined) on the
+ * current device, bound to `cuda_stream` (a cudaStream_t, NULL = legacy
+ * default stream).  Sec. 2: the state is 2^n complex numbers.
+ * Errors: SV_ERR_INVALID (n_qubits outside 1..SV_MAX_QUBITS, bad dtype,
+ * out NULL), SV_ERR_OOM. */
+sv_status sv_alloc(int n_qubits, sv_dtype dtype, void* cuda_stream, sv_state* out);
+
+/* Wrap caller-owned device memory `dev_ptr` (2^n_qubits amplitudes of
+ * `dtype`, 16-byte aligned) without copying; the caller keeps ownership and
+ * must keep it alive until sv_free.  Errors as sv_alloc, plus
+ * SV_ERR_INVALID for a NULL or misaligned pointer. */
+sv_status sv_wrap(void* dev_ptr, int n_qubits, sv_dtype dtype, void* cuda_stream,
+                  sv_state* out);
+
+/* Release the handle, its work buffers, and the state buffer if owned. */
+sv_status sv_free(sv_state s);
+
+/* Rebind the handle to another stream (e.g. a stream being captured into a
+ * CUDA graph).  Later calls launch there. */
+sv_status sv_set_stream(sv_state s, void* cuda_stream);
+
+/* Device pointer, qubit count and dtype of the state. */
+sv_status sv_info(sv_state s, void** dev_ptr, int* n_qubits, sv_dtype* dtype);
+
+/* Set the state to the basis state |basis_index> (Sec. 2: amplitudes in the
+ * computational basis).  Asynchronous.  SV_ERR_INVALID if basis_index >= 2^n. */
+sv_status sv_init(sv_state s, uint64_t basis_index);
+
+/* Copy 2^n amplitudes between host memory (pinned or pageable, same dtype
+ * layout) and the state.  sv_upload is asynchronous for pinned memory;
+ * sv_download synchronises the stream. */
+sv_status sv_upload(sv_state s, const void* host);
+sv_status sv_download(sv_state s, void* host);
+
+/* Copy the amplitudes of `src` into `dst` (same n and dtype). Asynchronous. */
+sv_status sv_copy(sv_state dst, sv_state src);
+
+/* ---- gate application (Sec. 2, Eq. 1) ---------------------------------- */
+
+/* Apply G (host complex128, 2^n_tar x 2^n_tar, row-major (re, im) pairs) to
+ * targets[0..n_tar-1] where every qubit in controls[0..n_ctrl-1] is 1,
+ * in place.  1 <= n_tar <= 5, 0 <= n_ctrl <= 16, all qubits distinct and
+ * < n.  G is rounded once to the state's precision.  Asynchronous.
+ * Errors: SV_ERR_INVALID for any bad argument (state untouched). */
+sv_status sv_apply_gate(sv_state s, const int* targets, int n_tar,
+                        const int* controls, int n_ctrl, const double* matrix);
+
+/* Apply every gate of `c` in order (Sec. 2: Eq. 1 per gate; Sec. 1: cost
+ * linear in the gate count).  theta: host, c->n_params angles (may be NULL
+ * when n_params == 0).  Gate matrices are built in fp64 on the host from
+ * the angles.  fuse_k = 0 launches one kernel per gate; fuse_k >= 2 lets
+ * the planner group gates into passes over shared-memory qubit blocks of
+ * which each gate group acts on at most fuse_k qubits (fuse_k <= 5).
+ * Asynchronous.  Errors: SV_ERR_INVALID (validated before any launch). */
+sv_status sv_apply_circuit(sv_state s, const sv_circuit* c, const double* theta,
+                           int fuse_k);
+
+/* ---- reductions (fp64 accumulation, fixed reduction order) ------------ */
+
+/* <psi|psi>.  Synchronises.  Result bit-identical across calls. */
+sv_status sv_norm(sv_state s, double* out);
+
+/* <psi|H|psi> for a Pauli sum (Sec. 3: Hamiltonians, VQE energies).
+ * Products in the state's precision, accumulation in fp64, fixed tree.
+ * sv_expval writes the host double `out` and synchronises; sv_expval_async
+ * writes the device double `dev_out` and does not synchronise (usable
+ * under stream capture).  SV_ERR_INVALID for masks with bits >= n. */
+sv_status sv_expval(sv_state s, const sv_pauli_sum* H, double* out);
+sv_status sv_expval_async(sv_state s, const sv_pauli_sum* H, double* dev_out);
+
+/* out = H psi_in (a full state; Sec. 3 Hamiltonian applied to a state).
+ * in and out must be distinct handles of equal n and dtype. Asynchronous. */
+sv_status sv_apply_pauli_sum(sv_state out, sv_state in, const sv_pauli_sum* H);
+
+/* ---- gradients --------------------------------------------------------- */
+
+/* Adjoint gradient of E(theta) = <psi_N|H|psi_N>, psi_N = U(theta) psi_0
+ * (Sec. 2: automatic gradients of variational circuits, here by the adjoint
+ * method).  On entry `s` holds psi_N as left by sv_apply_circuit(s, c,
+ * theta, *) on psi_0; it is not modified.  The reverse sweep keeps two work
+ * states (lambda = H psi and the un-applied psi) owned by the handle.
+ * Parameterised gates must be RX/RY/RZ; energy (host) and grad (host,
+ * c->n_params doubles, gradients of gates sharing a parameter are summed)
+ * are written and the stream is synchronised.  Gradients accumulate in
+ * fp64. */
+sv_status sv_adjoint(sv_state s, const sv_circuit* c, const double* theta,
+                     const sv_pauli_sum* H, double* energy, double* grad);
+
+/* Forward pass plus adjoint gradient with forward-state checkpoints.  On
+ * entry `s` holds psi_0; on return it holds psi_N.  checkpoint_gates lists
+ * n_checkpoints increasing gate indices g: the forward state before gate g
+ * is stored, and the reverse sweep replaces its un-applied psi by that
+ * stored state when it reaches g (this bounds the rounding drift of
+ * un-applying in complex64).  n_checkpoints = 0 gives the plain sweep.
+ * Outputs as sv_adjoint. */
+sv_status sv_grad(sv_state s, const sv_circuit* c, const double* theta,
+                  const sv_pauli_sum* H, const int32_t* checkpoint_gates,
+                  int n_checkpoints, double* energy, double* grad);
+
+/* ---- status ------------------------------------------------------------ */
+
+/* Synchronise the stream and surface any asynchronous error. */
+sv_status sv_sync(sv_state s);
+
+/* Message describing the calling thread's last failure ("" if none). */
+const char* sv_last_error(void);
+
+/* Tracing: between sv_profile_start() and sv_profile_stop() every kernel
+ * launch of the library is bracketed by two CUDA events on its stream.
+ * sv_profile_stop synchronises on the last event and writes one line per
+ * kernel name, "name launches total_ms\n", into buf (NUL-terminated);
+ * SV_ERR_INVALID if buf is NULL or too small.  Not for use while a stream is
+ * being captured into a CUDA graph. */
+sv_status sv_profile_start(void);
+sv_status sv_profile_stop(char* buf, size_t len);
+
+/* Number of kernels this process has launched through the library. */
+uint64_t sv_launch_count(void);
+
+/* ABI version (major * 100 + minor). */
+int sv_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SV_H */

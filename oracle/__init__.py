@@ -206,17 +206,36 @@ def energy(c: Circuit, theta, terms, psi0=None, shift_gate=-1, shift=0.0) -> flo
 
 def grad_param_shift(c: Circuit, theta, terms, params: Optional[Sequence[int]] = None,
                      psi0=None) -> np.ndarray:
-    """Exact gradient by the parameter-shift rule, summed over every gate that
-    uses a parameter.  If `params` is given, only those entries are filled."""
+    """Exact gradient by shift rules, summed over every gate that uses a
+    parameter.  If `params` is given, only those entries are filled.
+
+    Uncontrolled RX/RY/RZ = exp(-i a P / 2): E(a) = A + B cos a + C sin a,
+    so dE/da = (E(a + pi/2) - E(a - pi/2)) / 2.
+    Controlled rotations = exp(-i a (Pc x P) / 2), Pc the all-ones projector
+    of the controls: the generator's eigenvalues are 0 and +-1/2, so E(a)
+    has frequencies 1/2 and 1.  For a component of frequency w,
+    f(a + s) - f(a - s) = (2 sin(w s) / w) f'(a); requiring
+    d+ (2 sin(w pi/2)/w) - d- (2 sin(w 3pi/2)/w) = 1 for w = 1 and w = 1/2
+    gives d+ + d- = 1/2 and d+ - d- = 1/(2 sqrt 2), i.e. the exact rule
+    dE/da = d+ [E(a+pi/2) - E(a-pi/2)] - d- [E(a+3pi/2) - E(a-3pi/2)],
+    d+- = (sqrt2 +- 1) / (4 sqrt2)."""
     want = set(range(c.n_params)) if params is None else set(int(p) for p in params)
     g = np.zeros(c.n_params)
+    dp = (math.sqrt(2) + 1) / (4 * math.sqrt(2))
+    dm = (math.sqrt(2) - 1) / (4 * math.sqrt(2))
     for idx, gate in enumerate(c.gates):
         if gate.param >= 0 and gate.param in want:
             if gate.kind not in ("RX", "RY", "RZ"):
-                raise ValueError("parameter shift needs exp(-i a P / 2) gates")
-            ep = energy(c, theta, terms, psi0, idx, math.pi / 2)
-            em = energy(c, theta, terms, psi0, idx, -math.pi / 2)
-            g[gate.param] += 0.5 * (ep - em)
+                raise ValueError("shift rules need RX, RY or RZ gates")
+
+            def E(s):
+                return energy(c, theta, terms, psi0, idx, s)
+
+            if not gate.controls:
+                g[gate.param] += 0.5 * (E(math.pi / 2) - E(-math.pi / 2))
+            else:
+                g[gate.param] += (dp * (E(math.pi / 2) - E(-math.pi / 2))
+                                  - dm * (E(1.5 * math.pi) - E(-1.5 * math.pi)))
     return g
 
 

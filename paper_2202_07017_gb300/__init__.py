@@ -1,0 +1,146 @@
+"""GB300 state-vector simulation of circuits (Sec. 2, Eq. 1 of the Qibo 0.1.7
+paper): hand-written CUDA kernels for sm_103a behind the C ABI of
+include/sv.h, with PyTorch providing device memory, streams and autograd.
+
+    from paper_2202_07017_gb300 import State, Energy
+    st = State(20, "c64")                 # torch-owned device buffer
+    st.init(0)
+    st.apply_circuit(circuit, theta)      # one kernel per gate (fuse_k = 0)
+    e = st.expval(hamiltonian)            # fp64-accumulated <psi|H|psi>
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .sv import (C64, C128, EXPORTS, PackedCircuit, PackedPauli, SvError, load, pack_circuit,
+                 pack_pauli, sv_adjoint, sv_alloc, sv_apply_circuit, sv_apply_gate,
+                 sv_apply_pauli_sum, sv_copy, sv_download, sv_expval, sv_expval_async, sv_free,
+                 sv_grad, sv_info, sv_init, sv_last_error, sv_launch_count, sv_norm, sv_profile_start,
+                 sv_profile_stop, sv_set_stream,
+                 sv_sync, sv_upload, sv_version, sv_wrap)
+
+__all__ = ["State", "Energy", "energy", "C64", "C128", "SvError", "pack_circuit", "pack_pauli",
+           "load"] + list(EXPORTS)
+
+
+def _dtype_code(dtype) -> int:
+    if dtype in ("c64", "complex64", C64):
+        return C64
+    if dtype in ("c128", "complex128", C128):
+        return C128
+    raise ValueError(f"dtype {dtype!r}: expected c64 or c128")
+
+
+class State:
+    """A 2^n-amplitude state in a torch CUDA tensor, wrapped by an sv handle
+    bound to a torch stream (the current stream by default)."""
+
+    def __init__(self, n_qubits: int, dtype="c64", device="cuda", stream=None):
+        import torch
+        self.n = int(n_qubits)
+        self.code = _dtype_code(dtype)
+        tdt = torch.complex64 if self.code == C64 else torch.complex128
+        self.tensor = torch.empty(1 << self.n, dtype=tdt, device=device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.tensor.device)
+        self.h = sv_wrap(self.tensor.data_ptr(), self.n, self.code, self.stream.cuda_stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            sv_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        self.stream = stream
+        sv_set_stream(self.h, stream.cuda_stream)
+
+    def init(self, basis_index: int = 0):
+        sv_init(self.h, basis_index)
+        return self
+
+    def load(self, amplitudes: np.ndarray):
+        a = np.ascontiguousarray(amplitudes,
+                                 dtype=np.complex64 if self.code == C64 else np.complex128)
+        sv_upload(self.h, a)
+        sv_sync(self.h)
+        return self
+
+    def numpy(self) -> np.ndarray:
+        out = np.empty(1 << self.n, np.complex64 if self.code == C64 else np.complex128)
+        sv_download(self.h, out)
+        return out
+
+    def apply_gate(self, targets, controls, matrix):
+        sv_apply_gate(self.h, targets, controls, matrix)
+        return self
+
+    def apply_circuit(self, circuit, theta=None, fuse_k: int = 0):
+        sv_apply_circuit(self.h, circuit, theta, fuse_k)
+        return self
+
+    def norm(self) -> float:
+        return sv_norm(self.h)
+
+    def expval(self, terms) -> float:
+        return sv_expval(self.h, pack_pauli(terms, self.n))
+
+    def adjoint(self, circuit, theta, terms):
+        return sv_adjoint(self.h, circuit, theta, pack_pauli(terms, self.n))
+
+    def grad(self, circuit, theta, terms, checkpoint_gates=()):
+        return sv_grad(self.h, circuit, theta, pack_pauli(terms, self.n), checkpoint_gates)
+
+    def sync(self):
+        sv_sync(self.h)
+
+
+def _energy_fn():
+    import torch
+
+    class Energy(torch.autograd.Function):
+        """E(theta) = <psi(theta)|H|psi(theta)>, psi(theta) = U(theta)|basis>.
+
+        forward: sv_init + sv_apply_circuit + sv_expval on `state`;
+        backward: sv_adjoint on the forward state (the state must not be
+        changed between the two), times the incoming gradient."""
+
+        @staticmethod
+        def forward(ctx, theta, state, circuit, terms, basis=0):
+            th = theta.detach().to("cpu", torch.float64).numpy().copy()
+            pc = pack_circuit(circuit)
+            pp = pack_pauli(terms, state.n)
+            state.init(basis)
+            sv_apply_circuit(state.h, pc, th, 0)
+            e = sv_expval(state.h, pp)
+            ctx.state, ctx.pc, ctx.pp, ctx.th = state, pc, pp, th
+            return torch.tensor(e, dtype=torch.float64, device=theta.device)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            _, g = sv_adjoint(ctx.state.h, ctx.pc, ctx.th, ctx.pp)
+            gt = torch.from_numpy(g).to(grad_out.device) * grad_out
+            return gt, None, None, None, None
+
+    return Energy
+
+
+class _Lazy:
+    _cls = None
+
+    def __getattr__(self, name):
+        if _Lazy._cls is None:
+            _Lazy._cls = _energy_fn()
+        return getattr(_Lazy._cls, name)
+
+
+Energy = _Lazy()
+
+
+def energy(theta, state: State, circuit, terms, basis: int = 0):
+    """Differentiable energy (torch scalar) via the adjoint kernels."""
+    return Energy.apply(theta, state, circuit, terms, basis)

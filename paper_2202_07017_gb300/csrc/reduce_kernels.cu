@@ -1,0 +1,207 @@
+// Reductions over the state: <psi|psi>, <psi|H|psi> for a Pauli sum H
+// (Sec. 3: Hamiltonians and VQE energies), and H psi.
+//
+// Precision: products in the state's precision, accumulation in fp64.  A
+// thread sums its indices in fp64, a block reduces with warp shuffles and
+// shared memory, and a second kernel sums the per-block partials in a fixed
+// order, so a result is bit-identical from call to call (no atomics).
+//
+// A Pauli string P with masks (xm, zm) maps |b> to
+// i^{#Y} (-1)^{popcount(b & zm)} |b ^ xm>, so
+// (P psi)_x = i^{#Y} (-1)^{popcount((x ^ xm) & zm)} psi_{x ^ xm}.
+// The host folds coeff * i^{#Y} into one complex coefficient per term.
+#include <vector>
+
+#include "sv_device.cuh"
+
+namespace sv {
+
+int red_blocks(uint64_t units) {
+  const uint64_t b = (units + kRedThreads - 1) / kRedThreads;
+  return (int)(b < (uint64_t)kRedMaxBlocks ? (b ? b : 1) : kRedMaxBlocks);
+}
+
+namespace {
+
+__global__ void __launch_bounds__(kRedThreads)
+    knorm_c64(const float4* __restrict__ psi, uint64_t nvec, double* __restrict__ partials) {
+  double acc = 0.0;
+  for (uint64_t v = (uint64_t)blockIdx.x * kRedThreads + threadIdx.x; v < nvec;
+       v += (uint64_t)gridDim.x * kRedThreads) {
+    const float4 a = psi[v];
+    acc += (double)(a.x * a.x + a.y * a.y + a.z * a.z + a.w * a.w);
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+    knorm_c128(const double2* __restrict__ psi, uint64_t nvec, double* __restrict__ partials) {
+  double acc = 0.0;
+  for (uint64_t v = (uint64_t)blockIdx.x * kRedThreads + threadIdx.x; v < nvec;
+       v += (uint64_t)gridDim.x * kRedThreads) {
+    const double2 a = psi[v];
+    acc += a.x * a.x + a.y * a.y;
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+// sum_x Re( c'_k s_k(x) conj(psi_x) psi_{x ^ xm_k} ) over this chunk's terms.
+template <typename R, typename T2>
+__global__ void __launch_bounds__(kRedThreads)
+    kexpval(const T2* __restrict__ psi, uint64_t dim, const __grid_constant__ PauliDev P,
+            double* __restrict__ partials) {
+  double acc = 0.0;
+  for (uint64_t x = (uint64_t)blockIdx.x * kRedThreads + threadIdx.x; x < dim;
+       x += (uint64_t)gridDim.x * kRedThreads) {
+    const T2 a = psi[x];
+    R sum = 0;
+    for (int k = 0; k < P.nt; ++k) {
+      const uint64_t xm = P.xm[k];
+      const T2 b = xm ? psi[x ^ xm] : a;
+      const R zr = a.x * b.x + a.y * b.y;  // Re conj(a) b
+      const R zi = a.x * b.y - a.y * b.x;  // Im conj(a) b
+      const R t = (R)P.cre[k] * zr - (R)P.cim[k] * zi;
+      sum += (__popcll((x ^ xm) & P.zm[k]) & 1) ? -t : t;
+    }
+    acc += (double)sum;
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+// out_x (+)= sum_k c'_k s_k(x) psi_{x ^ xm_k}; optional partials of
+// Re conj(psi_x) out_x (the energy, when this chunk completes out).
+template <typename R, typename T2>
+__global__ void __launch_bounds__(kRedThreads)
+    kapply_pauli(T2* __restrict__ out, const T2* __restrict__ psi, uint64_t dim,
+                 const __grid_constant__ PauliDev P, int accumulate,
+                 double* __restrict__ partials) {
+  double acc = 0.0;
+  for (uint64_t x = (uint64_t)blockIdx.x * kRedThreads + threadIdx.x; x < dim;
+       x += (uint64_t)gridDim.x * kRedThreads) {
+    R orr = 0, oi = 0;
+    if (accumulate) {
+      const T2 o = out[x];
+      orr = o.x;
+      oi = o.y;
+    }
+    for (int k = 0; k < P.nt; ++k) {
+      const uint64_t xm = P.xm[k];
+      const T2 b = psi[x ^ xm];
+      const R cr = (R)P.cre[k], ci = (R)P.cim[k];
+      const R sr = cr * b.x - ci * b.y;
+      const R si = cr * b.y + ci * b.x;
+      if (__popcll((x ^ xm) & P.zm[k]) & 1) {
+        orr -= sr;
+        oi -= si;
+      } else {
+        orr += sr;
+        oi += si;
+      }
+    }
+    T2 o;
+    o.x = orr;
+    o.y = oi;
+    out[x] = o;
+    if (partials) {
+      const T2 a = psi[x];
+      acc += (double)(a.x * orr + a.y * oi);
+    }
+  }
+  if (partials) {
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+  }
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+    kfinish(const double* __restrict__ src, int count, double* __restrict__ dst, int add) {
+  const double* s = src + (size_t)blockIdx.x * count;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < count; i += kRedThreads) acc += s[i];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) dst[blockIdx.x] = add ? dst[blockIdx.x] + acc : acc;
+}
+
+}  // namespace
+
+void pauli_chunks(const sv_pauli_sum* H, std::vector<PauliDev>* out) {
+  out->clear();
+  for (int k0 = 0; k0 < H->n_terms; k0 += 64) {
+    PauliDev P{};
+    P.nt = H->n_terms - k0 < 64 ? H->n_terms - k0 : 64;
+    for (int j = 0; j < P.nt; ++j) {
+      const uint64_t xm = H->xmask[k0 + j], zm = H->zmask[k0 + j];
+      const int ny = __builtin_popcountll(xm & zm) & 3;
+      const double c = H->coeff[k0 + j];
+      P.xm[j] = xm;
+      P.zm[j] = zm;
+      // c * i^{ny}
+      P.cre[j] = ny == 0 ? c : ny == 2 ? -c : 0.0;
+      P.cim[j] = ny == 1 ? c : ny == 3 ? -c : 0.0;
+    }
+    out->push_back(P);
+  }
+}
+
+sv_status launch_norm_partials(sv_state s, double* partials, int* nparts) {
+  ProfScope prof(s->stream, "knorm");
+  if (s->dt == SV_C64) {
+    const uint64_t nvec = s->n >= 1 ? (uint64_t(1) << (s->n - 1)) : 1;
+    const int g = red_blocks(nvec);
+    knorm_c64<<<g, kRedThreads, 0, s->stream>>>((const float4*)s->data, nvec, partials);
+    *nparts = g;
+  } else {
+    const uint64_t nvec = uint64_t(1) << s->n;
+    const int g = red_blocks(nvec);
+    knorm_c128<<<g, kRedThreads, 0, s->stream>>>((const double2*)s->data, nvec, partials);
+    *nparts = g;
+  }
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return check_launch("norm kernel");
+}
+
+sv_status launch_expval_partials(sv_state s, const PauliDev& P, double* partials, int* nparts) {
+  const uint64_t dim = uint64_t(1) << s->n;
+  const int g = red_blocks(dim);
+  ProfScope prof(s->stream, "kexpval");
+  if (s->dt == SV_C64)
+    kexpval<float, float2><<<g, kRedThreads, 0, s->stream>>>((const float2*)s->data, dim, P,
+                                                             partials);
+  else
+    kexpval<double, double2><<<g, kRedThreads, 0, s->stream>>>((const double2*)s->data, dim, P,
+                                                               partials);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  *nparts = g;
+  return check_launch("expval kernel");
+}
+
+sv_status launch_apply_pauli(void* out, const void* in, sv_dtype dt, int n, cudaStream_t st,
+                             const PauliDev& P, bool accumulate, double* partials,
+                             int* nparts) {
+  const uint64_t dim = uint64_t(1) << n;
+  const int g = red_blocks(dim);
+  ProfScope prof(st, "kapply_pauli");
+  if (dt == SV_C64)
+    kapply_pauli<float, float2><<<g, kRedThreads, 0, st>>>((float2*)out, (const float2*)in, dim,
+                                                           P, accumulate ? 1 : 0, partials);
+  else
+    kapply_pauli<double, double2><<<g, kRedThreads, 0, st>>>(
+        (double2*)out, (const double2*)in, dim, P, accumulate ? 1 : 0, partials);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  if (nparts) *nparts = g;
+  return check_launch("apply_pauli kernel");
+}
+
+sv_status launch_finish(const double* src, int count, int slots, double* dst, cudaStream_t st,
+                        bool add_to_dst) {
+  if (slots <= 0) return SV_OK;
+  ProfScope prof(st, "kfinish");
+  kfinish<<<slots, kRedThreads, 0, st>>>(src, count, dst, add_to_dst ? 1 : 0);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return check_launch("finish kernel");
+}
+
+}  // namespace sv

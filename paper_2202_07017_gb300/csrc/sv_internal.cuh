@@ -1,0 +1,134 @@
+// Internal declarations of libsv: the state handle, error plumbing, the
+// kernel launchers shared by the C-ABI translation unit and the kernel
+// translation units.  Bit conventions: kernels speak in amplitude-index bit
+// positions p (qubit q <-> p = n-1-q).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <string>
+#include <vector>
+
+#include "sv.h"
+
+namespace sv {
+
+// ---- errors ----------------------------------------------------------------
+void set_error(const char* fmt, ...);
+extern std::atomic<uint64_t> g_launches;
+
+#define SV_CUDA_TRY(expr)                                                   \
+  do {                                                                      \
+    cudaError_t e_ = (expr);                                                \
+    if (e_ != cudaSuccess) {                                                \
+      ::sv::set_error("%s failed: %s", #expr, cudaGetErrorString(e_));      \
+      return e_ == cudaErrorMemoryAllocation ? SV_ERR_OOM : SV_ERR_CUDA;    \
+    }                                                                       \
+  } while (0)
+
+// Check the most recent launch on this thread.
+sv_status check_launch(const char* what);
+
+// Per-launch CUDA-event timing while sv_profile_start() is active: the
+// scope records an event before and after the launch it encloses, tagged
+// with the kernel's name.  Inactive scopes cost one atomic load.
+struct ProfScope {
+  ProfScope(cudaStream_t st, const char* name);
+  ~ProfScope();
+  cudaStream_t st;
+  int slot;
+};
+
+// ---- complex gate matrices on the host (fp64) ------------------------------
+struct cd {
+  double re, im;
+};
+
+// Up to 32 x 32 row-major.
+struct HostMatrix {
+  int k = 1;  // number of targets
+  cd m[32 * 32];
+  cd at(int r, int c) const { return m[r * (1 << k) + c]; }
+};
+
+// Builds the fp64 matrix of a circuit record (kinds of sv.h).  Returns false
+// for an unknown kind or a wrong target count.
+bool gate_matrix(const sv_gate& g, const double* theta, const double* pool, HostMatrix* out);
+
+// ---- reduction geometry -----------------------------------------------------
+constexpr int kRedThreads = 256;
+constexpr int kRedMaxBlocks = 1216;  // 152 SMs x 8
+int red_blocks(uint64_t units);
+
+}  // namespace sv
+
+// ---- the state handle --------------------------------------------------------
+struct sv_state_s {
+  void* data = nullptr;
+  int n = 0;
+  sv_dtype dt = SV_C64;
+  cudaStream_t stream = nullptr;
+  bool owned = false;
+  int device = 0;
+  // fp64 reduction scratch: partials and device results
+  double* partials = nullptr;
+  size_t partials_cap = 0;  // doubles
+  double* dres = nullptr;   // 64 doubles of device results
+  double* hres = nullptr;   // pinned host mirror of dres
+  // adjoint work states and forward checkpoints
+  void* work[2] = {nullptr, nullptr};
+  std::vector<void*> ckpt;
+  size_t bytes() const { return (size_t(1) << n) * (dt == SV_C64 ? 8 : 16); }
+};
+
+namespace sv {
+
+sv_status ensure_partials(sv_state s, size_t doubles);
+sv_status ensure_work(sv_state s, int which);
+
+// ---- gate launchers (gate_kernels.cu) -----------------------------------------
+// Applies matrix G on target bit positions tp[0..k-1] (tp[0] = MSB of tau)
+// where all bit positions cp[0..nc-1] are 1.  Picks the specialised kernel
+// from the matrix structure (phase-on-subspace, diagonal, real, swap,
+// dense 1-qubit, generic k-qubit).
+sv_status launch_gate(void* data, sv_dtype dt, int n, cudaStream_t st, int k, const int* tp,
+                      int nc, const int* cp, const HostMatrix& G);
+
+sv_status launch_init(void* data, sv_dtype dt, int n, cudaStream_t st, uint64_t basis);
+
+// ---- reductions (reduce_kernels.cu) --------------------------------------------
+struct PauliDev {
+  // terms after host preprocessing: coefficient times i^{#Y}, folded to
+  // (cre, cim); the sign (-1)^popcount((x ^ xm) & zm) is applied per index.
+  int nt;
+  uint64_t xm[64];
+  uint64_t zm[64];
+  double cre[64];
+  double cim[64];
+};
+// Fills PauliDev chunks (64 terms each) from a host Pauli sum.
+void pauli_chunks(const sv_pauli_sum* H, std::vector<PauliDev>* out);
+
+// sum over blocks -> partials[0..blocks); returns the number of partials.
+sv_status launch_norm_partials(sv_state s, double* partials, int* nparts);
+sv_status launch_expval_partials(sv_state s, const PauliDev& P, double* partials, int* nparts);
+// out = H in; if partials != NULL also Re<in|out> per block.
+sv_status launch_apply_pauli(void* out, const void* in, sv_dtype dt, int n, cudaStream_t st,
+                             const PauliDev& P, bool accumulate, double* partials,
+                             int* nparts);
+// dst[j] = sum_{i<count} src[j * count + i] for j < slots (fixed order).
+sv_status launch_finish(const double* src, int count, int slots, double* dst,
+                        cudaStream_t st, bool add_to_dst);
+
+// ---- adjoint (adjoint_kernels.cu) ----------------------------------------------
+// Un-applies U^dagger (given as matrix Gdag on bit tp, controls cp) on both
+// psi and lam; if pauli in {1,2,3} (X, Y, Z generator) first accumulates
+// Im<lam|P|psi> restricted to the control subspace into
+// partials[0..nparts).
+sv_status launch_adjoint_1q(void* psi, void* lam, sv_dtype dt, int n, cudaStream_t st, int tp,
+                            int nc, const int* cp, const HostMatrix& Gdag, int pauli,
+                            double* partials, int* nparts);
+
+}  // namespace sv

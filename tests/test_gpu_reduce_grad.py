@@ -1,0 +1,215 @@
+"""GPU parity of the fp64-accumulated reductions (norm, Pauli-sum energy,
+H psi) and of the adjoint gradient against the oracle's exact
+parameter-shift gradient and central finite differences; the
+hardware-efficient ansatz at n = 20 with the transverse-field Ising energy
+in complex64; forward-state checkpoints; the torch.autograd path."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from gpu_helpers import TOL, gpu_run, max_err, oracle_threads, rounded
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+DTYPES = ["c64", "c128"]
+# normwise relative gradient bars: ||g - g_ref||_inf / ||g_ref||_inf
+GRAD_TOL = {"c64": 1e-5, "c128": 1e-10}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _threads():
+    oracle_threads()
+
+
+def _state(n, dtype, psi):
+    from paper_2202_07017_gb300 import State
+    return State(n, dtype).load(np.asarray(psi))
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("n", [1, 2, 4, 7, 12])
+def test_norm_and_expval(dtype, n):
+    psi = rounded(W.random_state(n, 50 + n), dtype)
+    terms = W.random_pauli_sum(n, 30, n) + (W.tfim(n) if n > 1 else [])
+    st = _state(n, dtype, psi)
+    try:
+        e = st.expval(terms)
+        nrm = st.norm()
+        e2 = st.expval(terms)
+    finally:
+        st.close()
+    ref = oracle.expval(psi, terms)
+    scale = sum(abs(c) for c, _ in terms)
+    assert abs(e - ref) <= TOL[dtype] * scale
+    assert e == e2  # fixed reduction order: bit-identical repeat
+    assert abs(nrm - oracle.norm2(psi)) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_expval_more_than_one_chunk_of_terms(dtype):
+    n = 9
+    psi = rounded(W.random_state(n, 8), dtype)
+    terms = W.random_pauli_sum(n, 150, 17)
+    st = _state(n, dtype, psi)
+    try:
+        e = st.expval(terms)
+    finally:
+        st.close()
+    assert abs(e - oracle.expval(psi, terms)) <= TOL[dtype] * sum(abs(c) for c, _ in terms)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_apply_pauli_sum(dtype):
+    from paper_2202_07017_gb300 import State, sv_apply_pauli_sum
+    n = 8
+    psi = rounded(W.random_state(n, 4), dtype)
+    terms = W.random_pauli_sum(n, 70, 5)
+    a = _state(n, dtype, psi)
+    b = State(n, dtype)
+    try:
+        sv_apply_pauli_sum(b.h, a.h, terms)
+        got = b.numpy()
+    finally:
+        a.close()
+        b.close()
+    P = {"X": np.array([[0, 1], [1, 0]]), "Y": np.array([[0, -1j], [1j, 0]]),
+         "Z": np.array([[1, 0], [0, -1]])}
+    ref = np.zeros_like(psi)
+    for c, ops in terms:
+        phi = psi.copy()
+        for q, L in ops:
+            phi = oracle.apply_gate(phi, n, [q], [], P[L])
+        ref += c * phi
+    assert max_err(got, ref) <= TOL[dtype] * sum(abs(c) for c, _ in terms)
+
+
+def _adjoint(c, theta, terms, dtype, psi0=None, checkpoints=None):
+    from paper_2202_07017_gb300 import State
+    st = State(c.n_qubits, dtype)
+    try:
+        if psi0 is None:
+            st.init(0)
+        else:
+            st.load(np.asarray(psi0))
+        if checkpoints is None:
+            st.apply_circuit(c, theta)
+            e, g = st.adjoint(c, theta, terms)
+        else:
+            e, g = st.grad(c, theta, terms, checkpoints)
+        return e, g, st.numpy()
+    finally:
+        st.close()
+
+
+def _rel(g, ref):
+    return float(np.max(np.abs(g - ref)) / max(np.max(np.abs(ref)), 1e-300))
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("n,seed", [(1, 1), (3, 2), (6, 3), (9, 4)])
+def test_adjoint_random_circuits_vs_parameter_shift(dtype, n, seed):
+    kinds = ("H", "X", "Y", "Z", "RX", "RY", "RZ", "U1", "SWAP", "MATRIX")
+    c, theta = W.random_gates(n, 40, 300 + seed, max_tar=min(3, n), max_ctrl=2, kinds=kinds)
+    terms = W.random_pauli_sum(n, 8, seed)
+    psi0 = rounded(W.random_state(n, seed), dtype)
+    e, g, _ = _adjoint(c, theta, terms, dtype, psi0)
+    e_ref = oracle.energy(c, theta, terms, psi0)
+    g_ref = oracle.grad_param_shift(c, theta, terms, psi0=psi0)
+    assert abs(e - e_ref) <= TOL[dtype] * sum(abs(t[0]) for t in terms)
+    if c.n_params:
+        assert _rel(g, g_ref) <= GRAD_TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_adjoint_shared_parameters(dtype):
+    n = 5
+    gates = [W.Gate("RX", (0,), (), 0), W.Gate("RY", (1,), (0,), 1), W.Gate("RZ", (2,), (), 0),
+             W.Gate("H", (3,)), W.Gate("RY", (3,), (4,), 1), W.Gate("Z", (4,), (2,)),
+             W.Gate("RX", (4,), (), 0)]
+    c = W.Circuit(n, gates, 2)
+    theta = np.array([0.37, -1.2])
+    terms = W.tfim(n)
+    e, g, _ = _adjoint(c, theta, terms, dtype)
+    assert _rel(g, oracle.grad_param_shift(c, theta, terms)) <= GRAD_TOL[dtype]
+
+
+def test_hea_n20_energy_and_gradient():
+    """Hardware-efficient ansatz n = 20, L = 10 (200 parameters), TFIM
+    energy, complex64 state with fp64 reductions: energy against the oracle,
+    gradient against the exact parameter shift on sampled parameters and
+    against central differences of the GPU energy."""
+    n, L = 20, 10
+    c, theta = W.hea(n, L, 1002)
+    terms = W.tfim(n)
+    e, g, _ = _adjoint(c, theta, terms, "c64")
+    e_ref = oracle.energy(c, theta, terms)
+    assert abs(e - e_ref) <= 1e-5 * sum(abs(t[0]) for t in terms)
+    sample = [0, 7, 19, 63, 101, 150, 188, 199]
+    g_ref = oracle.grad_param_shift(c, theta, terms, params=sample)
+    assert np.max(np.abs(g[sample] - g_ref[sample])) <= 1e-5 * np.max(np.abs(g_ref[sample]))
+    # central differences of the GPU energy, h = 1e-2 (truncation ~ h^2 / 6)
+    from paper_2202_07017_gb300 import State
+    st = State(n, "c64")
+    try:
+        h = 1e-2
+        fd = []
+        for j in sample[:4]:
+            tp, tm = theta.copy(), theta.copy()
+            tp[j] += h
+            tm[j] -= h
+            ep = st.init(0).apply_circuit(c, tp).expval(terms)
+            em = st.init(0).apply_circuit(c, tm).expval(terms)
+            fd.append((ep - em) / (2 * h))
+    finally:
+        st.close()
+    fd = np.array(fd)
+    assert np.max(np.abs(g[sample[:4]] - fd)) <= 1e-3 * np.max(np.abs(g[sample]))
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_checkpointed_grad_matches_plain_adjoint(dtype):
+    n, depth = 12, 8
+    c, theta = W.random_layered(n, depth, 55)
+    terms = W.sum_z(n)
+    e0, g0, _ = _adjoint(c, theta, terms, dtype)
+    per_layer = [i for i, gt in enumerate(c.gates) if gt.kind == "RX" and gt.targets == (0,)]
+    ck = per_layer[2::2]
+    e1, g1, final = _adjoint(c, theta, terms, dtype, checkpoints=ck)
+    ref_state = oracle.run(c, theta)
+    assert max_err(final, ref_state) <= TOL[dtype]
+    assert abs(e1 - e0) <= TOL[dtype] * n
+    g_ref = oracle.grad_param_shift(c, theta, terms, params=list(range(0, c.n_params, 7)))
+    idx = list(range(0, c.n_params, 7))
+    assert np.max(np.abs(g1[idx] - g_ref[idx])) <= GRAD_TOL[dtype] * np.max(np.abs(g_ref[idx]))
+    assert np.max(np.abs(g1 - g0)) <= GRAD_TOL[dtype] * np.max(np.abs(g0))
+
+
+def test_torch_autograd_energy():
+    from paper_2202_07017_gb300 import State, energy
+    n, L = 8, 3
+    c, theta = W.hea(n, L, 9)
+    terms = W.tfim(n)
+    st = State(n, "c64")
+    try:
+        th = torch.tensor(theta, dtype=torch.float64, requires_grad=True)
+        e = energy(th, st, c, terms)
+        (2.0 * e).backward()
+    finally:
+        st.close()
+    g_ref = oracle.grad_param_shift(c, theta, terms)
+    assert abs(e.item() - oracle.energy(c, theta, terms)) <= 1e-5 * n
+    assert np.max(np.abs(th.grad.numpy() - 2.0 * g_ref)) <= 2e-5 * np.max(np.abs(g_ref))
+
+
+def test_gradient_rejects_non_rotation_parameters():
+    from paper_2202_07017_gb300 import State, SvError
+    n = 3
+    st = State(n, "c64").init(0)
+    c = W.Circuit(n, [W.Gate("U1", (0,), (), 0)], 1)
+    with pytest.raises(SvError):
+        st.adjoint(c, [0.3], W.sum_z(n))
+    st.close()

@@ -261,6 +261,23 @@ def test_param_shift_matches_central_difference():
     assert np.max(np.abs(gs - gf)) < 1e-7
 
 
+def test_controlled_rotation_shift_rule_matches_central_difference():
+    n = 4
+    gates = [W.Gate("H", (0,)), W.Gate("H", (1,)), W.Gate("RX", (2,), (0,), 0),
+             W.Gate("RY", (3,), (1, 0), 1), W.Gate("RZ", (1,), (3,), 2),
+             W.Gate("RY", (0,), (), 3), W.Gate("X", (2,), (3,))]
+    c = W.Circuit(n, gates, 4)
+    theta = np.array([0.4, -1.3, 2.2, 0.9])
+    H = W.random_pauli_sum(n, 6, 3)
+    gs = oracle.grad_param_shift(c, theta, H)
+    gf = oracle.grad_fd(c, theta, H, h=1e-4)
+    assert np.max(np.abs(gs - gf)) < 1e-7
+    # the two-term rule alone is not exact for a controlled rotation
+    two = 0.5 * (oracle.energy(c, theta, H, None, 2, math.pi / 2)
+                 - oracle.energy(c, theta, H, None, 2, -math.pi / 2))
+    assert abs(two - gs[0]) > 1e-4
+
+
 def test_threads_do_not_change_results():
     if not oracle.have_openmp():
         pytest.skip("oracle built without OpenMP")
