@@ -97,7 +97,7 @@ class _Packed:
         self.ntar = np.zeros(ng, np.int32)
         self.tar = np.zeros(5 * max(ng, 1), np.int32)
         self.nctl = np.zeros(ng, np.int32)
-        self.ctl = np.zeros(8 * max(ng, 1), np.int32)
+        self.ctl = np.zeros(40 * max(ng, 1), np.int32)
         self.param = np.full(ng, -1, np.int32)
         self.angle = np.zeros(ng, np.float64)
         self.mat_off = np.zeros(ng, np.int64)
@@ -108,7 +108,7 @@ class _Packed:
             self.ntar[g] = len(gate.targets)
             self.tar[5 * g:5 * g + len(gate.targets)] = gate.targets
             self.nctl[g] = len(gate.controls)
-            self.ctl[8 * g:8 * g + len(gate.controls)] = gate.controls
+            self.ctl[40 * g:40 * g + len(gate.controls)] = gate.controls
             self.param[g] = gate.param
             self.angle[g] = gate.angle
             if gate.kind == "MATRIX":

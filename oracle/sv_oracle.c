@@ -138,7 +138,7 @@ int orc_apply(int n, cplx* psi, int k, const int* targets, int nc,
 }
 
 /* A circuit applied gate by gate.  Gate g has kind[g], ntar[g] targets in
- * tar[5g..], nctl[g] controls in ctl[8g..], and either a parameter index
+ * tar[5g..], nctl[g] controls in ctl[40g..], and either a parameter index
  * param[g] >= 0 (angle theta[param[g]]) or a fixed angle angle[g].  MATRIX
  * gates read 4^ntar entries of pool from mat_off[g].  If shift_gate >= 0,
  * that gate's angle is increased by `shift` (parameter-shift evaluations). */
@@ -157,7 +157,7 @@ int orc_run(int n, cplx* psi, int ng, const int* kind, const int* ntar,
       int want = gate_matrix(kind[g], a, G);
       if (want != ntar[g]) return 1;
     }
-    int rc = orc_apply(n, psi, ntar[g], tar + 5 * g, nctl[g], ctl + 8 * g, M);
+    int rc = orc_apply(n, psi, ntar[g], tar + 5 * g, nctl[g], ctl + 40 * g, M);
     if (rc) return rc;
   }
   return 0;

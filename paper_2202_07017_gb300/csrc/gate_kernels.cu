@@ -17,6 +17,7 @@
 // costs more than the HBM traffic.
 #include <algorithm>
 #include <cstdlib>
+#include <type_traits>
 #include <vector>
 
 #include "sv_device.cuh"
@@ -346,13 +347,32 @@ __global__ void kinit_c128(double2* __restrict__ psi, I n_vec, I bvec) {
 }
 
 // ---- host side -------------------------------------------------------------------
-int items_setting() {
-  static int v = [] {
-    const char* e = getenv("SV_GATE_ITEMS");
-    int x = e ? atoi(e) : 2;
-    return (x == 1 || x == 2 || x == 4) ? x : 2;
-  }();
+// Amplitude vectors per thread: kernels that read two streams (pairs, SWAP)
+// keep 2 x ITEMS vectors in flight, single-stream kernels (bit-0 pairs,
+// phases, init) ITEMS vectors; both defaults give 64 bytes in flight per
+// thread.  SV_ITEMS_PAIR / SV_ITEMS_SINGLE (1, 2, 4, 8) override them.
+int env_items(const char* name, int dflt) {
+  const char* e = getenv(name);
+  const int x = e ? atoi(e) : dflt;
+  return (x == 1 || x == 2 || x == 4 || x == 8) ? x : dflt;
+}
+int items_pair() {
+  static const int v = env_items("SV_ITEMS_PAIR", 2);
   return v;
+}
+int items_single() {
+  static const int v = env_items("SV_ITEMS_SINGLE", 4);
+  return v;
+}
+
+template <typename F>
+void with_items(int items, F&& f) {
+  switch (items) {
+    case 1: f(std::integral_constant<int, 1>{}); break;
+    case 2: f(std::integral_constant<int, 2>{}); break;
+    case 8: f(std::integral_constant<int, 8>{}); break;
+    default: f(std::integral_constant<int, 4>{}); break;
+  }
 }
 
 template <typename I>
@@ -388,39 +408,44 @@ void launch_k(void (*kern)(KArgs...), const char* name, unsigned grid, cudaStrea
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 
-// complex64 1-qubit dense/diag/real/imoff dispatch on ITEMS.
+// Splits control bit positions for complex64 vectors: bit 0 selects the odd
+// amplitude of each vector (amp1_only), bits >= 1 become vector-index bits.
+template <typename I>
+void split_c64(const int* bits, int nb, std::vector<int>* vpos, I* vmask, int* amp1_only) {
+  for (int j = 0; j < nb; ++j) {
+    if (bits[j] == 0) {
+      *amp1_only = 1;
+    } else {
+      vpos->push_back(bits[j] - 1);
+      *vmask |= I(1) << (bits[j] - 1);
+    }
+  }
+}
+
 template <typename I, int MK>
 void run_1q_c64(float4* psi, int n, cudaStream_t st, int t, int nc, const int* cp,
                 const M2<float>& g) {
   std::vector<int> vpos;
   I cmask = 0;
   int amp1_only = 0;
-  for (int j = 0; j < nc; ++j) {
-    if (cp[j] == 0) {
-      amp1_only = 1;
-    } else {
-      vpos.push_back(cp[j] - 1);
-      cmask |= I(1) << (cp[j] - 1);
-    }
-  }
-  const int items = items_setting();
+  split_c64<I>(cp, nc, &vpos, &cmask, &amp1_only);
   if (t == 0) {
     Ins<I> ins = make_ins<I>(vpos);
     const I nu = I(1) << (n - 1 - (int)vpos.size());
-    if (items == 1) launch_k(k1q_c64_in<I, MK, 1>, "k1q_c64_in", grid_for(nu, 1), st, psi, nu, ins, cmask, g);
-    else if (items == 2) launch_k(k1q_c64_in<I, MK, 2>, "k1q_c64_in", grid_for(nu, 2), st, psi, nu, ins, cmask, g);
-    else launch_k(k1q_c64_in<I, MK, 4>, "k1q_c64_in", grid_for(nu, 4), st, psi, nu, ins, cmask, g);
+    with_items(items_single(), [&](auto it) {
+      constexpr int IT = decltype(it)::value;
+      launch_k(k1q_c64_in<I, MK, IT>, "k1q_c64_in", grid_for(nu, IT), st, psi, nu, ins, cmask, g);
+    });
   } else {
     vpos.push_back(t - 1);
     Ins<I> ins = make_ins<I>(vpos);
     const I tmask = I(1) << (t - 1);
     const I nu = I(1) << (n - 1 - (int)vpos.size());
-    if (items == 1)
-      launch_k(k1q_c64_pair<I, MK, 1>, "k1q_c64_pair", grid_for(nu, 1), st, psi, nu, ins, tmask, cmask, amp1_only, g);
-    else if (items == 2)
-      launch_k(k1q_c64_pair<I, MK, 2>, "k1q_c64_pair", grid_for(nu, 2), st, psi, nu, ins, tmask, cmask, amp1_only, g);
-    else
-      launch_k(k1q_c64_pair<I, MK, 4>, "k1q_c64_pair", grid_for(nu, 4), st, psi, nu, ins, tmask, cmask, amp1_only, g);
+    with_items(items_pair(), [&](auto it) {
+      constexpr int IT = decltype(it)::value;
+      launch_k(k1q_c64_pair<I, MK, IT>, "k1q_c64_pair", grid_for(nu, IT), st, psi, nu, ins,
+               tmask, cmask, amp1_only, g);
+    });
   }
 }
 
@@ -436,10 +461,11 @@ void run_1q_c128(double2* psi, int n, cudaStream_t st, int t, int nc, const int*
   Ins<I> ins = make_ins<I>(pos);
   const I tmask = I(1) << t;
   const I nu = I(1) << (n - (int)pos.size());
-  const int items = items_setting();
-  if (items == 1) launch_k(k1q_c128_pair<I, MK, 1>, "k1q_c128_pair", grid_for(nu, 1), st, psi, nu, ins, tmask, cmask, g);
-  else if (items == 2) launch_k(k1q_c128_pair<I, MK, 2>, "k1q_c128_pair", grid_for(nu, 2), st, psi, nu, ins, tmask, cmask, g);
-  else launch_k(k1q_c128_pair<I, MK, 4>, "k1q_c128_pair", grid_for(nu, 4), st, psi, nu, ins, tmask, cmask, g);
+  with_items(items_pair(), [&](auto it) {
+    constexpr int IT = decltype(it)::value;
+    launch_k(k1q_c128_pair<I, MK, IT>, "k1q_c128_pair", grid_for(nu, IT), st, psi, nu, ins,
+             tmask, cmask, g);
+  });
 }
 
 template <typename I>
@@ -470,35 +496,31 @@ void run_1q(void* data, sv_dtype dt, int n, cudaStream_t st, int t, int nc, cons
 template <typename I, int PK>
 void run_phase_pk(void* data, sv_dtype dt, int n, cudaStream_t st, const std::vector<int>& bits,
                   cd ph) {
-  const int items = items_setting();
   if (dt == SV_C64) {
     float4* psi = (float4*)data;
     std::vector<int> vpos;
     I omask = 0;
     int amp1_only = 0;
-    for (int b : bits) {
-      if (b == 0) {
-        amp1_only = 1;
-      } else {
-        vpos.push_back(b - 1);
-        omask |= I(1) << (b - 1);
-      }
-    }
+    split_c64<I>(bits.data(), (int)bits.size(), &vpos, &omask, &amp1_only);
     Ins<I> ins = make_ins<I>(vpos);
     const I nu = I(1) << (n - 1 - (int)vpos.size());
     const float c = (float)ph.re, s = (float)ph.im;
-    if (items == 1) launch_k(kphase_c64<I, PK, 1>, "kphase_c64", grid_for(nu, 1), st, psi, nu, ins, omask, amp1_only, c, s);
-    else if (items == 2) launch_k(kphase_c64<I, PK, 2>, "kphase_c64", grid_for(nu, 2), st, psi, nu, ins, omask, amp1_only, c, s);
-    else launch_k(kphase_c64<I, PK, 4>, "kphase_c64", grid_for(nu, 4), st, psi, nu, ins, omask, amp1_only, c, s);
+    with_items(items_single(), [&](auto it) {
+      constexpr int IT = decltype(it)::value;
+      launch_k(kphase_c64<I, PK, IT>, "kphase_c64", grid_for(nu, IT), st, psi, nu, ins, omask,
+               amp1_only, c, s);
+    });
   } else {
     double2* psi = (double2*)data;
     I omask = 0;
     for (int b : bits) omask |= I(1) << b;
     Ins<I> ins = make_ins<I>(bits);
     const I nu = I(1) << (n - (int)bits.size());
-    if (items == 1) launch_k(kphase_c128<I, PK, 1>, "kphase_c128", grid_for(nu, 1), st, psi, nu, ins, omask, ph.re, ph.im);
-    else if (items == 2) launch_k(kphase_c128<I, PK, 2>, "kphase_c128", grid_for(nu, 2), st, psi, nu, ins, omask, ph.re, ph.im);
-    else launch_k(kphase_c128<I, PK, 4>, "kphase_c128", grid_for(nu, 4), st, psi, nu, ins, omask, ph.re, ph.im);
+    with_items(items_single(), [&](auto it) {
+      constexpr int IT = decltype(it)::value;
+      launch_k(kphase_c128<I, PK, IT>, "kphase_c128", grid_for(nu, IT), st, psi, nu, ins, omask,
+               ph.re, ph.im);
+    });
   }
 }
 
@@ -517,37 +539,33 @@ template <typename I>
 void run_swap(void* data, sv_dtype dt, int n, cudaStream_t st, int a, int b, int nc,
               const int* cp) {
   if (a < b) std::swap(a, b);  // a > b
-  const int items = items_setting();
   if (dt == SV_C64) {
     float4* psi = (float4*)data;
     std::vector<int> vpos;
     I cmask = 0;
     int amp1_only = 0;
-    for (int j = 0; j < nc; ++j) {
-      if (cp[j] == 0) {
-        amp1_only = 1;
-      } else {
-        vpos.push_back(cp[j] - 1);
-        cmask |= I(1) << (cp[j] - 1);
-      }
-    }
+    split_c64<I>(cp, nc, &vpos, &cmask, &amp1_only);
     const I amask = I(1) << (a - 1);
     if (b == 0) {
       vpos.push_back(a - 1);
       Ins<I> ins = make_ins<I>(vpos);
       const I nu = I(1) << (n - 1 - (int)vpos.size());
-      if (items == 1) launch_k(kswap_c64_v0<I, 1>, "kswap_c64_v0", grid_for(nu, 1), st, psi, nu, ins, amask, cmask);
-      else if (items == 2) launch_k(kswap_c64_v0<I, 2>, "kswap_c64_v0", grid_for(nu, 2), st, psi, nu, ins, amask, cmask);
-      else launch_k(kswap_c64_v0<I, 4>, "kswap_c64_v0", grid_for(nu, 4), st, psi, nu, ins, amask, cmask);
+      with_items(items_pair(), [&](auto it) {
+        constexpr int IT = decltype(it)::value;
+        launch_k(kswap_c64_v0<I, IT>, "kswap_c64_v0", grid_for(nu, IT), st, psi, nu, ins, amask,
+                 cmask);
+      });
     } else {
       const I bmask = I(1) << (b - 1);
       vpos.push_back(a - 1);
       vpos.push_back(b - 1);
       Ins<I> ins = make_ins<I>(vpos);
       const I nu = I(1) << (n - 1 - (int)vpos.size());
-      if (items == 1) launch_k(kswap_c64_vv<I, 1>, "kswap_c64_vv", grid_for(nu, 1), st, psi, nu, ins, amask, bmask, cmask, amp1_only);
-      else if (items == 2) launch_k(kswap_c64_vv<I, 2>, "kswap_c64_vv", grid_for(nu, 2), st, psi, nu, ins, amask, bmask, cmask, amp1_only);
-      else launch_k(kswap_c64_vv<I, 4>, "kswap_c64_vv", grid_for(nu, 4), st, psi, nu, ins, amask, bmask, cmask, amp1_only);
+      with_items(items_pair(), [&](auto it) {
+        constexpr int IT = decltype(it)::value;
+        launch_k(kswap_c64_vv<I, IT>, "kswap_c64_vv", grid_for(nu, IT), st, psi, nu, ins, amask,
+                 bmask, cmask, amp1_only);
+      });
     }
   } else {
     double2* psi = (double2*)data;
@@ -560,16 +578,34 @@ void run_swap(void* data, sv_dtype dt, int n, cudaStream_t st, int a, int b, int
     Ins<I> ins = make_ins<I>(pos);
     const I amask = I(1) << a, bmask = I(1) << b;
     const I nu = I(1) << (n - (int)pos.size());
-    if (items == 1) launch_k(kswap_c128<I, 1>, "kswap_c128", grid_for(nu, 1), st, psi, nu, ins, amask, bmask, cmask);
-    else if (items == 2) launch_k(kswap_c128<I, 2>, "kswap_c128", grid_for(nu, 2), st, psi, nu, ins, amask, bmask, cmask);
-    else launch_k(kswap_c128<I, 4>, "kswap_c128", grid_for(nu, 4), st, psi, nu, ins, amask, bmask, cmask);
+    with_items(items_pair(), [&](auto it) {
+      constexpr int IT = decltype(it)::value;
+      launch_k(kswap_c128<I, IT>, "kswap_c128", grid_for(nu, IT), st, psi, nu, ins, amask, bmask,
+               cmask);
+    });
   }
+}
+
+template <int K, typename R, typename I>
+GenParams<K, R, I> gen_params(const int* tp, const HostMatrix& G) {
+  constexpr int D = 1 << K;
+  GenParams<K, R, I> p;
+  for (int t = 0; t < D; ++t) {
+    I o = 0;
+    for (int j = 0; j < K; ++j)
+      if ((t >> (K - 1 - j)) & 1) o |= I(1) << tp[j];
+    p.off[t] = o;
+  }
+  for (int e = 0; e < D * D; ++e) {
+    p.gr[e] = (R)G.m[e].re;
+    p.gi[e] = (R)G.m[e].im;
+  }
+  return p;
 }
 
 template <int K, typename I>
 void run_gen_k(void* data, sv_dtype dt, int n, cudaStream_t st, const int* tp, int nc,
                const int* cp, const HostMatrix& G) {
-  constexpr int D = 1 << K;
   std::vector<int> pos(tp, tp + K);
   I cmask = 0;
   for (int j = 0; j < nc; ++j) {
@@ -579,33 +615,12 @@ void run_gen_k(void* data, sv_dtype dt, int n, cudaStream_t st, const int* tp, i
   Ins<I> ins = make_ins<I>(pos);
   const I nu = I(1) << (n - (int)pos.size());
   const unsigned grid = grid_for(nu, 1);
-  if (dt == SV_C64) {
-    GenParams<K, float, I> p;
-    for (int t = 0; t < D; ++t) {
-      I o = 0;
-      for (int j = 0; j < K; ++j)
-        if ((t >> (K - 1 - j)) & 1) o |= I(1) << tp[j];
-      p.off[t] = o;
-    }
-    for (int e = 0; e < D * D; ++e) {
-      p.gr[e] = (float)G.m[e].re;
-      p.gi[e] = (float)G.m[e].im;
-    }
-    launch_k(kgen<K, float, float2, I>, "kgen", grid, st, (float2*)data, nu, ins, cmask, p);
-  } else {
-    GenParams<K, double, I> p;
-    for (int t = 0; t < D; ++t) {
-      I o = 0;
-      for (int j = 0; j < K; ++j)
-        if ((t >> (K - 1 - j)) & 1) o |= I(1) << tp[j];
-      p.off[t] = o;
-    }
-    for (int e = 0; e < D * D; ++e) {
-      p.gr[e] = G.m[e].re;
-      p.gi[e] = G.m[e].im;
-    }
-    launch_k(kgen<K, double, double2, I>, "kgen", grid, st, (double2*)data, nu, ins, cmask, p);
-  }
+  if (dt == SV_C64)
+    launch_k(kgen<K, float, float2, I>, "kgen_c64", grid, st, (float2*)data, nu, ins, cmask,
+             gen_params<K, float, I>(tp, G));
+  else
+    launch_k(kgen<K, double, double2, I>, "kgen_c128", grid, st, (double2*)data, nu, ins, cmask,
+             gen_params<K, double, I>(tp, G));
 }
 
 template <typename I>
@@ -690,16 +705,18 @@ sv_status launch_init(void* data, sv_dtype dt, int n, cudaStream_t st, uint64_t 
       launch_k(kinit_c64<uint32_t, 4>, "kinit_c64", grid_for(nu, 4), st, (float4*)data, nu,
                (uint32_t)(basis >> 1), (int)(basis & 1));
     } else {
-      launch_k(kinit_c64<uint64_t, 4>, "kinit_c64", grid_for(nvec, 4), st, (float4*)data, nvec, basis >> 1,
-               (int)(basis & 1));
+      launch_k(kinit_c64<uint64_t, 4>, "kinit_c64", grid_for(nvec, 4), st, (float4*)data, nvec,
+               basis >> 1, (int)(basis & 1));
     }
   } else {
     const uint64_t nvec = uint64_t(1) << n;
     if (use_32bit_index(n, dt)) {
       const uint32_t nu = (uint32_t)nvec;
-      launch_k(kinit_c128<uint32_t, 4>, "kinit_c128", grid_for(nu, 4), st, (double2*)data, nu, (uint32_t)basis);
+      launch_k(kinit_c128<uint32_t, 4>, "kinit_c128", grid_for(nu, 4), st, (double2*)data, nu,
+               (uint32_t)basis);
     } else {
-      launch_k(kinit_c128<uint64_t, 4>, "kinit_c128", grid_for(nvec, 4), st, (double2*)data, nvec, basis);
+      launch_k(kinit_c128<uint64_t, 4>, "kinit_c128", grid_for(nvec, 4), st, (double2*)data, nvec,
+               basis);
     }
   }
   return check_launch("init kernel");
