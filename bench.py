@@ -185,6 +185,90 @@ def adjoint_ratio(torch, reps=3):
             "energy": e}
 
 
+def fused_layered(torch, n=33, depth=40, k=4):
+    """Random layered circuit (RX, RY, RZ on every qubit + CZ brick), n = 33
+    complex64 (64 GiB), depth 40: fused qubit-block passes for the whole
+    circuit, and fused vs one-kernel-per-gate on its first two layers."""
+    import workloads as W
+    from paper_2202_07017_gb300 import (C64, pack_circuit, sv_alloc, sv_apply_circuit, sv_free,
+                                        sv_fusion_plan, sv_init)
+    c, theta = W.random_layered(n, depth, 1004)
+    pc = pack_circuit(c)
+    # the first two layers: 3n rotations each, CZ brick from i = 0 and from i = 1
+    layer2 = W.Circuit(n, c.gates[:2 * 3 * n + len(range(0, n - 1, 2)) + len(range(1, n - 1, 2))],
+                       c.n_params)
+    p2 = pack_circuit(layer2)
+    _, _, npass, _ = sv_fusion_plan(pc, theta, C64, k)
+    st = torch.cuda.current_stream()
+    h = sv_alloc(n, C64, st.cuda_stream)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        ev[0].record(st)
+        fn()
+        ev[1].record(st)
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1]) / 1e3
+
+    try:
+        sv_init(h, 0)
+        sv_apply_circuit(h, p2, theta, k)        # warm-up
+        t_full = timed(lambda: sv_apply_circuit(h, pc, theta, k))
+        sv_init(h, 0)
+        t2_f = timed(lambda: sv_apply_circuit(h, p2, theta, k))
+        sv_init(h, 0)
+        t2_u = timed(lambda: sv_apply_circuit(h, p2, theta, 0))
+    finally:
+        sv_free(h)
+    pass_bytes = 2 * 8 * 2 ** n
+    return {"workload": f"random layered n={n} complex64 depth {depth} ({len(c.gates)} gates), "
+                        f"fused register groups of <= {k} qubits",
+            "passes": npass, "fused_s": t_full, "gate_apps_per_s": len(c.gates) / t_full,
+            "fused_pass_gbs": npass * pass_bytes / t_full / 1e9,
+            "first_2_layers": {"gates": len(layer2.gates), "fused_s": t2_f, "unfused_s": t2_u,
+                               "speedup": t2_u / t2_f},
+            "unfused_full_estimate_s": t2_u * len(c.gates) / len(layer2.gates)}
+
+
+def gate_table(n, dtype, reps=5):
+    """Per-kernel bandwidth for single gates on every kind of bit position:
+    H on bit p, controlled-U1 on bits (a, b), SWAP on (a, b).  Algorithmic
+    bytes: 2 * amplitude bytes * amplitudes changed."""
+    import torch
+    from paper_2202_07017_gb300 import State, sv_apply_gate, sv_profile_start, sv_profile_stop
+    st = State(n, dtype).init(0)
+    amp = 8 if dtype == "c64" else 16
+    Hm = np.array([[1, 1], [1, -1]]) / np.sqrt(2)
+    U1 = np.diag([1, np.exp(0.3j)])
+    SW = np.eye(4)[[0, 2, 1, 3]]
+
+    def q(p):
+        return n - 1 - p
+
+    cases = [(f"H b{p}", [q(p)], [], Hm, 2 * amp * 2 ** n)
+             for p in [0, 1, 2, 3, 4, 5, 8, 12, 16, 20, 24, n - 2, n - 1]]
+    cases += [(f"CU1 b{a},{b}", [q(a)], [q(b)], U1, 2 * amp * 2 ** (n - 2))
+              for a, b in [(n - 1, 0), (n - 1, 1), (n - 1, 2), (n - 1, 3), (n - 1, 4), (n - 1, 5),
+                           (n - 1, 8), (n - 1, 16), (n - 1, n - 2), (15, 0), (15, 14), (1, 0)]]
+    cases += [(f"SWAP b{a},{b}", [q(a), q(b)], [], SW, 2 * amp * 2 ** (n - 1))
+              for a, b in [(n - 1, 0), (n - 2, 1), (20, 9), (15, 14)]]
+    out = []
+    for name, t, c, m, balg in cases:
+        for _ in range(2):
+            sv_apply_gate(st.h, t, c, m)
+        torch.cuda.synchronize()
+        sv_profile_start()
+        for _ in range(reps):
+            sv_apply_gate(st.h, t, c, m)
+        prof = sv_profile_stop()
+        (k, (cnt, ms)), = prof.items()
+        out.append({"case": name, "kernel": k, "ms": ms / cnt,
+                    "alg_gbs": balg / (ms / cnt / 1e3) / 1e9})
+    st.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -194,8 +278,16 @@ def main():
     ap.add_argument("--n", type=int, default=N_QFT)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fused", action="store_true")
+    ap.add_argument("--gate-table", choices=["c64", "c128"],
+                    help="print per-kernel bandwidth by bit position and exit")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+
+    if args.gate_table:
+        for row in gate_table(args.n, args.gate_table):
+            print(json.dumps(row), flush=True)
+        return
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -311,6 +403,7 @@ def main():
                    "path": "sv_upload (pinned host) + sv_apply_circuit + sv_download"}
             del host, hv
         adj = adjoint_ratio(torch)
+        fused = None if args.no_fused else fused_layered(torch)
         cpu = None
         if not args.no_cpu:
             threads = os.cpu_count() or 1
@@ -342,6 +435,7 @@ def main():
             "gpu_launches": launches,
             "clocks": clk,
             "adjoint": adj,
+            "fused": fused,
         }
     sv_free(h)
     if out is not None:

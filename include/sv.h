@@ -170,6 +170,18 @@ sv_status sv_apply_gate(sv_state s, const int* targets, int n_tar,
 sv_status sv_apply_circuit(sv_state s, const sv_circuit* c, const double* theta,
                            int fuse_k);
 
+/* Host-only dry run of the fusion planner used by sv_apply_circuit with
+ * fuse_k >= 2 (no GPU call).  order[0..n_gates) receives the circuit gate
+ * indices in the order they will be applied, pass_of[k] the pass that
+ * applies order[k] (-1: applied alone by the unfused kernels), *n_passes
+ * the number of passes; if staged_bits is not NULL, staged_bits[2p] and
+ * [2p+1] receive the low and high 32 bits of pass p's staged amplitude-index
+ * bit mask.  Arrays are caller-owned with n_gates (staged_bits: 2 n_gates)
+ * entries.  Errors: SV_ERR_INVALID. */
+sv_status sv_fusion_plan(const sv_circuit* c, const double* theta, sv_dtype dtype, int fuse_k,
+                         int32_t* order, int32_t* pass_of, int32_t* n_passes,
+                         int32_t* staged_bits);
+
 /* ---- reductions (fp64 accumulation, fixed reduction order) ------------ */
 
 /* <psi|psi>.  Synchronises.  Result bit-identical across calls. */

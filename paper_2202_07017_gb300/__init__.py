@@ -15,6 +15,7 @@ import numpy as np
 from .sv import (C64, C128, EXPORTS, PackedCircuit, PackedPauli, SvError, load, pack_circuit,
                  pack_pauli, sv_adjoint, sv_alloc, sv_apply_circuit, sv_apply_gate,
                  sv_apply_pauli_sum, sv_copy, sv_download, sv_expval, sv_expval_async, sv_free,
+                 sv_fusion_plan,
                  sv_grad, sv_info, sv_init, sv_last_error, sv_launch_count, sv_norm, sv_profile_start,
                  sv_profile_stop, sv_set_stream,
                  sv_sync, sv_upload, sv_version, sv_wrap)

@@ -1,0 +1,233 @@
+// Gate-fusion planner (host, fp64).
+//
+// The paper applies a circuit gate by gate (Sec. 2, Eq. 1), one pass over
+// the 2^n-amplitude state per gate.  Here consecutive gates are grouped
+// into passes: a pass stages m amplitude-index bits S (the L lowest bits,
+// giving contiguous runs, plus high bits) so that each thread block loads
+// one 2^m-amplitude slice into shared memory, applies every gate of the
+// pass whose qubits lie in S, and writes the slice back: one HBM round
+// trip for many gates.  Gates on disjoint qubits commute, so any order
+// that keeps, for every qubit, the circuit order of the gates touching it
+// computes the same product.
+//
+// Planning steps:
+//   1. gates become FGates (1-qubit dense with controls, phase on an
+//      all-ones subspace, SWAP with controls, or "alone" for anything else
+//      or anything wider than fuse_k qubits); consecutive uncontrolled
+//      1-qubit gates on one qubit are multiplied into one 2x2 in fp64;
+//   2. a pass grows S greedily from the earliest remaining gate, taking
+//      every later gate whose qubits fit in S and that no skipped earlier
+//      gate overlaps; unused places in S are filled with the lowest free
+//      bits (longer contiguous runs);
+//   3. the pass's gates are list-scheduled into register groups of at
+//      most fuse_k qubits (a gate joins the open group when every earlier
+//      unscheduled gate it overlaps is scheduled and the union stays within
+//      fuse_k qubits).
+#include <algorithm>
+
+#include "sv_internal.cuh"
+
+namespace sv {
+namespace {
+
+int popc(uint64_t x) { return __builtin_popcountll(x); }
+
+bool is_zero(cd z) { return z.re == 0.0 && z.im == 0.0; }
+bool is_one(cd z) { return z.re == 1.0 && z.im == 0.0; }
+
+// a := b * a (2x2 complex, row-major)
+void mul2_left(const cd* b, cd* a) {
+  cd r[4];
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) {
+      double re = 0, im = 0;
+      for (int k = 0; k < 2; ++k) {
+        const cd x = b[i * 2 + k], y = a[k * 2 + j];
+        re += x.re * y.re - x.im * y.im;
+        im += x.re * y.im + x.im * y.re;
+      }
+      r[i * 2 + j] = {re, im};
+    }
+  for (int e = 0; e < 4; ++e) a[e] = r[e];
+}
+
+bool to_fgates(const sv_circuit* c, const double* theta, int kmax, std::vector<FGate>* out) {
+  const int n = c->n_qubits;
+  std::vector<int> last(64, -1);
+  HostMatrix G;
+  for (int i = 0; i < c->n_gates; ++i) {
+    const sv_gate& g = c->gates[i];
+    if (!gate_matrix(g, theta, c->mat_pool, &G)) {
+      set_error("gate %d: cannot build matrix", i);
+      return false;
+    }
+    FGate f;
+    f.orig = i;
+    f.origs.push_back(i);
+    int tp[SV_MAX_TARGETS];
+    uint64_t cm = 0;
+    for (int j = 0; j < g.n_tar; ++j) {
+      tp[j] = n - 1 - g.targets[j];
+      f.qmask |= uint64_t(1) << tp[j];
+    }
+    for (int j = 0; j < g.n_ctrl; ++j) cm |= uint64_t(1) << (n - 1 - g.controls[j]);
+    f.qmask |= cm;
+    const int k = g.n_tar, d = 1 << k;
+    bool diag = true, ones = true;
+    for (int r = 0; r < d; ++r)
+      for (int q = 0; q < d; ++q)
+        if (r != q && !is_zero(G.at(r, q))) diag = false;
+    for (int r = 0; r + 1 < d; ++r)
+      if (!is_one(G.at(r, r))) ones = false;
+    bool swap = k == 2;
+    if (swap) {
+      static const int perm[4] = {0, 2, 1, 3};
+      for (int r = 0; r < 4; ++r)
+        for (int q = 0; q < 4; ++q)
+          if (q == perm[r] ? !is_one(G.at(r, q)) : !is_zero(G.at(r, q))) swap = false;
+    }
+    if (diag && ones) {
+      f.type = FG_PHASE;
+      f.cmask = f.qmask;
+      f.m[0] = G.at(d - 1, d - 1);
+    } else if (swap) {
+      f.type = FG_SWAP;
+      f.a = tp[0];
+      f.b = tp[1];
+      f.cmask = cm;
+    } else if (k == 1) {
+      f.type = FG_1Q;
+      f.t = tp[0];
+      f.cmask = cm;
+      for (int e = 0; e < 4; ++e) f.m[e] = G.m[e];
+    } else {
+      f.type = FG_ALONE;
+    }
+    if (popc(f.qmask) > kmax) f.type = FG_ALONE;
+    if (f.type == FG_1Q && f.cmask == 0) {
+      const int p = last[f.t];
+      if (p >= 0 && (*out)[p].type == FG_1Q && (*out)[p].cmask == 0 && (*out)[p].t == f.t) {
+        mul2_left(f.m, (*out)[p].m);
+        (*out)[p].origs.push_back(i);
+        (*out)[p].orig = i;
+        continue;
+      }
+    }
+    out->push_back(f);
+    for (int b = 0; b < 64; ++b)
+      if ((f.qmask >> b) & 1) last[b] = (int)out->size() - 1;
+  }
+  return true;
+}
+
+int local_of(const std::vector<int>& S, int bit) {
+  return (int)(std::lower_bound(S.begin(), S.end(), bit) - S.begin());
+}
+
+}  // namespace
+
+FusionConfig fusion_config(int n, sv_dtype dt, int fuse_k) {
+  FusionConfig c;
+  c.fuse_k = fuse_k;
+  int m = std::min(n, dt == SV_C64 ? 13 : 12);
+  // keep at least 2^8 blocks for mid-size states, down to 2^10 amplitudes
+  if (n > 10) m = std::max(std::min(m, n - 8), std::min(n, 10));
+  c.m = m;
+  c.L = std::min(dt == SV_C64 ? 5 : 4, m);
+  if (c.m - c.L < fuse_k) c.L = std::max(1, c.m - fuse_k);
+  return c;
+}
+
+bool plan_fusion(const sv_circuit* c, const double* theta, const FusionConfig& cfg,
+                 std::vector<FusionItem>* out) {
+  const int n = c->n_qubits;
+  std::vector<FGate> F;
+  if (!to_fgates(c, theta, std::min(cfg.fuse_k, cfg.m), &F)) return false;
+  std::vector<char> done(F.size(), 0);
+  const uint64_t lowL = (cfg.L >= 64) ? ~uint64_t(0) : ((uint64_t(1) << cfg.L) - 1);
+  size_t first = 0;
+  out->clear();
+  while (true) {
+    while (first < F.size() && done[first]) ++first;
+    if (first == F.size()) break;
+    const FGate& f0 = F[first];
+    if (f0.type == FG_ALONE || popc(f0.qmask & ~lowL) > cfg.m - cfg.L) {
+      for (int o : f0.origs) {
+        FusionItem it;
+        it.gate = o;
+        out->push_back(it);
+      }
+      done[first] = 1;
+      continue;
+    }
+    // 2. grow S from the earliest remaining gate
+    uint64_t S = lowL, blocked = 0;
+    int nS = cfg.L;
+    std::vector<int> take;
+    for (size_t j = first; j < F.size(); ++j) {
+      if (done[j]) continue;
+      const FGate& f = F[j];
+      bool ok = f.type != FG_ALONE && !(f.qmask & blocked) && (int)take.size() < cfg.max_ops;
+      if (ok) {
+        const uint64_t need = f.qmask & ~S;
+        if (nS + popc(need) > cfg.m) {
+          ok = false;
+        } else {
+          S |= need;
+          nS += popc(need);
+        }
+      }
+      if (ok)
+        take.push_back((int)j);
+      else
+        blocked |= f.qmask;
+    }
+    for (int b = 0; b < n && nS < cfg.m; ++b)
+      if (!((S >> b) & 1)) {
+        S |= uint64_t(1) << b;
+        ++nS;
+      }
+    // 3. register groups by list scheduling
+    std::vector<int> pending = take;
+    std::vector<FusedGroup> groups;
+    std::vector<int> placed;
+    std::vector<FusionItem> none;
+    FusionItem item;
+    item.is_pass = true;
+    FusedPass& P = item.pass;
+    for (int b = 0; b < n; ++b)
+      if ((S >> b) & 1) P.S.push_back(b);
+    P.L = 0;
+    while (P.L < (int)P.S.size() && P.S[P.L] == P.L) ++P.L;
+    while (!pending.empty() && (int)groups.size() < cfg.max_groups) {
+      uint64_t gq = F[pending[0]].qmask, acc = 0;
+      std::vector<int> members, rest;
+      for (int j : pending) {
+        const FGate& f = F[j];
+        if (!(f.qmask & acc) && popc(gq | f.qmask) <= cfg.fuse_k) {
+          gq |= f.qmask;
+          members.push_back(j);
+        } else {
+          acc |= f.qmask;
+          rest.push_back(j);
+        }
+      }
+      FusedGroup grp;
+      for (int b = 0; b < n; ++b)
+        if ((gq >> b) & 1) grp.bits[grp.k++] = local_of(P.S, b);
+      for (int j : members) {
+        grp.ops.push_back((int)P.gates.size());
+        P.gates.push_back(F[j]);
+        placed.push_back(j);
+      }
+      groups.push_back(grp);
+      pending.swap(rest);
+    }
+    P.groups = groups;
+    for (int j : placed) done[j] = 1;
+    out->push_back(std::move(item));
+  }
+  return true;
+}
+
+}  // namespace sv

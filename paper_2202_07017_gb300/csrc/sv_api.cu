@@ -370,11 +370,26 @@ sv_status sv_apply_circuit(sv_state s, const sv_circuit* c, const double* theta,
     set_error("fuse_k = %d: expected 0 (unfused) or 2..5", fuse_k);
     return SV_ERR_INVALID;
   }
-  if (fuse_k > 0) {
-    set_error("fused circuit application is not built in this library version");
-    return SV_ERR_UNSUPPORTED;
-  }
   HostMatrix G;
+  if (fuse_k > 0) {
+    std::vector<FusionItem> plan;
+    if (!plan_fusion(c, theta, fusion_config(s->n, s->dt, fuse_k), &plan)) return SV_ERR_INVALID;
+    for (const FusionItem& it : plan) {
+      sv_status st;
+      if (it.is_pass) {
+        st = launch_fused_pass(s->data, s->dt, s->n, s->stream, it.pass);
+      } else {
+        const sv_gate& g = c->gates[it.gate];
+        gate_matrix(g, theta, c->mat_pool, &G);
+        int tp[SV_MAX_TARGETS], cp[SV_MAX_CONTROLS];
+        to_bits(s->n, g.targets, g.n_tar, tp);
+        to_bits(s->n, g.controls, g.n_ctrl, cp);
+        st = launch_gate(s->data, s->dt, s->n, s->stream, g.n_tar, tp, g.n_ctrl, cp, G);
+      }
+      if (st != SV_OK) return st;
+    }
+    return SV_OK;
+  }
   for (int i = 0; i < c->n_gates; ++i) {
     const sv_gate& g = c->gates[i];
     if (!gate_matrix(g, theta, c->mat_pool, &G)) {
@@ -386,6 +401,52 @@ sv_status sv_apply_circuit(sv_state s, const sv_circuit* c, const double* theta,
     to_bits(s->n, g.controls, g.n_ctrl, cp);
     sv_status st = launch_gate(s->data, s->dt, s->n, s->stream, g.n_tar, tp, g.n_ctrl, cp, G);
     if (st != SV_OK) return st;
+  }
+  return SV_OK;
+}
+
+sv_status sv_fusion_plan(const sv_circuit* c, const double* theta, sv_dtype dtype, int fuse_k,
+                         int32_t* order, int32_t* pass_of, int32_t* n_passes,
+                         int32_t* staged_bits) {
+  if (!c || !order || !pass_of || !n_passes || c->n_qubits < 1 ||
+      c->n_qubits > SV_MAX_QUBITS || fuse_k < 2 || fuse_k > 5 ||
+      (dtype != SV_C64 && dtype != SV_C128)) {
+    set_error("sv_fusion_plan: bad arguments");
+    return SV_ERR_INVALID;
+  }
+  sv_state_s probe;
+  probe.n = c->n_qubits;
+  probe.dt = dtype;
+  probe.data = (void*)1;
+  if (!valid_circuit(&probe, c, theta)) return SV_ERR_INVALID;
+  const FusionConfig cfg = fusion_config(c->n_qubits, dtype, fuse_k);
+  std::vector<FusionItem> plan;
+  if (!plan_fusion(c, theta, cfg, &plan)) return SV_ERR_INVALID;
+  int k = 0, p = 0;
+  for (const FusionItem& it : plan) {
+    if (it.is_pass) {
+      for (const FusedGroup& g : it.pass.groups)
+        for (int oi : g.ops)
+          for (int o : it.pass.gates[oi].origs) {
+            order[k] = o;
+            pass_of[k++] = p;
+          }
+      if (staged_bits) {
+        uint64_t m = 0;
+        for (int b : it.pass.S) m |= uint64_t(1) << b;
+        staged_bits[2 * p] = (int32_t)(m & 0xffffffffu);
+        staged_bits[2 * p + 1] = (int32_t)(m >> 32);
+      }
+      ++p;
+    } else {
+      order[k] = it.gate;
+      pass_of[k++] = -1;
+    }
+  }
+  *n_passes = p;
+  if (k != c->n_gates) {
+    set_error("sv_fusion_plan: internal error, %d of %d gates planned", k, c->n_gates);
+    return SV_ERR_INVALID;
   }
   return SV_OK;
 }

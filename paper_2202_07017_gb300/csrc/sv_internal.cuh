@@ -122,6 +122,54 @@ sv_status launch_apply_pauli(void* out, const void* in, sv_dtype dt, int n, cuda
 sv_status launch_finish(const double* src, int count, int slots, double* dst,
                         cudaStream_t st, bool add_to_dst);
 
+// ---- fusion (planner.cu, fused_kernels.cu) ------------------------------------
+// A gate as the fused kernels see it, in amplitude-index bit positions.
+enum { FG_1Q = 0, FG_PHASE = 1, FG_SWAP = 2, FG_ALONE = 3 };
+struct FGate {
+  int type = FG_ALONE;
+  uint64_t qmask = 0;  // every bit the gate touches (targets and controls)
+  uint64_t cmask = 0;  // control bits (FG_1Q, FG_SWAP); all bits for FG_PHASE
+  int t = 0, a = 0, b = 0;  // FG_1Q target bit; FG_SWAP bits
+  cd m[4] = {};        // FG_1Q: 2x2 row-major; FG_PHASE: m[0] = phase
+  int orig = -1;       // index of the (last merged) circuit gate
+  std::vector<int> origs;  // every circuit gate folded into this one
+};
+
+struct FusedGroup {
+  int k = 0;                 // staged-local bits of the group, ascending
+  int bits[5] = {0, 0, 0, 0, 0};
+  std::vector<int> ops;      // indices into the pass's gate list, in order
+};
+
+struct FusedPass {
+  std::vector<int> S;        // staged bit positions, ascending; S[0..L) = 0..L-1
+  int L = 0;
+  std::vector<FGate> gates;  // the pass's gates (bits are global)
+  std::vector<FusedGroup> groups;
+};
+
+struct FusionItem {
+  bool is_pass = false;
+  FusedPass pass;            // when is_pass
+  int gate = -1;             // circuit gate index to run unfused otherwise
+};
+
+struct FusionConfig {
+  int fuse_k = 4;            // max qubits per register group
+  int m = 13;                // staged bits per block
+  int L = 5;                 // low bits staged as contiguous runs
+  int max_ops = 200;         // gate capacity of one pass
+  int max_groups = 64;       // group capacity of one pass
+};
+
+FusionConfig fusion_config(int n, sv_dtype dt, int fuse_k);
+// Plans `c` into passes and unfused gates; returns false (with an error
+// set) if a matrix cannot be built.
+bool plan_fusion(const sv_circuit* c, const double* theta, const FusionConfig& cfg,
+                 std::vector<FusionItem>* out);
+sv_status launch_fused_pass(void* data, sv_dtype dt, int n, cudaStream_t st,
+                            const FusedPass& pass);
+
 // ---- adjoint (adjoint_kernels.cu) ----------------------------------------------
 // Un-applies U^dagger (given as matrix Gdag on bit tp, controls cp) on both
 // psi and lam; if pauli in {1,2,3} (X, Y, Z generator) first accumulates

@@ -53,7 +53,7 @@ EXPORTS = ("sv_alloc", "sv_wrap", "sv_free", "sv_set_stream", "sv_info", "sv_ini
            "sv_upload", "sv_download", "sv_copy", "sv_apply_gate", "sv_apply_circuit",
            "sv_norm", "sv_expval", "sv_expval_async", "sv_apply_pauli_sum", "sv_adjoint",
            "sv_grad", "sv_sync", "sv_last_error", "sv_launch_count", "sv_version",
-           "sv_profile_start", "sv_profile_stop")
+           "sv_profile_start", "sv_profile_stop", "sv_fusion_plan")
 
 _lib = None
 
@@ -95,6 +95,8 @@ def load(build: bool = True):
                     P(c_dbl), P(c_dbl)],
         "sv_sync": [c_vp],
         "sv_profile_start": [],
+        "sv_fusion_plan": [P(SvCircuit), P(c_dbl), ctypes.c_int, ctypes.c_int, P(c_i32), P(c_i32),
+                           P(c_i32), P(c_i32)],
         "sv_profile_stop": [ctypes.c_char_p, ctypes.c_size_t],
     }
     for name, args in sig.items():
@@ -248,6 +250,25 @@ def sv_apply_circuit(h: int, circuit, theta=None, fuse_k: int = 0) -> None:
     pc = pack_circuit(circuit)
     keep, tp = _theta_ptr(theta)
     _check(load().sv_apply_circuit(c_vp(h), ctypes.byref(pc.c), tp, int(fuse_k)))
+
+
+def sv_fusion_plan(circuit, theta=None, dtype: int = C64, fuse_k: int = 4):
+    """Dry run of the fusion planner: (order, pass_of, n_passes, staged masks)."""
+    pc = pack_circuit(circuit)
+    keep, tp = _theta_ptr(theta)
+    ng = max(1, pc.n_gates)
+    order = np.zeros(ng, np.int32)
+    pass_of = np.zeros(ng, np.int32)
+    staged = np.zeros(2 * ng, np.int32)
+    npass = c_i32()
+    P = ctypes.POINTER
+    _check(load().sv_fusion_plan(ctypes.byref(pc.c), tp, dtype, fuse_k,
+                                 order.ctypes.data_as(P(c_i32)), pass_of.ctypes.data_as(P(c_i32)),
+                                 ctypes.byref(npass), staged.ctypes.data_as(P(c_i32))))
+    p = npass.value
+    masks = [(int(staged[2 * i]) & 0xffffffff) | ((int(staged[2 * i + 1]) & 0xffffffff) << 32)
+             for i in range(p)]
+    return order[:pc.n_gates], pass_of[:pc.n_gates], p, masks
 
 
 def sv_norm(h: int) -> float:
