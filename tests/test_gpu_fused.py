@@ -56,8 +56,9 @@ def test_fused_layered_n33_inverse_and_unfused_prefix():
         st.apply_circuit(c, theta, 4)
         nrm = st.norm()
         st.apply_circuit(inv, None, 4)
-        idx = torch.tensor([0, 1, 2, 3, 1 << 20, (1 << n) - 1, 12345678901], dtype=torch.int64,
-                           device=st.tensor.device)
+        picks = [0, 1, 2, 3, 1 << 20, (1 << n) - 1, 1234567890]
+        assert all(0 <= i < (1 << n) for i in picks)  # checked on the host before indexing
+        idx = torch.tensor(picks, dtype=torch.int64, device=st.tensor.device)
         amps = st.tensor[idx].cpu().numpy()
         nrm2 = st.norm()
         # first two layers, fused vs unfused, on a random-looking start

@@ -149,7 +149,8 @@ def test_qft_n30_closed_form(dtype):
         rs = np.random.default_rng(5)
         idx = np.unique(np.concatenate([np.arange(4096), np.arange(N - 4096, N),
                                         rs.integers(0, N, 1 << 20)]))
-        got = st.tensor[torch.from_numpy(idx.astype(np.int64)).to(st.tensor.device)].cpu().numpy()
+        assert idx.min() >= 0 and idx.max() < N  # checked on the host before indexing
+        got =st.tensor[torch.from_numpy(idx.astype(np.int64)).to(st.tensor.device)].cpu().numpy()
     finally:
         st.close()
     ref = _qft_closed_form(n, x, idx)
