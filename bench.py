@@ -279,6 +279,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fused", action="store_true")
+    ap.add_argument("--fused-n", type=int, default=33,
+                    help="qubits of the fused layered-circuit measurement")
     ap.add_argument("--gate-table", choices=["c64", "c128"],
                     help="print per-kernel bandwidth by bit position and exit")
     args = ap.parse_args()
@@ -403,7 +405,7 @@ def main():
                    "path": "sv_upload (pinned host) + sv_apply_circuit + sv_download"}
             del host, hv
         adj = adjoint_ratio(torch)
-        fused = None if args.no_fused else fused_layered(torch)
+        fused = None if args.no_fused else fused_layered(torch, n=args.fused_n)
         cpu = None
         if not args.no_cpu:
             threads = os.cpu_count() or 1
