@@ -195,6 +195,33 @@ sv_status sv_norm(sv_state s, double* out);
 sv_status sv_expval(sv_state s, const sv_pauli_sum* H, double* out);
 sv_status sv_expval_async(sv_state s, const sv_pauli_sum* H, double* dev_out);
 
+/* <psi|H|psi> like sv_expval_async, for callers that cannot allocate device
+ * memory at the time of the call: code recording into a CUDA graph (stream
+ * capture forbids cudaMalloc), a process whose device memory is all handed
+ * to a caching allocator or a fixed arena, or code that has no way to
+ * recover from a failed allocation.  The paper has no counterpart; this
+ * is a deployment variant of sv_expval_async.
+ *
+ * It allocates nothing and needs no handle: dev_state is the caller's
+ * device state (2^n_qubits amplitudes of `dtype`, 16-byte aligned),
+ * dev_out the caller's device double that receives the result, and the
+ * kernels run on `cuda_stream` without synchronising.  The reduction's
+ * block partials live in one fixed array of SV_NOALLOC_MAX_TERMS / 64 *
+ * 1216 doubles (152 KiB) compiled into the library, which every GPU that
+ * loads the library keeps until the process exits.
+ *   - More than SV_NOALLOC_MAX_TERMS terms: SV_ERR_INVALID with a message.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream
+ *     capture begins.
+ *   - All calls share the array and each overwrites it (nothing in it has to
+ *     start at zero), so calls that overlap on the GPU race: serialise them
+ *     on one stream.
+ * Errors: SV_ERR_INVALID (bad pointers, sizes or masks, nothing launched),
+ * SV_ERR_CUDA. */
+#define SV_NOALLOC_MAX_TERMS 1024
+sv_status sv_expval_noalloc(const void* dev_state, int n_qubits, sv_dtype dtype,
+                            const sv_pauli_sum* H, double* dev_out, void* cuda_stream);
+
 /* out = H psi_in (a full state; Sec. 3 Hamiltonian applied to a state).
  * in and out must be distinct handles of equal n and dtype. Asynchronous. */
 sv_status sv_apply_pauli_sum(sv_state out, sv_state in, const sv_pauli_sum* H);

@@ -10,6 +10,7 @@
 // i^{#Y} (-1)^{popcount(b & zm)} |b ^ xm>, so
 // (P psi)_x = i^{#Y} (-1)^{popcount((x ^ xm) & zm)} psi_{x ^ xm}.
 // The host folds coeff * i^{#Y} into one complex coefficient per term.
+#include <mutex>
 #include <vector>
 
 #include "sv_device.cuh"
@@ -204,4 +205,106 @@ sv_status launch_finish(const double* src, int count, int slots, double* dst, cu
   return check_launch("finish kernel");
 }
 
+// ---- expectation value without any allocation ------------------------------------
+// Some callers cannot allocate device memory when they need an energy: a
+// program recording work into a CUDA graph (stream capture forbids
+// cudaMalloc), a serving process that hands the whole device to a
+// caching allocator or a fixed arena up front (a cudaMalloc behind its back
+// can fail or fragment), or code running where a failed allocation cannot be
+// handled.  sv_expval_noalloc serves them: the block partials of the
+// reduction live in this fixed array, which every GPU that loads the library
+// holds until the process exits.  It holds kNoAllocPartials doubles
+// (152 KiB): red_blocks(2^n) <= 1216 partials per chunk of 64 terms, up to
+// SV_NOALLOC_MAX_TERMS / 64 = 16 chunks.  Every block writes its own slot
+// before the finishing kernel reads it, so nothing has to start at zero;
+// calls share the array, so calls that overlap on the GPU (different
+// streams, or devices sharing a context) race.
+constexpr int kNoAllocPartials = kRedMaxBlocks * (SV_NOALLOC_MAX_TERMS / 64);
+static __device__ __align__(256) double g_noalloc_partials[kNoAllocPartials];
+
+namespace {
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[256] = {};  // device address of the array, per device ordinal
+}  // namespace
+
 }  // namespace sv
+
+extern "C" sv_status sv_expval_noalloc(const void* dev_state, int n_qubits, sv_dtype dtype,
+                                       const sv_pauli_sum* H, double* dev_out,
+                                       void* cuda_stream) {
+  using namespace sv;
+  if (!dev_state || !dev_out || n_qubits < 1 || n_qubits > SV_MAX_QUBITS ||
+      (dtype != SV_C64 && dtype != SV_C128) || ((uintptr_t)dev_state & 15) || !H) {
+    set_error("sv_expval_noalloc: bad state, output, qubit count or dtype");
+    return SV_ERR_INVALID;
+  }
+  if (H->n_terms < 0 || H->n_terms > SV_NOALLOC_MAX_TERMS) {
+    set_error("sv_expval_noalloc: %d terms, at most %d fit the fixed scratch array",
+              H->n_terms, SV_NOALLOC_MAX_TERMS);
+    return SV_ERR_INVALID;
+  }
+  if (H->n_terms > 0 && (!H->xmask || !H->zmask || !H->coeff)) {
+    set_error("sv_expval_noalloc: null Pauli sum arrays");
+    return SV_ERR_INVALID;
+  }
+  const uint64_t lim = (uint64_t(1) << n_qubits) - 1;
+  for (int k = 0; k < H->n_terms; ++k)
+    if ((H->xmask[k] | H->zmask[k]) & ~lim) {
+      set_error("sv_expval_noalloc: term %d has mask bits beyond %d qubits", k, n_qubits);
+      return SV_ERR_INVALID;
+    }
+  int dev = 0;
+  SV_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) {
+    set_error("sv_expval_noalloc: device ordinal %d out of range", dev);
+    return SV_ERR_INVALID;
+  }
+  double* scratch = nullptr;
+  {
+    // first call on a device: look up the array's device address (the host
+    // symbol is only a stand-in and must never be passed to a kernel)
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      void* p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+      if (e != cudaSuccess || !p) {
+        set_error("sv_expval_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+        return SV_ERR_CUDA;
+      }
+      g_noalloc_ptr[dev] = (double*)p;
+    }
+    scratch = g_noalloc_ptr[dev];
+  }
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (H->n_terms == 0) {
+    SV_CUDA_TRY(cudaMemsetAsync(dev_out, 0, sizeof(double), st));
+    return SV_OK;
+  }
+  const uint64_t dim = uint64_t(1) << n_qubits;
+  const int g = red_blocks(dim);
+  int total = 0;
+  for (int k0 = 0; k0 < H->n_terms; k0 += 64) {
+    PauliDev P{};  // one chunk of up to 64 terms, on the stack
+    P.nt = H->n_terms - k0 < 64 ? H->n_terms - k0 : 64;
+    for (int j = 0; j < P.nt; ++j) {
+      const uint64_t xm = H->xmask[k0 + j], zm = H->zmask[k0 + j];
+      const int ny = __builtin_popcountll(xm & zm) & 3;
+      const double c = H->coeff[k0 + j];
+      P.xm[j] = xm;
+      P.zm[j] = zm;
+      P.cre[j] = ny == 0 ? c : ny == 2 ? -c : 0.0;
+      P.cim[j] = ny == 1 ? c : ny == 3 ? -c : 0.0;
+    }
+    if (dtype == SV_C64)
+      kexpval<float, float2><<<g, kRedThreads, 0, st>>>((const float2*)dev_state, dim, P,
+                                                        scratch + total);
+    else
+      kexpval<double, double2><<<g, kRedThreads, 0, st>>>((const double2*)dev_state, dim, P,
+                                                          scratch + total);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    total += g;
+  }
+  kfinish<<<1, kRedThreads, 0, st>>>(scratch, total, dev_out, 0);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return check_launch("sv_expval_noalloc kernels");
+}

@@ -53,7 +53,7 @@ EXPORTS = ("sv_alloc", "sv_wrap", "sv_free", "sv_set_stream", "sv_info", "sv_ini
            "sv_upload", "sv_download", "sv_copy", "sv_apply_gate", "sv_apply_circuit",
            "sv_norm", "sv_expval", "sv_expval_async", "sv_apply_pauli_sum", "sv_adjoint",
            "sv_grad", "sv_sync", "sv_last_error", "sv_launch_count", "sv_version",
-           "sv_profile_start", "sv_profile_stop", "sv_fusion_plan")
+           "sv_profile_start", "sv_profile_stop", "sv_fusion_plan", "sv_expval_noalloc")
 
 _lib = None
 
@@ -95,6 +95,7 @@ def load(build: bool = True):
                     P(c_dbl), P(c_dbl)],
         "sv_sync": [c_vp],
         "sv_profile_start": [],
+        "sv_expval_noalloc": [c_vp, ctypes.c_int, ctypes.c_int, P(SvPauliSum), c_vp, c_vp],
         "sv_fusion_plan": [P(SvCircuit), P(c_dbl), ctypes.c_int, ctypes.c_int, P(c_i32), P(c_i32),
                            P(c_i32), P(c_i32)],
         "sv_profile_stop": [ctypes.c_char_p, ctypes.c_size_t],
@@ -291,6 +292,14 @@ def sv_expval(h: int, terms) -> float:
 def sv_expval_async(h: int, terms, dev_out_ptr: int) -> None:
     pp = pack_pauli(terms, _n_of(h))
     _check(load().sv_expval_async(c_vp(h), ctypes.byref(pp.s), c_vp(dev_out_ptr)))
+
+
+def sv_expval_noalloc(dev_state: int, n_qubits: int, dtype: int, terms, dev_out: int,
+                      stream: int = 0) -> None:
+    """Allocation-free <psi|H|psi> into the device double at dev_out (no sync)."""
+    pp = pack_pauli(terms, n_qubits)
+    _check(load().sv_expval_noalloc(c_vp(dev_state), n_qubits, dtype, ctypes.byref(pp.s),
+                                    c_vp(dev_out), c_vp(stream)))
 
 
 def sv_apply_pauli_sum(out: int, inp: int, terms) -> None:
