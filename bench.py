@@ -231,6 +231,47 @@ def fused_layered(torch, n=33, depth=40, k=4):
             "unfused_full_estimate_s": t2_u * len(c.gates) / len(layer2.gates)}
 
 
+def batch_solves(torch, reps=5):
+    """4096 parameter sets of the n = 14, L = 10 hardware-efficient ansatz
+    plus 1024 mixed ansatz circuits (n 8..16, depth 5..15), TFIM energies and
+    adjoint gradients, complex64: one persistent launch per step, replayed
+    from a CUDA graph, tile chosen by the autotuner."""
+    import workloads as W
+    from paper_2202_07017_gb300 import Batch
+    hea14, _ = W.hea(14, 10, 1003)
+    mixed = W.mixed_batch(1024, 1003)
+    circuits = [hea14] + [m[0] for m in mixed]
+    hams = [W.tfim(14)] + [m[2] for m in mixed]
+    items = [0] * 4096 + list(range(1, 1025))
+    theta = np.concatenate([W.hea_theta(14, 10, 1003 + i) for i in range(4096)]
+                           + [m[1] for m in mixed])
+    t0 = time.perf_counter()
+    b = Batch(circuits, hams, items, tune=True)
+    t_create = time.perf_counter() - t0
+    th = torch.tensor(theta, dtype=torch.float64, device="cuda")
+    e = torch.empty(len(items), dtype=torch.float64, device="cuda")
+    g = torch.empty(len(theta), dtype=torch.float64, device="cuda")
+    st = torch.cuda.current_stream()
+    for _ in range(3):
+        b.run(th, e, g, graph=True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    ev[0].record(st)
+    for _ in range(reps):
+        b.run(th, e, g, graph=True)
+    ev[1].record(st)
+    torch.cuda.synchronize()
+    secs = ev[0].elapsed_time(ev[1]) / 1e3 / reps
+    out = {"workload": "4096 x HEA n=14 L=10 + 1024 mixed HEA (n 8..16, L 5..15), TFIM, "
+                       "energy + adjoint gradient, complex64, one persistent launch (CUDA graph)",
+           "items": len(items), "ms_per_launch": 1e3 * secs, "items_per_s": len(items) / secs,
+           "gradients_per_s": len(theta) / secs,
+           "tile": {"k": b.k, "threads": b.threads, "blocks": b.blocks},
+           "create_and_tune_s": t_create}
+    b.close()
+    return out
+
+
 def gate_table(n, dtype, reps=5):
     """Per-kernel bandwidth for single gates on every kind of bit position:
     H on bit p, controlled-U1 on bits (a, b), SWAP on (a, b).  Algorithmic
@@ -279,6 +320,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fused", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--fused-n", type=int, default=33,
                     help="qubits of the fused layered-circuit measurement")
     ap.add_argument("--gate-table", choices=["c64", "c128"],
@@ -406,6 +448,7 @@ def main():
             del host, hv
         adj = adjoint_ratio(torch)
         fused = None if args.no_fused else fused_layered(torch, n=args.fused_n)
+        batch = None if args.no_batch else batch_solves(torch)
         cpu = None
         if not args.no_cpu:
             threads = os.cpu_count() or 1
@@ -438,6 +481,7 @@ def main():
             "clocks": clk,
             "adjoint": adj,
             "fused": fused,
+            "batch": batch,
         }
     sv_free(h)
     if out is not None:

@@ -251,6 +251,60 @@ sv_status sv_grad(sv_state s, const sv_circuit* c, const double* theta,
                   const sv_pauli_sum* H, const int32_t* checkpoint_gates,
                   int n_checkpoints, double* energy, double* grad);
 
+/* ---- batched energies and gradients (one persistent launch) ------------ */
+
+/* Many small variational circuits at once (Sec. 3: variational layers and
+ * VQE; Sec. 2 gradients): item i runs circuits[item_circuit[i]] from
+ * |0...0> in complex64, evaluates E_i = <psi|H|psi> with
+ * hamiltonians[item_circuit[i]] and the adjoint gradient dE_i/dtheta.  All
+ * items run in one persistent kernel whose thread blocks pull items from an
+ * atomic queue (longest first); each block keeps its item's two states in a
+ * workspace slot that stays in L1/L2.  Energies and gradients accumulate in
+ * fp64 in a fixed order.
+ *
+ * Limits: <= SV_BATCH_MAX_QUBITS qubits, <= 480 gates and <= 256
+ * parameters per circuit, <= 64 Pauli terms per Hamiltonian; gates are the
+ * 1-qubit kinds H X Y Z RX RY RZ U1 with up to 3 controls (CZ = Z with a
+ * control), parameters on RX/RY/RZ only.  Violations: SV_ERR_INVALID.
+ *
+ * Parameters are packed per item in item order: item i's n_params angles
+ * start at the sum of the parameter counts of items 0..i-1 (sv_batch_info
+ * gives the total).  Gradients use the same packing.
+ *
+ * sv_batch_create uploads the descriptors and allocates the workspace; with
+ * tune != 0 its autotuner times every (register-group width k in {2,3,4},
+ * threads per block in {128,256,512}, blocks per SM in {1,2,4}) on the batch
+ * and keeps the fastest (this synchronises the device).  The handle is
+ * library-owned; sv_batch_free releases it. */
+#define SV_BATCH_MAX_QUBITS 18
+typedef struct sv_batch_s* sv_batch;
+
+sv_status sv_batch_create(const sv_circuit* circuits, const sv_pauli_sum* hamiltonians,
+                          int n_circuits, const int32_t* item_circuit, int n_items, int tune,
+                          sv_batch* out);
+
+/* Chosen tile (k, threads per block, blocks) and total parameter count. */
+sv_status sv_batch_info(sv_batch b, int* k, int* threads, int* blocks, int* total_params);
+
+/* One persistent launch (a queue reset plus the kernel) on cuda_stream;
+ * dev_theta, dev_energy (n_items) and dev_grad (total_params) are device
+ * arrays.  Asynchronous; usable under stream capture. */
+sv_status sv_batch_run(sv_batch b, const double* dev_theta, double* dev_energy, double* dev_grad,
+                       void* cuda_stream);
+
+/* The same launch through a CUDA graph the handle captures on first use
+ * for these pointers and this stream and replays afterwards. */
+sv_status sv_batch_run_graph(sv_batch b, const double* dev_theta, double* dev_energy,
+                             double* dev_grad, void* cuda_stream);
+
+/* One-shot host convenience: create (no tuning), copy theta from the host,
+ * run, copy energies and gradients back to the host, free.  Synchronises. */
+sv_status sv_batch_grad(const sv_circuit* circuits, const sv_pauli_sum* hamiltonians,
+                        int n_circuits, const int32_t* item_circuit, int n_items,
+                        const double* theta, void* cuda_stream, double* energies, double* grads);
+
+sv_status sv_batch_free(sv_batch b);
+
 /* ---- status ------------------------------------------------------------ */
 
 /* Synchronise the stream and surface any asynchronous error. */

@@ -12,7 +12,8 @@ from __future__ import annotations
 
 import numpy as np
 
-from .sv import (C64, C128, EXPORTS, PackedCircuit, PackedPauli, SvError, load, pack_circuit,
+from .sv import (C64, C128, EXPORTS, PackedBatch, sv_batch_create, sv_batch_free, sv_batch_grad,
+                 sv_batch_info, sv_batch_run, sv_batch_run_graph, PackedCircuit, PackedPauli, SvError, load, pack_circuit,
                  pack_pauli, sv_adjoint, sv_alloc, sv_apply_circuit, sv_apply_gate,
                  sv_apply_pauli_sum, sv_copy, sv_download, sv_expval, sv_expval_async, sv_free,
                  sv_fusion_plan,
@@ -20,7 +21,7 @@ from .sv import (C64, C128, EXPORTS, PackedCircuit, PackedPauli, SvError, load, 
                  sv_profile_stop, sv_set_stream,
                  sv_sync, sv_upload, sv_version, sv_wrap)
 
-__all__ = ["State", "Energy", "energy", "C64", "C128", "SvError", "pack_circuit", "pack_pauli",
+__all__ = ["State", "Batch", "Energy", "energy", "C64", "C128", "SvError", "pack_circuit", "pack_pauli",
            "load"] + list(EXPORTS)
 
 
@@ -98,6 +99,40 @@ class State:
 
     def sync(self):
         sv_sync(self.h)
+
+
+class Batch:
+    """Energies and adjoint gradients of many small circuits in one persistent
+    launch (complex64, fp64 accumulation).  theta / energy / grad are torch
+    CUDA float64 tensors; parameters are packed per item in item order."""
+
+    def __init__(self, circuits, hamiltonians, item_circuit, tune: bool = True):
+        self.h, self.packed = sv_batch_create(circuits, hamiltonians, item_circuit, tune)
+        self.k, self.threads, self.blocks, self.total_params = sv_batch_info(self.h)
+        self.n_items = len(self.packed.items)
+
+    def run(self, theta, energy=None, grad=None, graph: bool = False, stream=None):
+        import torch
+        dev = theta.device
+        if energy is None:
+            energy = torch.empty(self.n_items, dtype=torch.float64, device=dev)
+        if grad is None:
+            grad = torch.empty(max(1, self.total_params), dtype=torch.float64, device=dev)
+        st = (stream or torch.cuda.current_stream(dev)).cuda_stream
+        fn = sv_batch_run_graph if graph else sv_batch_run
+        fn(self.h, theta.data_ptr(), energy.data_ptr(), grad.data_ptr(), st)
+        return energy, grad
+
+    def close(self):
+        if getattr(self, "h", None):
+            sv_batch_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _energy_fn():

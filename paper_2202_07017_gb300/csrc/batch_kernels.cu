@@ -1,0 +1,828 @@
+// Batched energies and adjoint gradients in one persistent launch.
+//
+// Many small variational circuits (Sec. 3: variational layers, VQE) are
+// evaluated together: thread blocks pull items (a circuit, its parameters and
+// its Pauli-sum Hamiltonian) from an atomic queue and run each item to the
+// end inside the block - the forward pass from |0...0>, lambda = H psi and
+// E = <psi|lambda>, then the adjoint reverse sweep (dE/dtheta_j =
+// Im<lambda|P_j|psi> before U_j is un-applied on both states).  Each block
+// owns one workspace slot of two states (2 x 2^nmax complex64), small enough
+// to stay in L1/L2 while the block works on it.
+//
+// Gates are applied in register groups: the host list-schedules each
+// circuit's gates into groups of at most k qubits; a thread pulls the 2^k
+// amplitudes of a sub-block into registers, applies the group's gates in
+// order (backward: their adjoints in reverse order) and writes them back, so
+// the block synchronises once per group instead of once per gate.
+//
+// Precision: states and gate arithmetic in fp32; gate matrices from fp64
+// sincos; the energy and every gradient accumulate in fp64 (per-warp slots
+// summed in a fixed order, so results repeat bit for bit).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "sv_device.cuh"
+
+namespace sv {
+namespace {
+
+constexpr int kBMaxGates = 480;    // gates of one circuit (static smem stays < 48 KB)
+constexpr int kBMaxParams = 256;   // parameters of one circuit
+constexpr int kBMaxWarps = 16;     // 512 threads
+constexpr int kBMaxTerms = 64;     // Pauli terms of one Hamiltonian
+
+struct BCirc {
+  int n, ngates, gate0, ngroups, group0, nparams, nterms, term0;
+};
+struct BGateDesc {
+  int kind;   // SV_GATE_* (1-qubit kinds)
+  int param;  // -1: fixed angle
+  double angle;
+};
+struct BGroup {
+  uint8_t k, bits[5];
+  int32_t op0, op1;
+};
+struct BOp {
+  uint8_t b0;     // group-local target index
+  uint8_t cm;     // group-local control mask
+  uint8_t pauli;  // generator for gradients: 0 none, 1 X, 2 Y, 3 Z
+  uint8_t pad;
+  int16_t param;  // parameter index or -1
+  int16_t gi;     // gate index within the circuit (matrix table slot)
+};
+struct BTerm {
+  uint64_t xm, zm;
+  double cre, cim;  // coefficient times i^{#Y}
+};
+
+struct BatchArgs {
+  const BCirc* circs;
+  const BGateDesc* gates;
+  const BGroup* groups;
+  const BOp* ops;
+  const BTerm* terms;
+  const int* order;      // items, longest first
+  const int* item_circ;  // circuit of each item
+  const int* theta_off;  // parameter offset of each item
+  int n_items, nmax;
+  const double* theta;
+  double* energy;
+  double* grad;
+  float2* work;          // gridDim.x slots of 2 x 2^nmax amplitudes
+  int* queue;
+};
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__host__ __device__ constexpr int lowbit_b(int r) { return (r & 1) ? 0 : 1 + lowbit_b(r >> 1); }
+
+// (a, b) <- M (a, b) for every register pair on group bit B with controls cm.
+template <int K, int B>
+__device__ __forceinline__ void pair_apply(const float* M, int cm, float (&re)[1 << K],
+                                           float (&im)[1 << K]) {
+  const float g0r = M[0], g0i = M[1], g1r = M[2], g1i = M[3];
+  const float g2r = M[4], g2i = M[5], g3r = M[6], g3i = M[7];
+#pragma unroll
+  for (int r = 0; r < (1 << K); ++r) {
+    if (r & (1 << B)) continue;
+    const int r1 = r | (1 << B);
+    if ((r & cm) != cm) continue;
+    const float ar = re[r], ai = im[r], br = re[r1], bi = im[r1];
+    re[r] = g0r * ar - g0i * ai + g1r * br - g1i * bi;
+    im[r] = g0r * ai + g0i * ar + g1r * bi + g1i * br;
+    re[r1] = g2r * ar - g2i * ai + g3r * br - g3i * bi;
+    im[r1] = g2r * ai + g2i * ar + g3r * bi + g3i * br;
+  }
+}
+
+// the adjoint of M applied to the pairs
+template <int K, int B>
+__device__ __forceinline__ void pair_apply_dag(const float* M, int cm, float (&re)[1 << K],
+                                               float (&im)[1 << K]) {
+  // M^dagger = [[conj g0, conj g2], [conj g1, conj g3]]
+  const float h[8] = {M[0], -M[1], M[4], -M[5], M[2], -M[3], M[6], -M[7]};
+  pair_apply<K, B>(h, cm, re, im);
+}
+
+// sum over the pairs of Im( conj(l0) (P p)_0 + conj(l1) (P p)_1 )
+template <int K, int B>
+__device__ __forceinline__ float pair_grad(int pauli, int cm, const float (&pr)[1 << K],
+                                           const float (&pi)[1 << K], const float (&lr)[1 << K],
+                                           const float (&li)[1 << K]) {
+  float acc = 0.f;
+#pragma unroll
+  for (int r = 0; r < (1 << K); ++r) {
+    if (r & (1 << B)) continue;
+    const int r1 = r | (1 << B);
+    if ((r & cm) != cm) continue;
+    const float p0r = pr[r], p0i = pi[r], p1r = pr[r1], p1i = pi[r1];
+    const float l0r = lr[r], l0i = li[r], l1r = lr[r1], l1i = li[r1];
+    if (pauli == 1)
+      acc += (l0r * p1i - l0i * p1r) + (l1r * p0i - l1i * p0r);
+    else if (pauli == 2)
+      acc += -(l0r * p1r + l0i * p1i) + (l1r * p0r + l1i * p0i);
+    else
+      acc += (l0r * p0i - l0i * p0r) - (l1r * p1i - l1i * p1r);
+  }
+  return acc;
+}
+
+#define SV_BIT_SWITCH(B, CALL) \
+  switch (B) {                 \
+    case 0: CALL(0); break;    \
+    case 1: CALL(1); break;    \
+    case 2: CALL(2); break;    \
+    default: CALL(3); break;   \
+  }
+
+template <int K>
+__device__ void group_offsets(const BGroup& g, int (&off)[1 << K], int (&lm)[K]) {
+  off[0] = 0;
+#pragma unroll
+  for (int r = 1; r < (1 << K); ++r) off[r] = off[r & (r - 1)] | (1 << g.bits[lowbit_b(r)]);
+#pragma unroll
+  for (int i = 0; i < K; ++i) lm[i] = (1 << g.bits[i]) - 1;
+}
+
+template <int K>
+__device__ __forceinline__ int sub_base(int s, const int (&lm)[K], int kk) {
+  int b = s;
+#pragma unroll
+  for (int i = 0; i < K; ++i)
+    if (i < kk) b = ((b & ~lm[i]) << 1) | (b & lm[i]);
+  return b;
+}
+
+// forward: psi <- group ops in order
+template <int K>
+__device__ void group_fwd(float2* psi, int n, const BGroup& g, const BOp* ops, const float* mats) {
+  int off[1 << K], lm[K];
+  group_offsets<K>(g, off, lm);
+  const int kk = g.k;
+  const int nsub = 1 << (n - kk);
+  const int width = 1 << kk;
+  for (int s = threadIdx.x; s < nsub; s += blockDim.x) {
+    const int b = sub_base<K>(s, lm, kk);
+    float re[1 << K], im[1 << K];
+#pragma unroll
+    for (int r = 0; r < (1 << K); ++r)
+      if (r < width) {
+        const float2 v = psi[b | off[r]];
+        re[r] = v.x;
+        im[r] = v.y;
+      }
+    for (int o = g.op0; o < g.op1; ++o) {
+      const BOp op = ops[o];
+      const float* M = mats + 8 * op.gi;
+#define SV_FWD(BB) \
+  if constexpr (BB < K) pair_apply<K, BB>(M, op.cm, re, im)
+      SV_BIT_SWITCH(op.b0, SV_FWD)
+#undef SV_FWD
+    }
+#pragma unroll
+    for (int r = 0; r < (1 << K); ++r)
+      if (r < width) psi[b | off[r]] = make_float2(re[r], im[r]);
+  }
+}
+
+// backward: for ops in reverse, gradient contribution then un-apply on both
+template <int K>
+__device__ void group_bwd(float2* psi, float2* lam, int n, const BGroup& g, const BOp* ops,
+                          const float* mats, double* wpart) {
+  int off[1 << K], lm[K];
+  group_offsets<K>(g, off, lm);
+  const int kk = g.k;
+  const int nsub = 1 << (n - kk);
+  const int width = 1 << kk;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // every lane of a warp runs the same number of iterations (warp sums)
+  const int iters = (nsub + blockDim.x - 1) / blockDim.x;
+  for (int it = 0; it < iters; ++it) {
+    const int s = threadIdx.x + it * blockDim.x;
+    const bool live = s < nsub;
+    const int b = live ? sub_base<K>(s, lm, kk) : 0;
+    float pr[1 << K], pi[1 << K], lr[1 << K], li[1 << K];
+#pragma unroll
+    for (int r = 0; r < (1 << K); ++r) {
+      pr[r] = pi[r] = lr[r] = li[r] = 0.f;
+      if (live && r < width) {
+        const float2 v = psi[b | off[r]], w = lam[b | off[r]];
+        pr[r] = v.x;
+        pi[r] = v.y;
+        lr[r] = w.x;
+        li[r] = w.y;
+      }
+    }
+    for (int o = g.op1 - 1; o >= g.op0; --o) {
+      const BOp op = ops[o];
+      const float* M = mats + 8 * op.gi;
+      if (op.pauli) {
+        float c = 0.f;
+#define SV_GRAD(BB) \
+  if constexpr (BB < K) c = pair_grad<K, BB>(op.pauli, op.cm, pr, pi, lr, li)
+        SV_BIT_SWITCH(op.b0, SV_GRAD)
+#undef SV_GRAD
+        c = warp_sum_f(c);
+        if (lane == 0) wpart[warp * kBMaxParams + op.param] += (double)c;
+      }
+#define SV_BWD(BB)                                  \
+  if constexpr (BB < K) {                           \
+    pair_apply_dag<K, BB>(M, op.cm, pr, pi);        \
+    pair_apply_dag<K, BB>(M, op.cm, lr, li);        \
+  }
+      SV_BIT_SWITCH(op.b0, SV_BWD)
+#undef SV_BWD
+    }
+    if (live) {
+#pragma unroll
+      for (int r = 0; r < (1 << K); ++r)
+        if (r < width) {
+          psi[b | off[r]] = make_float2(pr[r], pi[r]);
+          lam[b | off[r]] = make_float2(lr[r], li[r]);
+        }
+    }
+  }
+}
+
+template <int K>
+__global__ void __launch_bounds__(512) kbatch(const BatchArgs A) {
+  __shared__ float mats[8 * kBMaxGates];
+  __shared__ double wpart[kBMaxWarps * kBMaxParams];
+  __shared__ double red[kBMaxWarps];
+  __shared__ int s_item;
+  const int nwarps = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float2* psi = A.work + (size_t)blockIdx.x * (size_t(2) << A.nmax);
+  float2* lam = psi + (size_t(1) << A.nmax);
+  while (true) {
+    if (threadIdx.x == 0) s_item = atomicAdd(A.queue, 1);
+    __syncthreads();
+    const int slot = s_item;
+    if (slot >= A.n_items) break;
+    const int item = A.order[slot];
+    const BCirc C = A.circs[A.item_circ[item]];
+    const double* th = A.theta + A.theta_off[item];
+    const int dim = 1 << C.n;
+    // gate matrices (fp64 trigonometry, rounded once), psi = |0...0>, zero partials
+    for (int gi = threadIdx.x; gi < C.ngates; gi += blockDim.x) {
+      const BGateDesc d = A.gates[C.gate0 + gi];
+      const double a = d.param >= 0 ? th[d.param] : d.angle;
+      double s, c;
+      sincos(0.5 * a, &s, &c);
+      double m[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      const double r2 = 0.70710678118654752440;
+      switch (d.kind) {
+        case SV_GATE_H: m[0] = r2; m[2] = r2; m[4] = r2; m[6] = -r2; break;
+        case SV_GATE_X: m[2] = 1; m[4] = 1; break;
+        case SV_GATE_Y: m[3] = -1; m[5] = 1; break;
+        case SV_GATE_Z: m[0] = 1; m[6] = -1; break;
+        case SV_GATE_RX: m[0] = c; m[3] = -s; m[5] = -s; m[6] = c; break;
+        case SV_GATE_RY: m[0] = c; m[2] = -s; m[4] = s; m[6] = c; break;
+        case SV_GATE_RZ: m[0] = c; m[1] = -s; m[6] = c; m[7] = s; break;
+        default: {  // U1: diag(1, e^{ia})
+          double sa, ca;
+          sincos(a, &sa, &ca);
+          m[0] = 1; m[6] = ca; m[7] = sa;
+        }
+      }
+      for (int e = 0; e < 8; ++e) mats[8 * gi + e] = (float)m[e];
+    }
+    for (int x = threadIdx.x; x < dim; x += blockDim.x) psi[x] = make_float2(x == 0 ? 1.f : 0.f, 0.f);
+    for (int i = threadIdx.x; i < nwarps * kBMaxParams; i += blockDim.x) wpart[i] = 0.0;
+    __syncthreads();
+    // forward
+    for (int gg = 0; gg < C.ngroups; ++gg) {
+      group_fwd<K>(psi, C.n, A.groups[C.group0 + gg], A.ops, mats);
+      __syncthreads();
+    }
+    // lambda = H psi, E = Re <psi|lambda>
+    double e = 0.0;
+    for (int x = threadIdx.x; x < dim; x += blockDim.x) {
+      float orr = 0.f, oi = 0.f;
+      for (int t = 0; t < C.nterms; ++t) {
+        const BTerm T = A.terms[C.term0 + t];
+        const float2 b = psi[x ^ (int)T.xm];
+        const float cr = (float)T.cre, ci = (float)T.cim;
+        const float sr = cr * b.x - ci * b.y, si = cr * b.y + ci * b.x;
+        if (__popcll(((uint64_t)x ^ T.xm) & T.zm) & 1) {
+          orr -= sr;
+          oi -= si;
+        } else {
+          orr += sr;
+          oi += si;
+        }
+      }
+      lam[x] = make_float2(orr, oi);
+      const float2 a = psi[x];
+      e += (double)(a.x * orr + a.y * oi);
+    }
+    e = warp_sum_d(e);
+    if (lane == 0) red[warp] = e;
+    __syncthreads();
+    // reverse sweep
+    for (int gg = C.ngroups - 1; gg >= 0; --gg) {
+      group_bwd<K>(psi, lam, C.n, A.groups[C.group0 + gg], A.ops, mats, wpart);
+      __syncthreads();
+    }
+    const int toff = A.theta_off[item];
+    for (int p = threadIdx.x; p < C.nparams; p += blockDim.x) {
+      double g = 0.0;
+      for (int w = 0; w < nwarps; ++w) g += wpart[w * kBMaxParams + p];
+      A.grad[toff + p] = g;
+    }
+    if (threadIdx.x == 0) {
+      double E = 0.0;
+      for (int w = 0; w < nwarps; ++w) E += red[w];
+      A.energy[item] = E;
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+}  // namespace sv
+
+// ---- host side: descriptors, autotuner, launches ---------------------------------
+struct sv_batch_s {
+  int n_items = 0, nmax = 0, total_params = 0;
+  int k = 4, threads = 256, blocks = 0;  // chosen tile
+  // device buffers
+  sv::BCirc* circs = nullptr;
+  sv::BGateDesc* gates = nullptr;
+  sv::BGroup* groups = nullptr;
+  sv::BOp* ops = nullptr;
+  sv::BTerm* terms = nullptr;
+  int* order = nullptr;
+  int* item_circ = nullptr;
+  int* theta_off = nullptr;
+  int* queue = nullptr;
+  float2* work = nullptr;
+  size_t work_slots = 0;
+  std::vector<int> h_theta_off;
+  // captured graph
+  cudaGraphExec_t gexec = nullptr;
+  const void* g_key[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+
+namespace sv {
+namespace {
+
+struct HostPlan {
+  std::vector<BCirc> circs;
+  std::vector<BGateDesc> gates;
+  std::vector<BGroup> groups;
+  std::vector<BOp> ops;
+  std::vector<BTerm> terms;
+};
+
+int popc64(uint64_t x) { return __builtin_popcountll(x); }
+
+// List-schedule one circuit's gates (1-qubit kinds with controls) into groups
+// of at most k qubits, as the fused pass planner does, without merging gates
+// (every parameter keeps its own gate for the gradient).
+bool plan_circuit(const sv_circuit* c, const sv_pauli_sum* H, int k, HostPlan* P) {
+  const int n = c->n_qubits;
+  BCirc C{};
+  C.n = n;
+  C.ngates = c->n_gates;
+  C.gate0 = (int)P->gates.size();
+  C.group0 = (int)P->groups.size();
+  C.nparams = c->n_params;
+  C.nterms = H->n_terms;
+  C.term0 = (int)P->terms.size();
+  std::vector<uint64_t> qm(c->n_gates);
+  for (int i = 0; i < c->n_gates; ++i) {
+    const sv_gate& g = c->gates[i];
+    BGateDesc d{g.kind, g.param, g.angle};
+    P->gates.push_back(d);
+    uint64_t m = uint64_t(1) << (n - 1 - g.targets[0]);
+    for (int j = 0; j < g.n_ctrl; ++j) m |= uint64_t(1) << (n - 1 - g.controls[j]);
+    qm[i] = m;
+  }
+  std::vector<int> pending(c->n_gates);
+  for (int i = 0; i < c->n_gates; ++i) pending[i] = i;
+  while (!pending.empty()) {
+    uint64_t gq = qm[pending[0]], acc = 0;
+    std::vector<int> members, rest;
+    for (int j : pending) {
+      if (!(qm[j] & acc) && popc64(gq | qm[j]) <= k) {
+        gq |= qm[j];
+        members.push_back(j);
+      } else {
+        acc |= qm[j];
+        rest.push_back(j);
+      }
+    }
+    BGroup G{};
+    int bits[64], nb = 0;
+    for (int b = 0; b < n; ++b)
+      if ((gq >> b) & 1) bits[nb++] = b;
+    // pad narrow groups with free bits so every group has exactly min(k, n) bits
+    for (int b = 0; b < n && nb < std::min(k, n); ++b)
+      if (!((gq >> b) & 1)) {
+        gq |= uint64_t(1) << b;
+        bits[nb++] = b;
+      }
+    std::sort(bits, bits + nb);
+    G.k = (uint8_t)nb;
+    for (int i = 0; i < nb; ++i) G.bits[i] = (uint8_t)bits[i];
+    G.op0 = (int32_t)P->ops.size();
+    for (int j : members) {
+      const sv_gate& g = c->gates[j];
+      auto local = [&](int bit) {
+        for (int i = 0; i < nb; ++i)
+          if (bits[i] == bit) return i;
+        return 0;
+      };
+      BOp op{};
+      op.b0 = (uint8_t)local(n - 1 - g.targets[0]);
+      for (int t = 0; t < g.n_ctrl; ++t) op.cm |= (uint8_t)(1 << local(n - 1 - g.controls[t]));
+      op.pauli = g.param >= 0 ? (g.kind == SV_GATE_RX ? 1 : g.kind == SV_GATE_RY ? 2 : 3) : 0;
+      op.param = (int16_t)g.param;
+      op.gi = (int16_t)j;
+      P->ops.push_back(op);
+    }
+    G.op1 = (int32_t)P->ops.size();
+    P->groups.push_back(G);
+    pending.swap(rest);
+  }
+  C.ngroups = (int)P->groups.size() - C.group0;
+  for (int t = 0; t < H->n_terms; ++t) {
+    const uint64_t xm = H->xmask[t], zm = H->zmask[t];
+    const int ny = popc64(xm & zm) & 3;
+    const double cf = H->coeff[t];
+    P->terms.push_back({xm, zm, ny == 0 ? cf : ny == 2 ? -cf : 0.0,
+                        ny == 1 ? cf : ny == 3 ? -cf : 0.0});
+  }
+  P->circs.push_back(C);
+  return P->ops.size() < (size_t)0x7fffffff;
+}
+
+template <typename T>
+sv_status upload(T** dst, const std::vector<T>& v) {
+  const size_t bytes = std::max<size_t>(1, v.size()) * sizeof(T);
+  SV_CUDA_TRY(cudaMalloc((void**)dst, bytes));
+  if (!v.empty()) SV_CUDA_TRY(cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return SV_OK;
+}
+
+void free_batch(sv_batch b) {
+  void* ptrs[] = {b->circs, b->gates, b->groups, b->ops, b->terms, b->order,
+                  b->item_circ, b->theta_off, b->queue, b->work};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+}
+
+typedef void (*BatchKernel)(const BatchArgs);
+BatchKernel kernel_for(int k) {
+  return k == 2 ? kbatch<2> : k == 3 ? kbatch<3> : kbatch<4>;
+}
+
+sv_status launch_batch(sv_batch b, const double* theta, double* energy, double* grad,
+                       cudaStream_t st, int k, int threads, int blocks) {
+  BatchArgs A;
+  A.circs = b->circs;
+  A.gates = b->gates;
+  A.groups = b->groups;
+  A.ops = b->ops;
+  A.terms = b->terms;
+  A.order = b->order;
+  A.item_circ = b->item_circ;
+  A.theta_off = b->theta_off;
+  A.n_items = b->n_items;
+  A.nmax = b->nmax;
+  A.theta = theta;
+  A.energy = energy;
+  A.grad = grad;
+  A.work = b->work;
+  A.queue = b->queue;
+  SV_CUDA_TRY(cudaMemsetAsync(b->queue, 0, sizeof(int), st));
+  ProfScope prof(st, "kbatch");
+  kernel_for(k)<<<blocks, threads, 0, st>>>(A);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return check_launch("batch kernel");
+}
+
+}  // namespace
+}  // namespace sv
+
+using namespace sv;
+
+extern "C" {
+
+sv_status sv_batch_create(const sv_circuit* circuits, const sv_pauli_sum* hamiltonians,
+                          int n_circuits, const int32_t* item_circuit, int n_items, int tune,
+                          sv_batch* out) {
+  if (!circuits || !hamiltonians || !item_circuit || !out || n_circuits < 1 || n_items < 1) {
+    set_error("sv_batch_create: bad arguments");
+    return SV_ERR_INVALID;
+  }
+  int nmax = 1;
+  for (int c = 0; c < n_circuits; ++c) {
+    const sv_circuit& C = circuits[c];
+    const sv_pauli_sum& H = hamiltonians[c];
+    if (C.n_qubits < 1 || C.n_qubits > SV_BATCH_MAX_QUBITS || C.n_gates < 0 ||
+        C.n_gates > kBMaxGates || C.n_params < 0 || C.n_params > kBMaxParams ||
+        (C.n_gates > 0 && !C.gates)) {
+      set_error("sv_batch_create: circuit %d outside the batch limits (qubits <= %d, gates <= %d,"
+                " parameters <= %d)", c, SV_BATCH_MAX_QUBITS, kBMaxGates, kBMaxParams);
+      return SV_ERR_INVALID;
+    }
+    if (H.n_terms < 0 || H.n_terms > kBMaxTerms || (H.n_terms > 0 && (!H.xmask || !H.zmask || !H.coeff))) {
+      set_error("sv_batch_create: Hamiltonian %d must have 0..%d terms", c, kBMaxTerms);
+      return SV_ERR_INVALID;
+    }
+    const uint64_t lim = (uint64_t(1) << C.n_qubits) - 1;
+    for (int t = 0; t < H.n_terms; ++t)
+      if ((H.xmask[t] | H.zmask[t]) & ~lim) {
+        set_error("sv_batch_create: Hamiltonian %d term %d has bits beyond %d qubits", c, t, C.n_qubits);
+        return SV_ERR_INVALID;
+      }
+    for (int i = 0; i < C.n_gates; ++i) {
+      const sv_gate& g = C.gates[i];
+      const bool onequbit = g.kind >= SV_GATE_H && g.kind <= SV_GATE_U1 && g.n_tar == 1;
+      bool ok = onequbit && g.n_ctrl >= 0 && g.n_ctrl <= 3 && g.param >= -1 && g.param < C.n_params;
+      if (g.param >= 0 && g.kind != SV_GATE_RX && g.kind != SV_GATE_RY && g.kind != SV_GATE_RZ) ok = false;
+      uint64_t seen = 0;
+      for (int j = 0; ok && j < 1 + g.n_ctrl; ++j) {
+        const int q = j == 0 ? g.targets[0] : g.controls[j - 1];
+        if (q < 0 || q >= C.n_qubits || ((seen >> q) & 1)) ok = false;
+        else seen |= uint64_t(1) << q;
+      }
+      if (!ok) {
+        set_error("sv_batch_create: circuit %d gate %d: the batch kernel takes 1-qubit kinds "
+                  "(H X Y Z RX RY RZ U1) with up to 3 controls; parameters on RX/RY/RZ only", c, i);
+        return SV_ERR_INVALID;
+      }
+    }
+    nmax = std::max(nmax, C.n_qubits);
+  }
+  std::vector<int> ic(item_circuit, item_circuit + n_items), toff(n_items);
+  int total = 0;
+  for (int i = 0; i < n_items; ++i) {
+    if (ic[i] < 0 || ic[i] >= n_circuits) {
+      set_error("sv_batch_create: item %d names circuit %d of %d", i, ic[i], n_circuits);
+      return SV_ERR_INVALID;
+    }
+    toff[i] = total;
+    total += circuits[ic[i]].n_params;
+  }
+  sv_batch b = new sv_batch_s();
+  b->n_items = n_items;
+  b->nmax = nmax;
+  b->total_params = total;
+  b->h_theta_off = toff;
+  // batch packing: longest items first (work ~ gates x 2^n)
+  std::vector<int> order(n_items);
+  for (int i = 0; i < n_items; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+    const sv_circuit& A = circuits[ic[a]];
+    const sv_circuit& C = circuits[ic[c]];
+    return (double)A.n_gates * (1 << A.n_qubits) > (double)C.n_gates * (1 << C.n_qubits);
+  });
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (sms <= 0) sms = 152;
+  // candidates: group width k, threads per block, blocks per SM
+  struct Cand {
+    int k, threads, per_sm;
+  };
+  std::vector<Cand> cands;
+  if (tune) {
+    for (int k : {2, 3, 4})
+      for (int t : {128, 256, 512})
+        for (int per : {1, 2, 4}) cands.push_back({k, t, per});
+  } else {
+    cands.push_back({4, 256, 2});
+  }
+  int max_per = 1;
+  for (auto& c : cands) max_per = std::max(max_per, c.per_sm);
+  b->work_slots = (size_t)sms * max_per;
+  sv_status st = SV_OK;
+  // plans per k are built on demand; start with the device buffers that do not depend on k
+  st = upload(&b->order, order);
+  if (!st) st = upload(&b->item_circ, ic);
+  if (!st) st = upload(&b->theta_off, toff);
+  if (!st) {
+    cudaError_t e = cudaMalloc(&b->queue, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->work, b->work_slots * (sizeof(float2) << (nmax + 1)));
+    if (e != cudaSuccess) {
+      set_error("sv_batch_create: %s", cudaGetErrorString(e));
+      st = e == cudaErrorMemoryAllocation ? SV_ERR_OOM : SV_ERR_CUDA;
+    }
+  }
+  auto build_for_k = [&](int k) -> sv_status {
+    HostPlan P;
+    for (int c = 0; c < n_circuits; ++c)
+      if (!plan_circuit(&circuits[c], &hamiltonians[c], k, &P)) {
+        set_error("sv_batch_create: too many gate operations");
+        return SV_ERR_INVALID;
+      }
+    void* olds[] = {b->circs, b->gates, b->groups, b->ops, b->terms};
+    for (void* p : olds)
+      if (p) cudaFree(p);
+    b->circs = nullptr; b->gates = nullptr; b->groups = nullptr; b->ops = nullptr; b->terms = nullptr;
+    sv_status s2 = upload(&b->circs, P.circs);
+    if (!s2) s2 = upload(&b->gates, P.gates);
+    if (!s2) s2 = upload(&b->groups, P.groups);
+    if (!s2) s2 = upload(&b->ops, P.ops);
+    if (!s2) s2 = upload(&b->terms, P.terms);
+    return s2;
+  };
+  double* th = nullptr;
+  double* en = nullptr;
+  double* gr = nullptr;
+  if (!st && cands.size() > 1) {
+    // autotune on the real batch with arbitrary parameters (timing does not depend on them)
+    std::vector<double> tv(std::max(1, total));
+    for (size_t i = 0; i < tv.size(); ++i) tv[i] = 0.001 * (double)(i % 997);
+    cudaError_t e = cudaMalloc(&th, tv.size() * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&en, n_items * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&gr, tv.size() * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemcpy(th, tv.data(), tv.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      set_error("sv_batch_create: tuning buffers: %s", cudaGetErrorString(e));
+      st = SV_ERR_CUDA;
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int built = -1;
+    for (const Cand& c : cands) {
+      if (st) break;
+      if (c.k != built) {
+        st = build_for_k(c.k);
+        built = c.k;
+        if (st) break;
+      }
+      const int blocks = sms * c.per_sm;
+      st = launch_batch(b, th, en, gr, 0, c.k, c.threads, blocks);  // warm-up
+      if (st) break;
+      cudaEventRecord(e0, 0);
+      st = launch_batch(b, th, en, gr, 0, c.k, c.threads, blocks);
+      cudaEventRecord(e1, 0);
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        set_error("sv_batch_create: tuning run failed: %s", cudaGetErrorString(cudaGetLastError()));
+        st = SV_ERR_CUDA;
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        b->k = c.k;
+        b->threads = c.threads;
+        b->blocks = blocks;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  } else if (!st) {
+    b->k = cands[0].k;
+    b->threads = cands[0].threads;
+    b->blocks = sms * cands[0].per_sm;
+  }
+  if (th) cudaFree(th);
+  if (en) cudaFree(en);
+  if (gr) cudaFree(gr);
+  if (!st) st = build_for_k(b->k);
+  if (!st) {
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+      set_error("sv_batch_create: %s", cudaGetErrorString(e));
+      st = SV_ERR_CUDA;
+    }
+  }
+  if (st) {
+    free_batch(b);
+    delete b;
+    return st;
+  }
+  *out = b;
+  return SV_OK;
+}
+
+sv_status sv_batch_info(sv_batch b, int* k, int* threads, int* blocks, int* total_params) {
+  if (!b) {
+    set_error("sv_batch_info: null batch");
+    return SV_ERR_INVALID;
+  }
+  if (k) *k = b->k;
+  if (threads) *threads = b->threads;
+  if (blocks) *blocks = b->blocks;
+  if (total_params) *total_params = b->total_params;
+  return SV_OK;
+}
+
+sv_status sv_batch_run(sv_batch b, const double* dev_theta, double* dev_energy, double* dev_grad,
+                       void* cuda_stream) {
+  if (!b || !dev_theta || !dev_energy || !dev_grad) {
+    set_error("sv_batch_run: bad arguments");
+    return SV_ERR_INVALID;
+  }
+  return launch_batch(b, dev_theta, dev_energy, dev_grad, (cudaStream_t)cuda_stream, b->k,
+                      b->threads, b->blocks);
+}
+
+sv_status sv_batch_run_graph(sv_batch b, const double* dev_theta, double* dev_energy,
+                             double* dev_grad, void* cuda_stream) {
+  if (!b || !dev_theta || !dev_energy || !dev_grad) {
+    set_error("sv_batch_run_graph: bad arguments");
+    return SV_ERR_INVALID;
+  }
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const void* key[4] = {dev_theta, dev_energy, dev_grad, cuda_stream};
+  if (!b->gexec || memcmp(key, b->g_key, sizeof(key)) != 0) {
+    if (b->gexec) {
+      cudaGraphExecDestroy(b->gexec);
+      b->gexec = nullptr;
+    }
+    cudaStream_t cap = nullptr;
+    SV_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    sv_status s2 = SV_OK;
+    if (e == cudaSuccess) {
+      s2 = launch_batch(b, dev_theta, dev_energy, dev_grad, cap, b->k, b->threads, b->blocks);
+      e = cudaStreamEndCapture(cap, &g);
+    }
+    if (e == cudaSuccess && s2 == SV_OK) e = cudaGraphInstantiate(&b->gexec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cap);
+    if (e != cudaSuccess || s2 != SV_OK) {
+      if (e != cudaSuccess) set_error("sv_batch_run_graph: capture: %s", cudaGetErrorString(e));
+      b->gexec = nullptr;
+      return s2 != SV_OK ? s2 : SV_ERR_CUDA;
+    }
+    memcpy(b->g_key, key, sizeof(key));
+  }
+  SV_CUDA_TRY(cudaGraphLaunch(b->gexec, st));
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return SV_OK;
+}
+
+sv_status sv_batch_grad(const sv_circuit* circuits, const sv_pauli_sum* hamiltonians,
+                        int n_circuits, const int32_t* item_circuit, int n_items,
+                        const double* theta, void* cuda_stream, double* energies, double* grads) {
+  if (!theta || !energies || !grads) {
+    set_error("sv_batch_grad: null host arrays");
+    return SV_ERR_INVALID;
+  }
+  sv_batch b = nullptr;
+  sv_status st = sv_batch_create(circuits, hamiltonians, n_circuits, item_circuit, n_items, 0, &b);
+  if (st) return st;
+  const size_t np = std::max(1, b->total_params);
+  double *th = nullptr, *en = nullptr, *gr = nullptr;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  cudaError_t e = cudaMalloc(&th, np * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&en, n_items * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&gr, np * sizeof(double));
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(th, theta, b->total_params * sizeof(double), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    st = sv_batch_run(b, th, en, gr, cuda_stream);
+    if (!st) {
+      e = cudaMemcpyAsync(energies, en, n_items * sizeof(double), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(grads, gr, b->total_params * sizeof(double), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+  }
+  if (e != cudaSuccess && !st) {
+    set_error("sv_batch_grad: %s", cudaGetErrorString(e));
+    st = e == cudaErrorMemoryAllocation ? SV_ERR_OOM : SV_ERR_CUDA;
+  }
+  if (th) cudaFree(th);
+  if (en) cudaFree(en);
+  if (gr) cudaFree(gr);
+  sv_batch_free(b);
+  return st;
+}
+
+sv_status sv_batch_free(sv_batch b) {
+  if (!b) return SV_OK;
+  cudaDeviceSynchronize();
+  free_batch(b);
+  delete b;
+  return SV_OK;
+}
+
+}  // extern "C"

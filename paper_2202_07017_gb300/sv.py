@@ -53,7 +53,9 @@ EXPORTS = ("sv_alloc", "sv_wrap", "sv_free", "sv_set_stream", "sv_info", "sv_ini
            "sv_upload", "sv_download", "sv_copy", "sv_apply_gate", "sv_apply_circuit",
            "sv_norm", "sv_expval", "sv_expval_async", "sv_apply_pauli_sum", "sv_adjoint",
            "sv_grad", "sv_sync", "sv_last_error", "sv_launch_count", "sv_version",
-           "sv_profile_start", "sv_profile_stop", "sv_fusion_plan", "sv_expval_noalloc")
+           "sv_profile_start", "sv_profile_stop", "sv_fusion_plan", "sv_expval_noalloc",
+           "sv_batch_create", "sv_batch_info", "sv_batch_run", "sv_batch_run_graph", "sv_batch_grad",
+           "sv_batch_free")
 
 _lib = None
 
@@ -95,6 +97,14 @@ def load(build: bool = True):
                     P(c_dbl), P(c_dbl)],
         "sv_sync": [c_vp],
         "sv_profile_start": [],
+        "sv_batch_create": [P(SvCircuit), P(SvPauliSum), ctypes.c_int, P(c_i32), ctypes.c_int,
+                            ctypes.c_int, P(c_vp)],
+        "sv_batch_info": [c_vp, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int)],
+        "sv_batch_run": [c_vp, c_vp, c_vp, c_vp, c_vp],
+        "sv_batch_run_graph": [c_vp, c_vp, c_vp, c_vp, c_vp],
+        "sv_batch_grad": [P(SvCircuit), P(SvPauliSum), ctypes.c_int, P(c_i32), ctypes.c_int,
+                          P(c_dbl), c_vp, P(c_dbl), P(c_dbl)],
+        "sv_batch_free": [c_vp],
         "sv_expval_noalloc": [c_vp, ctypes.c_int, ctypes.c_int, P(SvPauliSum), c_vp, c_vp],
         "sv_fusion_plan": [P(SvCircuit), P(c_dbl), ctypes.c_int, ctypes.c_int, P(c_i32), P(c_i32),
                            P(c_i32), P(c_i32)],
@@ -360,3 +370,65 @@ def sv_profile_stop() -> dict:
         name, cnt, ms = line.split()
         out[name] = (int(cnt), float(ms))
     return out
+
+
+# ---- batched energies and gradients ----------------------------------------------------
+class PackedBatch:
+    """Arrays of sv_circuit / sv_pauli_sum for a batch, plus the item map."""
+
+    def __init__(self, circuits, hamiltonians, item_circuit):
+        self.pcs = [pack_circuit(c) for c in circuits]
+        self.pps = [pack_pauli(h, pc.n_qubits) for h, pc in zip(hamiltonians, self.pcs)]
+        if len(self.pcs) != len(self.pps):
+            raise SvError(1, "one Hamiltonian per circuit")
+        self.carr = (SvCircuit * len(self.pcs))(*[pc.c for pc in self.pcs])
+        self.harr = (SvPauliSum * len(self.pps))(*[pp.s for pp in self.pps])
+        self.items = np.ascontiguousarray(item_circuit, dtype=np.int32)
+        self.n_params = [pc.n_params for pc in self.pcs]
+        self.total_params = int(sum(self.n_params[i] for i in self.items))
+
+
+def sv_batch_create(circuits, hamiltonians, item_circuit, tune: bool = False):
+    pb = PackedBatch(circuits, hamiltonians, item_circuit)
+    h = c_vp()
+    _check(load().sv_batch_create(pb.carr, pb.harr, len(pb.pcs),
+                                  pb.items.ctypes.data_as(ctypes.POINTER(c_i32)), len(pb.items),
+                                  int(bool(tune)), ctypes.byref(h)))
+    return h.value, pb
+
+
+def sv_batch_info(h: int):
+    k, t, b, p = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().sv_batch_info(c_vp(h), ctypes.byref(k), ctypes.byref(t), ctypes.byref(b),
+                                ctypes.byref(p)))
+    return k.value, t.value, b.value, p.value
+
+
+def sv_batch_run(h: int, dev_theta: int, dev_energy: int, dev_grad: int, stream: int = 0) -> None:
+    _check(load().sv_batch_run(c_vp(h), c_vp(dev_theta), c_vp(dev_energy), c_vp(dev_grad),
+                               c_vp(stream)))
+
+
+def sv_batch_run_graph(h: int, dev_theta: int, dev_energy: int, dev_grad: int,
+                       stream: int = 0) -> None:
+    _check(load().sv_batch_run_graph(c_vp(h), c_vp(dev_theta), c_vp(dev_energy),
+                                     c_vp(dev_grad), c_vp(stream)))
+
+
+def sv_batch_grad(circuits, hamiltonians, item_circuit, theta, stream: int = 0):
+    pb = PackedBatch(circuits, hamiltonians, item_circuit)
+    th = np.ascontiguousarray(theta if len(theta) else [0.0], dtype=np.float64)
+    if len(theta) != pb.total_params:
+        raise SvError(1, f"theta has {len(theta)} entries, the batch needs {pb.total_params}")
+    e = np.zeros(len(pb.items))
+    g = np.zeros(max(1, pb.total_params))
+    P = ctypes.POINTER
+    _check(load().sv_batch_grad(pb.carr, pb.harr, len(pb.pcs),
+                                pb.items.ctypes.data_as(P(c_i32)), len(pb.items),
+                                th.ctypes.data_as(P(c_dbl)), c_vp(stream),
+                                e.ctypes.data_as(P(c_dbl)), g.ctypes.data_as(P(c_dbl))))
+    return e, g[:pb.total_params]
+
+
+def sv_batch_free(h: int) -> None:
+    _check(load().sv_batch_free(c_vp(h)))

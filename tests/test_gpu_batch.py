@@ -1,0 +1,130 @@
+"""GPU parity of the batched persistent kernel (energies and adjoint
+gradients of many circuits in one launch) against the oracle's energies and
+exact shift-rule gradients and against the single-state adjoint path; graph
+replay and the autotuner; the batch shaped like 4096 parameter sets of the
+n = 14 hardware-efficient ansatz plus 1024 mixed circuits (n 8..16, depth
+5..15)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from gpu_helpers import oracle_threads
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+ONEQ = ("H", "X", "Y", "Z", "RX", "RY", "RZ", "U1")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _threads():
+    oracle_threads()
+
+
+def _rel(g, ref):
+    return float(np.max(np.abs(g - ref)) / max(np.max(np.abs(ref)), 1e-300))
+
+
+def _small_batch():
+    circuits, hams = [], []
+    for n in (1, 2, 3, 5, 8):
+        c, _ = W.hea(n, 3, 10 + n)
+        circuits.append(c)
+        hams.append(W.tfim(n) if n > 1 else [(1.0, ((0, "X"),)), (0.5, ((0, "Z"),))])
+    for n, seed in ((4, 1), (7, 2), (9, 3)):
+        c, _ = W.random_gates(n, 50, seed, max_tar=1, max_ctrl=2, kinds=ONEQ)
+        circuits.append(c)
+        hams.append(W.random_pauli_sum(n, 12, seed))
+    items = [i % len(circuits) for i in range(2 * len(circuits))]
+    rng = W.SplitMix64(77)
+    thetas = [np.array([rng.angle() for _ in range(circuits[ci].n_params)]) for ci in items]
+    return circuits, hams, items, thetas
+
+
+@pytest.mark.parametrize("tune", [False, True])
+def test_batch_against_oracle(tune):
+    from paper_2202_07017_gb300 import Batch
+    circuits, hams, items, thetas = _small_batch()
+    b = Batch(circuits, hams, items, tune=tune)
+    theta = torch.tensor(np.concatenate(thetas), dtype=torch.float64, device="cuda")
+    e, g = b.run(theta)
+    e2, g2 = b.run(theta, graph=True)
+    e3, g3 = b.run(theta, graph=True)
+    torch.cuda.synchronize()
+    e, g, e2, g2, e3, g3 = (t.cpu().numpy() for t in (e, g, e2, g2, e3, g3))
+    b.close()
+    assert np.array_equal(e, e2) and np.array_equal(g, g2)   # same kernel, fixed order
+    assert np.array_equal(e2, e3) and np.array_equal(g2, g3)
+    off = 0
+    for i, ci in enumerate(items):
+        c, H, th = circuits[ci], hams[ci], thetas[i]
+        scale = sum(abs(t[0]) for t in H)
+        assert abs(e[i] - oracle.energy(c, th, H)) <= 1e-5 * scale
+        if c.n_params:
+            gi = g[off:off + c.n_params]
+            ref = oracle.grad_param_shift(c, th, H)
+            assert _rel(gi, ref) <= 1e-5, (i, _rel(gi, ref))
+        off += c.n_params
+
+
+def test_batch_one_shot_matches_persistent_run():
+    from paper_2202_07017_gb300 import Batch, sv_batch_grad
+    circuits, hams, items, thetas = _small_batch()
+    theta = np.concatenate(thetas)
+    e1, g1 = sv_batch_grad(circuits, hams, items, theta)
+    b = Batch(circuits, hams, items, tune=False)
+    e2, g2 = b.run(torch.tensor(theta, dtype=torch.float64, device="cuda"))
+    torch.cuda.synchronize()
+    assert np.array_equal(e1, e2.cpu().numpy()) and np.array_equal(g1, g2.cpu().numpy())
+    b.close()
+
+
+def test_batch_rejects_unsupported_gates():
+    from paper_2202_07017_gb300 import Batch, SvError
+    c = W.Circuit(3, [W.Gate("SWAP", (0, 1))], 0)
+    with pytest.raises(SvError):
+        Batch([c], [W.tfim(3)], [0], tune=False)
+    c, th = W.hea(19, 1, 1)
+    with pytest.raises(SvError):
+        Batch([c], [W.tfim(19)], [0], tune=False)
+
+
+def test_batch_hea14_and_mixed_shapes():
+    """4096 parameter sets of the n = 14, L = 10 ansatz (TFIM) plus 1024
+    mixed circuits (n uniform in 8..16, depth 5..15), one persistent launch,
+    autotuned; sampled items against the oracle and the single-state
+    adjoint path."""
+    from paper_2202_07017_gb300 import Batch, State
+    hea14, _ = W.hea(14, 10, 1003)
+    mixed = W.mixed_batch(1024, 1003)
+    circuits = [hea14] + [m[0] for m in mixed]
+    hams = [W.tfim(14)] + [m[2] for m in mixed]
+    items = [0] * 4096 + list(range(1, 1025))
+    thetas = [W.hea_theta(14, 10, 1003 + i) for i in range(4096)] + [m[1] for m in mixed]
+    theta = np.concatenate(thetas)
+    b = Batch(circuits, hams, items, tune=True)
+    e, g = b.run(torch.tensor(theta, dtype=torch.float64, device="cuda"), graph=True)
+    torch.cuda.synchronize()
+    e, g = e.cpu().numpy(), g.cpu().numpy()
+    b.close()
+    offs = np.concatenate([[0], np.cumsum([circuits[ci].n_params for ci in items])])
+    rs = np.random.default_rng(1)
+    sample = [0, 4095, 4096, 5119] + list(rs.integers(0, 5120, 8))
+    for i in sample:
+        c, H, th = circuits[items[i]], hams[items[i]], thetas[i]
+        st = State(c.n_qubits, "c64").init(0)
+        st.apply_circuit(c, th)
+        e_ref, g_ref = st.adjoint(c, th, H)
+        st.close()
+        scale = sum(abs(t[0]) for t in H)
+        assert abs(e[i] - e_ref) <= 2e-5 * scale
+        gi = g[offs[i]:offs[i + 1]]
+        assert _rel(gi, g_ref) <= 2e-5
+    for i in (0, 4100):
+        c, H, th = circuits[items[i]], hams[items[i]], thetas[i]
+        assert abs(e[i] - oracle.energy(c, th, H)) <= 1e-5 * sum(abs(t[0]) for t in H)
+        ps = [0, c.n_params // 2, c.n_params - 1]
+        ref = oracle.grad_param_shift(c, th, H, params=ps)
+        gi = g[offs[i]:offs[i + 1]]
+        assert np.max(np.abs(gi[ps] - ref[ps])) <= 1e-5 * max(1.0, np.max(np.abs(ref[ps])))

@@ -177,6 +177,12 @@ def hea(n: int, layers: int, seed: int) -> Tuple[Circuit, np.ndarray]:
     return Circuit(n, gates, n * layers, f"hea_n{n}_L{layers}"), theta
 
 
+def hea_theta(n: int, layers: int, seed: int) -> np.ndarray:
+    """The parameter vector hea(n, layers, seed) draws, without the circuit."""
+    rng = SplitMix64(seed)
+    return np.array([rng.angle() for _ in range(n * layers)])
+
+
 def ghz(n: int) -> Circuit:
     gates = [Gate("H", (0,))] + [Gate("X", (k + 1,), (k,)) for k in range(n - 1)]
     return Circuit(n, gates, 0, f"ghz_n{n}")
