@@ -283,6 +283,13 @@ sv_status sv_batch_create(const sv_circuit* circuits, const sv_pauli_sum* hamilt
                           int n_circuits, const int32_t* item_circuit, int n_items, int tune,
                           sv_batch* out);
 
+/* Host-only dry run of the batch planner (no GPU call): validates the
+ * circuits and Hamiltonians as sv_batch_create does and writes, per
+ * circuit, the number of register groups of width k (max(2, widest gate)
+ * <= k <= 4) its gates are scheduled into.  Errors: SV_ERR_INVALID. */
+sv_status sv_batch_plan(const sv_circuit* circuits, const sv_pauli_sum* hamiltonians,
+                        int n_circuits, int k, int32_t* groups_per_circuit);
+
 /* Chosen tile (k, threads per block, blocks) and total parameter count. */
 sv_status sv_batch_info(sv_batch b, int* k, int* threads, int* blocks, int* total_params);
 

@@ -13,6 +13,7 @@ from __future__ import annotations
 import numpy as np
 
 from .sv import (C64, C128, EXPORTS, PackedBatch, sv_batch_create, sv_batch_free, sv_batch_grad,
+                 sv_batch_plan,
                  sv_batch_info, sv_batch_run, sv_batch_run_graph, PackedCircuit, PackedPauli, SvError, load, pack_circuit,
                  pack_pauli, sv_adjoint, sv_alloc, sv_apply_circuit, sv_apply_gate,
                  sv_apply_pauli_sum, sv_copy, sv_download, sv_expval, sv_expval_async, sv_free,

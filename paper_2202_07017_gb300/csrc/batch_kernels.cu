@@ -417,6 +417,7 @@ bool plan_circuit(const sv_circuit* c, const sv_pauli_sum* H, int k, HostPlan* P
   std::vector<int> pending(c->n_gates);
   for (int i = 0; i < c->n_gates; ++i) pending[i] = i;
   while (!pending.empty()) {
+    if (popc64(qm[pending[0]]) > k) return false;  // a gate wider than a group
     uint64_t gq = qm[pending[0]], acc = 0;
     std::vector<int> members, rest;
     for (int j : pending) {
@@ -526,32 +527,36 @@ using namespace sv;
 
 extern "C" {
 
-sv_status sv_batch_create(const sv_circuit* circuits, const sv_pauli_sum* hamiltonians,
-                          int n_circuits, const int32_t* item_circuit, int n_items, int tune,
-                          sv_batch* out) {
-  if (!circuits || !hamiltonians || !item_circuit || !out || n_circuits < 1 || n_items < 1) {
-    set_error("sv_batch_create: bad arguments");
+}  // extern "C"
+
+// Checks every circuit and Hamiltonian against the batch kernel's limits;
+// returns the largest qubit count and the widest gate (target + controls).
+static sv_status validate_batch(const char* who, const sv_circuit* circuits,
+                                const sv_pauli_sum* hamiltonians, int n_circuits, int* nmax_out,
+                                int* width_out) {
+  if (!circuits || !hamiltonians || n_circuits < 1) {
+    set_error("%s: bad arguments", who);
     return SV_ERR_INVALID;
   }
-  int nmax = 1;
+  int nmax = 1, width = 1;  // widest gate: target plus controls
   for (int c = 0; c < n_circuits; ++c) {
     const sv_circuit& C = circuits[c];
     const sv_pauli_sum& H = hamiltonians[c];
     if (C.n_qubits < 1 || C.n_qubits > SV_BATCH_MAX_QUBITS || C.n_gates < 0 ||
         C.n_gates > kBMaxGates || C.n_params < 0 || C.n_params > kBMaxParams ||
         (C.n_gates > 0 && !C.gates)) {
-      set_error("sv_batch_create: circuit %d outside the batch limits (qubits <= %d, gates <= %d,"
-                " parameters <= %d)", c, SV_BATCH_MAX_QUBITS, kBMaxGates, kBMaxParams);
+      set_error("%s: circuit %d outside the batch limits (qubits <= %d, gates <= %d,"
+                " parameters <= %d)", who, c, SV_BATCH_MAX_QUBITS, kBMaxGates, kBMaxParams);
       return SV_ERR_INVALID;
     }
     if (H.n_terms < 0 || H.n_terms > kBMaxTerms || (H.n_terms > 0 && (!H.xmask || !H.zmask || !H.coeff))) {
-      set_error("sv_batch_create: Hamiltonian %d must have 0..%d terms", c, kBMaxTerms);
+      set_error("%s: Hamiltonian %d must have 0..%d terms", who, c, kBMaxTerms);
       return SV_ERR_INVALID;
     }
     const uint64_t lim = (uint64_t(1) << C.n_qubits) - 1;
     for (int t = 0; t < H.n_terms; ++t)
       if ((H.xmask[t] | H.zmask[t]) & ~lim) {
-        set_error("sv_batch_create: Hamiltonian %d term %d has bits beyond %d qubits", c, t, C.n_qubits);
+        set_error("%s: Hamiltonian %d term %d has bits beyond %d qubits", who, c, t, C.n_qubits);
         return SV_ERR_INVALID;
       }
     for (int i = 0; i < C.n_gates; ++i) {
@@ -566,12 +571,54 @@ sv_status sv_batch_create(const sv_circuit* circuits, const sv_pauli_sum* hamilt
         else seen |= uint64_t(1) << q;
       }
       if (!ok) {
-        set_error("sv_batch_create: circuit %d gate %d: the batch kernel takes 1-qubit kinds "
-                  "(H X Y Z RX RY RZ U1) with up to 3 controls; parameters on RX/RY/RZ only", c, i);
+        set_error("%s: circuit %d gate %d: the batch kernel takes 1-qubit kinds "
+                  "(H X Y Z RX RY RZ U1) with up to 3 controls; parameters on RX/RY/RZ only", who, c, i);
         return SV_ERR_INVALID;
       }
     }
     nmax = std::max(nmax, C.n_qubits);
+    for (int i = 0; i < C.n_gates; ++i) width = std::max(width, 1 + C.gates[i].n_ctrl);
+  }
+  *nmax_out = nmax;
+  *width_out = width;
+  return SV_OK;
+}
+
+extern "C" {
+
+sv_status sv_batch_plan(const sv_circuit* circuits, const sv_pauli_sum* hamiltonians,
+                        int n_circuits, int k, int32_t* groups_per_circuit) {
+  int nmax = 0, width = 0;
+  sv_status st = validate_batch("sv_batch_plan", circuits, hamiltonians, n_circuits, &nmax, &width);
+  if (st) return st;
+  if (k < 2 || k > 4 || k < width || !groups_per_circuit) {
+    set_error("sv_batch_plan: group width %d must be in max(2, widest gate %d)..4", k, width);
+    return SV_ERR_INVALID;
+  }
+  HostPlan P;
+  for (int c = 0; c < n_circuits; ++c) {
+    const size_t g0 = P.groups.size();
+    if (!plan_circuit(&circuits[c], &hamiltonians[c], k, &P)) {
+      set_error("sv_batch_plan: circuit %d does not fit groups of %d qubits", c, k);
+      return SV_ERR_INVALID;
+    }
+    groups_per_circuit[c] = (int32_t)(P.groups.size() - g0);
+  }
+  return SV_OK;
+}
+
+sv_status sv_batch_create(const sv_circuit* circuits, const sv_pauli_sum* hamiltonians,
+                          int n_circuits, const int32_t* item_circuit, int n_items, int tune,
+                          sv_batch* out) {
+  if (!item_circuit || !out || n_items < 1) {
+    set_error("sv_batch_create: bad arguments");
+    return SV_ERR_INVALID;
+  }
+  int nmax = 1, width = 1;
+  {
+    sv_status vs = validate_batch("sv_batch_create", circuits, hamiltonians, n_circuits, &nmax,
+                                  &width);
+    if (vs) return vs;
   }
   std::vector<int> ic(item_circuit, item_circuit + n_items), toff(n_items);
   int total = 0;
@@ -607,10 +654,11 @@ sv_status sv_batch_create(const sv_circuit* circuits, const sv_pauli_sum* hamilt
   std::vector<Cand> cands;
   if (tune) {
     for (int k : {2, 3, 4})
+      if (k >= width)
       for (int t : {128, 256, 512})
         for (int per : {1, 2, 4}) cands.push_back({k, t, per});
   } else {
-    cands.push_back({4, 256, 2});
+    cands.push_back({std::max(4, width), 256, 2});
   }
   int max_per = 1;
   for (auto& c : cands) max_per = std::max(max_per, c.per_sm);
@@ -632,7 +680,7 @@ sv_status sv_batch_create(const sv_circuit* circuits, const sv_pauli_sum* hamilt
     HostPlan P;
     for (int c = 0; c < n_circuits; ++c)
       if (!plan_circuit(&circuits[c], &hamiltonians[c], k, &P)) {
-        set_error("sv_batch_create: too many gate operations");
+        set_error("sv_batch_create: a gate does not fit a register group of %d qubits", k);
         return SV_ERR_INVALID;
       }
     void* olds[] = {b->circs, b->gates, b->groups, b->ops, b->terms};

@@ -54,7 +54,7 @@ EXPORTS = ("sv_alloc", "sv_wrap", "sv_free", "sv_set_stream", "sv_info", "sv_ini
            "sv_norm", "sv_expval", "sv_expval_async", "sv_apply_pauli_sum", "sv_adjoint",
            "sv_grad", "sv_sync", "sv_last_error", "sv_launch_count", "sv_version",
            "sv_profile_start", "sv_profile_stop", "sv_fusion_plan", "sv_expval_noalloc",
-           "sv_batch_create", "sv_batch_info", "sv_batch_run", "sv_batch_run_graph", "sv_batch_grad",
+           "sv_batch_create", "sv_batch_plan", "sv_batch_info", "sv_batch_run", "sv_batch_run_graph", "sv_batch_grad",
            "sv_batch_free")
 
 _lib = None
@@ -99,6 +99,7 @@ def load(build: bool = True):
         "sv_profile_start": [],
         "sv_batch_create": [P(SvCircuit), P(SvPauliSum), ctypes.c_int, P(c_i32), ctypes.c_int,
                             ctypes.c_int, P(c_vp)],
+        "sv_batch_plan": [P(SvCircuit), P(SvPauliSum), ctypes.c_int, ctypes.c_int, P(c_i32)],
         "sv_batch_info": [c_vp, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int)],
         "sv_batch_run": [c_vp, c_vp, c_vp, c_vp, c_vp],
         "sv_batch_run_graph": [c_vp, c_vp, c_vp, c_vp, c_vp],
@@ -395,6 +396,15 @@ def sv_batch_create(circuits, hamiltonians, item_circuit, tune: bool = False):
                                   pb.items.ctypes.data_as(ctypes.POINTER(c_i32)), len(pb.items),
                                   int(bool(tune)), ctypes.byref(h)))
     return h.value, pb
+
+
+def sv_batch_plan(circuits, hamiltonians, k: int):
+    """Host-only: register groups per circuit for group width k."""
+    pb = PackedBatch(circuits, hamiltonians, [0])
+    out = np.zeros(len(pb.pcs), np.int32)
+    _check(load().sv_batch_plan(pb.carr, pb.harr, len(pb.pcs), int(k),
+                                out.ctypes.data_as(ctypes.POINTER(c_i32))))
+    return out
 
 
 def sv_batch_info(h: int):
