@@ -231,6 +231,38 @@ def fused_layered(torch, n=33, depth=40, k=4):
             "unfused_full_estimate_s": t2_u * len(c.gates) / len(layer2.gates)}
 
 
+def layered_adjoint(torch, n=28, depth=40):
+    """Adjoint gradient of <sum Z_i> for the random layered circuit at n = 28
+    (complex64, 3900 gates, 3360 parameters) with forward checkpoints every 10
+    layers: forward (circuit + energy) and forward + gradient times."""
+    import workloads as W
+    from paper_2202_07017_gb300 import (C64, pack_circuit, pack_pauli, sv_alloc, sv_apply_circuit,
+                                        sv_expval, sv_free, sv_grad, sv_init)
+    c, theta = W.random_layered(n, depth, 1004)
+    pc, pp = pack_circuit(c), pack_pauli(W.sum_z(n), n)
+    starts = [i for i, g in enumerate(c.gates) if g.kind == "RX" and g.targets == (0,)]
+    ck = [starts[10], starts[20], starts[30]]
+    h = sv_alloc(n, C64, torch.cuda.current_stream().cuda_stream)
+    try:
+        sv_init(h, 0)
+        sv_grad(h, pc, theta, pp, ck)  # warm-up (allocates work states and checkpoints)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sv_init(h, 0)
+        sv_apply_circuit(h, pc, theta, 0)
+        e = sv_expval(h, pp)
+        t1 = time.perf_counter()
+        sv_init(h, 0)
+        e2, g = sv_grad(h, pc, theta, pp, ck)
+        t2 = time.perf_counter()
+    finally:
+        sv_free(h)
+    return {"workload": f"random layered n={n} complex64 depth {depth} ({len(c.gates)} gates, "
+                        f"{c.n_params} params), <sum Z>, checkpoints every 10 layers",
+            "forward_s": t1 - t0, "forward_plus_grad_s": t2 - t1,
+            "grad_over_forward": (t2 - t1 - (t1 - t0)) / (t1 - t0), "energy": e2}
+
+
 def batch_solves(torch, reps=5):
     """4096 parameter sets of the n = 14, L = 10 hardware-efficient ansatz
     plus 1024 mixed ansatz circuits (n 8..16, depth 5..15), TFIM energies and
@@ -321,6 +353,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fused", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-adj28", action="store_true")
     ap.add_argument("--fused-n", type=int, default=33,
                     help="qubits of the fused layered-circuit measurement")
     ap.add_argument("--gate-table", choices=["c64", "c128"],
@@ -449,6 +482,7 @@ def main():
         adj = adjoint_ratio(torch)
         fused = None if args.no_fused else fused_layered(torch, n=args.fused_n)
         batch = None if args.no_batch else batch_solves(torch)
+        adj28 = None if args.no_adj28 else layered_adjoint(torch)
         cpu = None
         if not args.no_cpu:
             threads = os.cpu_count() or 1
@@ -482,6 +516,7 @@ def main():
             "adjoint": adj,
             "fused": fused,
             "batch": batch,
+            "adjoint_n28": adj28,
         }
     sv_free(h)
     if out is not None:
