@@ -51,7 +51,7 @@ struct BOp {
   uint8_t b0;     // group-local target index
   uint8_t cm;     // group-local control mask
   uint8_t pauli;  // generator for gradients: 0 none, 1 X, 2 Y, 3 Z
-  uint8_t pad;
+  uint8_t cls;    // arithmetic class of the 2x2 matrix (BC_*)
   int16_t param;  // parameter index or -1
   int16_t gi;     // gate index within the circuit (matrix table slot)
 };
@@ -91,32 +91,82 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 
 __host__ __device__ constexpr int lowbit_b(int r) { return (r & 1) ? 0 : 1 + lowbit_b(r >> 1); }
 
-// (a, b) <- M (a, b) for every register pair on group bit B with controls cm.
-template <int K, int B>
-__device__ __forceinline__ void pair_apply(const float* M, int cm, float (&re)[1 << K],
-                                           float (&im)[1 << K]) {
+// Arithmetic classes of a gate's 2x2 matrix: the work per pair drops from 16
+// multiply-adds (dense) to 8 (real: H, X, RY; imaginary off-diagonal: Y, RX;
+// diagonal: RZ), to 4 on one amplitude (phase: U1) or to a sign flip (Z, CZ).
+enum { BC_DENSE = 0, BC_REAL = 1, BC_IMOFF = 2, BC_DIAG = 3, BC_PHASE = 4, BC_NEG = 5 };
+
+// (a, b) <- M (a, b) for every register pair on group bit B (with controls cm
+// when CTRL).
+template <int K, int B, int CLS, bool CTRL>
+__device__ __forceinline__ void pair_apply_c(const float* M, int cm, float (&re)[1 << K],
+                                             float (&im)[1 << K]) {
   const float g0r = M[0], g0i = M[1], g1r = M[2], g1i = M[3];
   const float g2r = M[4], g2i = M[5], g3r = M[6], g3i = M[7];
 #pragma unroll
   for (int r = 0; r < (1 << K); ++r) {
     if (r & (1 << B)) continue;
+    if (CTRL && (r & cm) != cm) continue;
     const int r1 = r | (1 << B);
-    if ((r & cm) != cm) continue;
     const float ar = re[r], ai = im[r], br = re[r1], bi = im[r1];
-    re[r] = g0r * ar - g0i * ai + g1r * br - g1i * bi;
-    im[r] = g0r * ai + g0i * ar + g1r * bi + g1i * br;
-    re[r1] = g2r * ar - g2i * ai + g3r * br - g3i * bi;
-    im[r1] = g2r * ai + g2i * ar + g3r * bi + g3i * br;
+    if (CLS == BC_NEG) {
+      re[r1] = -br;
+      im[r1] = -bi;
+    } else if (CLS == BC_PHASE) {
+      re[r1] = g3r * br - g3i * bi;
+      im[r1] = g3r * bi + g3i * br;
+    } else if (CLS == BC_DIAG) {
+      re[r] = g0r * ar - g0i * ai;
+      im[r] = g0r * ai + g0i * ar;
+      re[r1] = g3r * br - g3i * bi;
+      im[r1] = g3r * bi + g3i * br;
+    } else if (CLS == BC_REAL) {
+      re[r] = g0r * ar + g1r * br;
+      im[r] = g0r * ai + g1r * bi;
+      re[r1] = g2r * ar + g3r * br;
+      im[r1] = g2r * ai + g3r * bi;
+    } else if (CLS == BC_IMOFF) {
+      re[r] = g0r * ar - g1i * bi;
+      im[r] = g0r * ai + g1i * br;
+      re[r1] = g3r * br - g2i * ai;
+      im[r1] = g3r * bi + g2i * ar;
+    } else {
+      re[r] = g0r * ar - g0i * ai + g1r * br - g1i * bi;
+      im[r] = g0r * ai + g0i * ar + g1r * bi + g1i * br;
+      re[r1] = g2r * ar - g2i * ai + g3r * br - g3i * bi;
+      im[r1] = g2r * ai + g2i * ar + g3r * bi + g3i * br;
+    }
   }
 }
 
-// the adjoint of M applied to the pairs
 template <int K, int B>
-__device__ __forceinline__ void pair_apply_dag(const float* M, int cm, float (&re)[1 << K],
-                                               float (&im)[1 << K]) {
+__device__ __forceinline__ void pair_apply(int cls, const float* M, int cm, float (&re)[1 << K],
+                                           float (&im)[1 << K]) {
+  if (cm) {
+    switch (cls) {
+      case BC_PHASE: pair_apply_c<K, B, BC_PHASE, true>(M, cm, re, im); break;
+      case BC_NEG: pair_apply_c<K, B, BC_NEG, true>(M, cm, re, im); break;
+      default: pair_apply_c<K, B, BC_DENSE, true>(M, cm, re, im); break;
+    }
+  } else {
+    switch (cls) {
+      case BC_REAL: pair_apply_c<K, B, BC_REAL, false>(M, 0, re, im); break;
+      case BC_IMOFF: pair_apply_c<K, B, BC_IMOFF, false>(M, 0, re, im); break;
+      case BC_DIAG: pair_apply_c<K, B, BC_DIAG, false>(M, 0, re, im); break;
+      case BC_PHASE: pair_apply_c<K, B, BC_PHASE, false>(M, 0, re, im); break;
+      case BC_NEG: pair_apply_c<K, B, BC_NEG, false>(M, 0, re, im); break;
+      default: pair_apply_c<K, B, BC_DENSE, false>(M, 0, re, im); break;
+    }
+  }
+}
+
+// the adjoint of M (same arithmetic class) applied to the pairs
+template <int K, int B>
+__device__ __forceinline__ void pair_apply_dag(int cls, const float* M, int cm,
+                                               float (&re)[1 << K], float (&im)[1 << K]) {
   // M^dagger = [[conj g0, conj g2], [conj g1, conj g3]]
   const float h[8] = {M[0], -M[1], M[4], -M[5], M[2], -M[3], M[6], -M[7]};
-  pair_apply<K, B>(h, cm, re, im);
+  pair_apply<K, B>(cls, h, cm, re, im);
 }
 
 // sum over the pairs of Im( conj(l0) (P p)_0 + conj(l1) (P p)_1 )
@@ -190,7 +240,7 @@ __device__ void group_fwd(float2* psi, int n, const BGroup& g, const BOp* ops, c
       const BOp op = ops[o];
       const float* M = mats + 8 * op.gi;
 #define SV_FWD(BB) \
-  if constexpr (BB < K) pair_apply<K, BB>(M, op.cm, re, im)
+  if constexpr (BB < K) pair_apply<K, BB>(op.cls, M, op.cm, re, im)
       SV_BIT_SWITCH(op.b0, SV_FWD)
 #undef SV_FWD
     }
@@ -242,8 +292,8 @@ __device__ void group_bwd(float2* psi, float2* lam, int n, const BGroup& g, cons
       }
 #define SV_BWD(BB)                                  \
   if constexpr (BB < K) {                           \
-    pair_apply_dag<K, BB>(M, op.cm, pr, pi);        \
-    pair_apply_dag<K, BB>(M, op.cm, lr, li);        \
+    pair_apply_dag<K, BB>(op.cls, M, op.cm, pr, pi); \
+    pair_apply_dag<K, BB>(op.cls, M, op.cm, lr, li); \
   }
       SV_BIT_SWITCH(op.b0, SV_BWD)
 #undef SV_BWD
@@ -259,11 +309,11 @@ __device__ void group_bwd(float2* psi, float2* lam, int n, const BGroup& g, cons
   }
 }
 
-template <int K>
-__global__ void __launch_bounds__(512) kbatch(const BatchArgs A) {
+template <int K, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) kbatch(const BatchArgs A) {
   __shared__ float mats[8 * kBMaxGates];
-  __shared__ double wpart[kBMaxWarps * kBMaxParams];
-  __shared__ double red[kBMaxWarps];
+  __shared__ double wpart[(MAXT / 32) * kBMaxParams];
+  __shared__ double red[MAXT / 32];
   __shared__ int s_item;
   const int nwarps = blockDim.x >> 5;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -361,6 +411,7 @@ __global__ void __launch_bounds__(512) kbatch(const BatchArgs A) {
 struct sv_batch_s {
   int n_items = 0, nmax = 0, total_params = 0;
   int k = 4, threads = 256, blocks = 0;  // chosen tile
+  int sms = 152;
   // device buffers
   sv::BCirc* circs = nullptr;
   sv::BGateDesc* gates = nullptr;
@@ -454,6 +505,14 @@ bool plan_circuit(const sv_circuit* c, const sv_pauli_sum* H, int k, HostPlan* P
       op.b0 = (uint8_t)local(n - 1 - g.targets[0]);
       for (int t = 0; t < g.n_ctrl; ++t) op.cm |= (uint8_t)(1 << local(n - 1 - g.controls[t]));
       op.pauli = g.param >= 0 ? (g.kind == SV_GATE_RX ? 1 : g.kind == SV_GATE_RY ? 2 : 3) : 0;
+      switch (g.kind) {
+        case SV_GATE_H: case SV_GATE_X: case SV_GATE_RY: op.cls = BC_REAL; break;
+        case SV_GATE_Y: case SV_GATE_RX: op.cls = BC_IMOFF; break;
+        case SV_GATE_RZ: op.cls = BC_DIAG; break;
+        case SV_GATE_Z: op.cls = BC_NEG; break;
+        case SV_GATE_U1: op.cls = BC_PHASE; break;
+        default: op.cls = BC_DENSE;
+      }
       op.param = (int16_t)g.param;
       op.gi = (int16_t)j;
       P->ops.push_back(op);
@@ -491,8 +550,13 @@ void free_batch(sv_batch b) {
 }
 
 typedef void (*BatchKernel)(const BatchArgs);
-BatchKernel kernel_for(int k) {
-  return k == 2 ? kbatch<2> : k == 3 ? kbatch<3> : kbatch<4>;
+// Kernel variants by (group width, threads per block, resident blocks per
+// SM): more resident blocks need fewer registers and less shared memory.
+BatchKernel kernel_for(int k, int threads, int per_sm) {
+  if (threads >= 512) return k == 2 ? kbatch<2, 512, 1> : k == 3 ? kbatch<3, 512, 1> : kbatch<4, 512, 1>;
+  if (threads <= 128) return k == 2 ? kbatch<2, 128, 8> : kbatch<3, 128, 8>;
+  if (per_sm >= 4) return k == 2 ? kbatch<2, 256, 4> : kbatch<3, 256, 4>;
+  return k == 2 ? kbatch<2, 256, 2> : k == 3 ? kbatch<3, 256, 2> : kbatch<4, 256, 2>;
 }
 
 sv_status launch_batch(sv_batch b, const double* theta, double* energy, double* grad,
@@ -515,7 +579,7 @@ sv_status launch_batch(sv_batch b, const double* theta, double* energy, double* 
   A.queue = b->queue;
   SV_CUDA_TRY(cudaMemsetAsync(b->queue, 0, sizeof(int), st));
   ProfScope prof(st, "kbatch");
-  kernel_for(k)<<<blocks, threads, 0, st>>>(A);
+  kernel_for(k, threads, std::max(1, blocks / std::max(1, b->sms)))<<<blocks, threads, 0, st>>>(A);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   return check_launch("batch kernel");
 }
@@ -653,16 +717,17 @@ sv_status sv_batch_create(const sv_circuit* circuits, const sv_pauli_sum* hamilt
   };
   std::vector<Cand> cands;
   if (tune) {
-    for (int k : {2, 3, 4})
-      if (k >= width)
-      for (int t : {128, 256, 512})
-        for (int per : {1, 2, 4}) cands.push_back({k, t, per});
+    const Cand all[] = {{2, 512, 1}, {3, 512, 1}, {4, 512, 1}, {2, 256, 2}, {3, 256, 2},
+                        {4, 256, 2}, {2, 256, 4}, {3, 256, 4}, {2, 128, 8}, {3, 128, 8}};
+    for (const Cand& c : all)
+      if (c.k >= width) cands.push_back(c);
   } else {
     cands.push_back({std::max(4, width), 256, 2});
   }
   int max_per = 1;
   for (auto& c : cands) max_per = std::max(max_per, c.per_sm);
   b->work_slots = (size_t)sms * max_per;
+  b->sms = sms;
   sv_status st = SV_OK;
   // plans per k are built on demand; start with the device buffers that do not depend on k
   st = upload(&b->order, order);

@@ -29,6 +29,8 @@ constexpr int kFMaxGroups = 64;
 template <typename R>
 struct FOpDev {
   uint8_t type, b0, b1, cmask;  // group-local bit indices and control mask
+  uint8_t cls;                  // FG_1Q: MK_* arithmetic class; FG_PHASE: 1 if the phase is -1
+  uint8_t pad[3];
   R m[8];                       // FG_1Q: G00 G01 G10 G11 (re, im); FG_PHASE: m[0..1]
 };
 
@@ -69,21 +71,37 @@ __device__ __forceinline__ int swz<double>(int j) {
 __host__ __device__ constexpr int lowbit(int r) { return (r & 1) ? 0 : 1 + lowbit(r >> 1); }
 
 // ---- register-level gate application -------------------------------------------
-template <int KG, int B, typename R>
+// (a, b) <- G (a, b) on every register pair of group bit B; CTRL: only where
+// the group-local control mask is set; MK: arithmetic class of G.
+template <int KG, int B, int MK, bool CTRL, typename R>
 __device__ __forceinline__ void ap1(const FOpDev<R>& op, R (&re)[1 << KG], R (&im)[1 << KG]) {
   const int cm = op.cmask;
-  const R g0r = op.m[0], g0i = op.m[1], g1r = op.m[2], g1i = op.m[3];
-  const R g2r = op.m[4], g2i = op.m[5], g3r = op.m[6], g3i = op.m[7];
+  M2<R> g;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    g.r[e] = op.m[2 * e];
+    g.i[e] = op.m[2 * e + 1];
+  }
 #pragma unroll
   for (int r = 0; r < (1 << KG); ++r) {
     if (r & (1 << B)) continue;
+    if (CTRL && (r & cm) != cm) continue;
     const int r1 = r | (1 << B);
-    if ((r & cm) != cm) continue;
-    const R ar = re[r], ai = im[r], br = re[r1], bi = im[r1];
-    re[r] = g0r * ar - g0i * ai + g1r * br - g1i * bi;
-    im[r] = g0r * ai + g0i * ar + g1r * bi + g1i * br;
-    re[r1] = g2r * ar - g2i * ai + g3r * br - g3i * bi;
-    im[r1] = g2r * ai + g2i * ar + g3r * bi + g3i * br;
+    mv2<MK, R>(g, re[r], im[r], re[r1], im[r1]);
+  }
+}
+
+template <int KG, int B, typename R>
+__device__ __forceinline__ void ap1_cls(const FOpDev<R>& op, R (&re)[1 << KG], R (&im)[1 << KG]) {
+  if (op.cmask) {
+    ap1<KG, B, MK_DENSE, true>(op, re, im);
+    return;
+  }
+  switch (op.cls) {
+    case MK_REAL: ap1<KG, B, MK_REAL, false>(op, re, im); break;
+    case MK_IMOFF: ap1<KG, B, MK_IMOFF, false>(op, re, im); break;
+    case MK_DIAG: ap1<KG, B, MK_DIAG, false>(op, re, im); break;
+    default: ap1<KG, B, MK_DENSE, false>(op, re, im); break;
   }
 }
 
@@ -107,21 +125,30 @@ __device__ __forceinline__ void apply_op(const FOpDev<R>& op, R (&re)[1 << KG],
                                          R (&im)[1 << KG]) {
   if (op.type == FG_1Q) {
     switch (op.b0) {
-      case 0: ap1<KG, 0>(op, re, im); break;
-      case 1: if constexpr (KG > 1) ap1<KG, 1>(op, re, im); break;
-      case 2: if constexpr (KG > 2) ap1<KG, 2>(op, re, im); break;
-      case 3: if constexpr (KG > 3) ap1<KG, 3>(op, re, im); break;
-      default: if constexpr (KG > 4) ap1<KG, 4>(op, re, im); break;
+      case 0: ap1_cls<KG, 0>(op, re, im); break;
+      case 1: if constexpr (KG > 1) ap1_cls<KG, 1>(op, re, im); break;
+      case 2: if constexpr (KG > 2) ap1_cls<KG, 2>(op, re, im); break;
+      case 3: if constexpr (KG > 3) ap1_cls<KG, 3>(op, re, im); break;
+      default: if constexpr (KG > 4) ap1_cls<KG, 4>(op, re, im); break;
     }
   } else if (op.type == FG_PHASE) {
     const int cm = op.cmask;
-    const R c = op.m[0], s = op.m[1];
+    if (op.cls) {  // phase -1 (Z, CZ): a sign flip
 #pragma unroll
-    for (int r = 0; r < (1 << KG); ++r) {
-      if ((r & cm) != cm) continue;
-      const R xr = re[r], xi = im[r];
-      re[r] = c * xr - s * xi;
-      im[r] = s * xr + c * xi;
+      for (int r = 0; r < (1 << KG); ++r) {
+        if ((r & cm) != cm) continue;
+        re[r] = -re[r];
+        im[r] = -im[r];
+      }
+    } else {
+      const R c = op.m[0], s = op.m[1];
+#pragma unroll
+      for (int r = 0; r < (1 << KG); ++r) {
+        if ((r & cm) != cm) continue;
+        const R xr = re[r], xi = im[r];
+        re[r] = c * xr - s * xi;
+        im[r] = s * xr + c * xi;
+      }
     }
   } else {  // FG_SWAP, b0 < b1
     if constexpr (KG >= 2) {
@@ -148,10 +175,12 @@ __device__ __forceinline__ void run_group(typename Cplx2<R>::T* sm, int m, const
                                           const FOpDev<R>* ops, int o0, int o1) {
   typedef typename Cplx2<R>::T V2;
   constexpr int D = 1 << KG;
-  int off[D];
-  off[0] = 0;
+  // the swizzle is linear over XOR and b, off[r] have disjoint bits, so
+  // swz(b | off[r]) = swz(b) ^ swz(off[r]): one XOR per access
+  int soff[D];
+  soff[0] = 0;
 #pragma unroll
-  for (int r = 1; r < D; ++r) off[r] = off[r & (r - 1)] | (1 << gb[lowbit(r)]);
+  for (int r = 1; r < D; ++r) soff[r] = soff[r & (r - 1)] ^ swz<R>(1 << gb[lowbit(r)]);
   int lm[KG];
 #pragma unroll
   for (int i = 0; i < KG; ++i) lm[i] = (1 << gb[i]) - 1;
@@ -160,10 +189,11 @@ __device__ __forceinline__ void run_group(typename Cplx2<R>::T* sm, int m, const
     int b = s;
 #pragma unroll
     for (int i = 0; i < KG; ++i) b = ((b & ~lm[i]) << 1) | (b & lm[i]);
+    const int sb = swz<R>(b);
     R re[D], im[D];
 #pragma unroll
     for (int r = 0; r < D; ++r) {
-      const V2 v = sm[swz<R>(b | off[r])];
+      const V2 v = sm[sb ^ soff[r]];
       re[r] = v.x;
       im[r] = v.y;
     }
@@ -173,7 +203,7 @@ __device__ __forceinline__ void run_group(typename Cplx2<R>::T* sm, int m, const
       V2 v;
       v.x = re[r];
       v.y = im[r];
-      sm[swz<R>(b | off[r])] = v;
+      sm[sb ^ soff[r]] = v;
     }
   }
 }
@@ -234,8 +264,7 @@ __global__ void __launch_bounds__(kFThreads)
         case 1: run_group<1, R>(sm, P.m, gb, P.ops, o0, o1); break;
         case 2: run_group<2, R>(sm, P.m, gb, P.ops, o0, o1); break;
         case 3: run_group<3, R>(sm, P.m, gb, P.ops, o0, o1); break;
-        case 4: run_group<4, R>(sm, P.m, gb, P.ops, o0, o1); break;
-        default: run_group<5, R>(sm, P.m, gb, P.ops, o0, o1); break;
+        default: run_group<4, R>(sm, P.m, gb, P.ops, o0, o1); break;
       }
       __syncthreads();
     }
@@ -293,9 +322,21 @@ bool build_params(const FusedPass& pass, FusedParams<R>* P) {
       o.type = (uint8_t)f.type;
       o.b0 = o.b1 = 0;
       o.cmask = (uint8_t)glmask(f.cmask);
+      o.cls = 0;
+      o.pad[0] = o.pad[1] = o.pad[2] = 0;
       for (int e = 0; e < 8; ++e) o.m[e] = 0;
       if (f.type == FG_1Q) {
         o.b0 = (uint8_t)gl(f.t);
+        const cd* g = f.m;
+        auto z = [](cd x) { return x.re == 0.0 && x.im == 0.0; };
+        if (z(g[1]) && z(g[2]))
+          o.cls = MK_DIAG;
+        else if (g[0].im == 0 && g[1].im == 0 && g[2].im == 0 && g[3].im == 0)
+          o.cls = MK_REAL;
+        else if (g[0].im == 0 && g[3].im == 0 && g[1].re == 0 && g[2].re == 0)
+          o.cls = MK_IMOFF;
+        else
+          o.cls = MK_DENSE;
         for (int e = 0; e < 4; ++e) {
           o.m[2 * e] = (R)f.m[e].re;
           o.m[2 * e + 1] = (R)f.m[e].im;
@@ -303,6 +344,7 @@ bool build_params(const FusedPass& pass, FusedParams<R>* P) {
       } else if (f.type == FG_PHASE) {
         o.m[0] = (R)f.m[0].re;
         o.m[1] = (R)f.m[0].im;
+        o.cls = (f.m[0].re == -1.0 && f.m[0].im == 0.0) ? 1 : 0;
       } else {
         const int x = gl(f.a), y = gl(f.b);
         o.b0 = (uint8_t)std::min(x, y);

@@ -128,7 +128,7 @@ int local_of(const std::vector<int>& S, int bit) {
 
 FusionConfig fusion_config(int n, sv_dtype dt, int fuse_k) {
   FusionConfig c;
-  c.fuse_k = fuse_k;
+  c.fuse_k = std::min(fuse_k, 4);  // the pass kernel holds register groups of <= 4 qubits
   int m = std::min(n, dt == SV_C64 ? 13 : 12);
   // keep at least 2^8 blocks for mid-size states, down to 2^10 amplitudes
   if (n > 10) m = std::max(std::min(m, n - 8), std::min(n, 10));
