@@ -56,6 +56,8 @@ def lib():
         L.orc_apply.argtypes = [I, P, I, P, I, P, P]
         L.orc_run.argtypes = [I, P, I, P, P, P, P, P, P, P, P, P, P, I, D]
         L.orc_expval.argtypes = [I, P, I, P, P, P, P, P, P, P]
+        L.orc_probabilities.argtypes = [I, P, I, P, P]
+        L.orc_sample.argtypes = [I, P, I, P, I, P, P]
         L.orc_norm2.argtypes = [I, P]
         L.orc_norm2.restype = D
         L.orc_dot.argtypes = [I, P, P, P, P]
@@ -155,6 +157,29 @@ def apply_gate(psi: np.ndarray, n: int, targets: Sequence[int],
                          _ptr(cc), _ptr(g))
     if rc:
         raise ValueError("oracle rejected the gate")
+    return out
+
+
+def probabilities(psi: np.ndarray, qubits: Sequence[int]) -> np.ndarray:
+    """P(outcome) of measuring `qubits` (qubits[0] = most significant bit)."""
+    n = int(psi.size).bit_length() - 1
+    a = np.ascontiguousarray(psi, np.complex128)
+    q = np.ascontiguousarray(qubits, np.int32)
+    out = np.zeros(1 << len(q))
+    if lib().orc_probabilities(n, _ptr(a), len(q), _ptr(q), _ptr(out)):
+        raise ValueError("oracle rejected the measurement")
+    return out
+
+
+def sample(psi: np.ndarray, qubits: Sequence[int], uniforms: Sequence[float]) -> np.ndarray:
+    """Inverse-CDF samples of `qubits` for the given uniforms in [0, 1)."""
+    n = int(psi.size).bit_length() - 1
+    a = np.ascontiguousarray(psi, np.complex128)
+    q = np.ascontiguousarray(qubits, np.int32)
+    u = np.ascontiguousarray(uniforms, np.float64)
+    out = np.zeros(len(u), np.uint64)
+    if lib().orc_sample(n, _ptr(a), len(q), _ptr(q), len(u), _ptr(u), _ptr(out)):
+        raise ValueError("oracle rejected the sampling request")
     return out
 
 

@@ -216,3 +216,47 @@ int orc_expval(int n, const cplx* psi, int nterms, const double* coeff,
   *energy = e;
   return 0;
 }
+
+/* Measurement in the computational basis (Sec. 3: sampling of measurements).
+ * The measured qubits q_0..q_{m-1} form the outcome r = sum_j b(q_j) 2^(m-1-j)
+ * (q_0 the most significant bit), and P(r) = sum of |psi_x|^2 over every x
+ * whose measured bits spell r. */
+int orc_probabilities(int n, const cplx* psi, int m, const int* qubits, double* out) {
+  if (m < 1 || m > n) return 1;
+  for (int r = 0; r < (1 << m); ++r) out[r] = 0.0;
+  for (uint64_t x = 0; x < (1ull << n); ++x) {
+    int r = 0;
+    for (int j = 0; j < m; ++j) r = (r << 1) | (int)((x >> (n - 1 - qubits[j])) & 1);
+    out[r] += creal(psi[x]) * creal(psi[x]) + cimag(psi[x]) * cimag(psi[x]);
+  }
+  return 0;
+}
+
+/* Inverse-CDF sampling: with c(x) = sum_{y <= x} |psi_y|^2 (ascending x, fp64)
+ * and total = c(2^n - 1), shot s takes the smallest x with c(x) > u_s * total
+ * for the given uniform u_s in [0, 1) and reports its measured bits. */
+int orc_sample(int n, const cplx* psi, int m, const int* qubits, int nshots,
+               const double* u, uint64_t* out) {
+  if (m < 1 || m > n || n > 30) return 1;
+  const uint64_t dim = 1ull << n;
+  double* cdf = (double*)malloc(sizeof(double) * dim);
+  if (!cdf) return 2;
+  double acc = 0.0;
+  for (uint64_t x = 0; x < dim; ++x) {
+    acc += creal(psi[x]) * creal(psi[x]) + cimag(psi[x]) * cimag(psi[x]);
+    cdf[x] = acc;
+  }
+  for (int s = 0; s < nshots; ++s) {
+    const double t = u[s] * acc;
+    uint64_t lo = 0, hi = dim - 1;  /* smallest x with cdf[x] > t */
+    while (lo < hi) {
+      uint64_t mid = lo + (hi - lo) / 2;
+      if (cdf[mid] > t) hi = mid; else lo = mid + 1;
+    }
+    uint64_t r = 0;
+    for (int j = 0; j < m; ++j) r = (r << 1) | ((lo >> (n - 1 - qubits[j])) & 1);
+    out[s] = r;
+  }
+  free(cdf);
+  return 0;
+}

@@ -320,3 +320,52 @@ def test_pins_catch_planted_mistakes(mutant):
     finally:
         oracle.set_mutant(0)
     assert _pin_battery()
+
+
+# --------------------------------------------------------------------------
+# measurement (Sec. 3: sampling of measurements)
+def test_probabilities_against_numpy_marginals():
+    n = 7
+    psi = W.random_state(n, 31)
+    p = np.abs(psi.reshape([2] * n)) ** 2          # axis q <-> qubit q (qubit 0 = MSB)
+    for qubits in ([0], [6], [2, 5], [5, 2], [0, 3, 6], list(range(n)), [4, 1, 6, 0]):
+        rest = tuple(q for q in range(n) if q not in qubits)
+        marg = p.sum(axis=rest) if rest else p
+        order = sorted(qubits)
+        ref = np.transpose(marg, [order.index(q) for q in qubits]).reshape(-1)
+        got = oracle.probabilities(psi, qubits)
+        assert np.max(np.abs(got - ref)) < 1e-15
+    assert abs(oracle.probabilities(psi, [3]).sum() - 1) < 1e-14
+
+
+def test_probabilities_closed_forms():
+    bell = oracle.run(W.Circuit(2, [W.Gate("H", (0,)), W.Gate("X", (1,), (0,))], 0))
+    assert np.allclose(oracle.probabilities(bell, [0, 1]), [0.5, 0, 0, 0.5], atol=1e-15)
+    # RY(a)|0>: P(1) = sin^2(a/2)
+    a = 1.234
+    psi = oracle.run(W.Circuit(1, [W.Gate("RY", (0,), (), -1, a)], 0))
+    assert abs(oracle.probabilities(psi, [0])[1] - np.sin(a / 2) ** 2) < 1e-15
+
+
+def test_sampling_against_numpy_searchsorted():
+    n = 9
+    psi = W.random_state(n, 32)
+    u = W.uniform_block(77, 0, 5000)
+    cdf = np.cumsum(np.abs(psi) ** 2)
+    full = np.searchsorted(cdf, u * cdf[-1], side="right")
+    got = oracle.sample(psi, list(range(n)), u)
+    assert np.array_equal(got.astype(np.int64), full)
+    # a subset is the projection of the full outcome: qubits (5, 0) -> 2 bits
+    sub = oracle.sample(psi, [5, 0], u)
+    ref = ((full >> (n - 1 - 5)) & 1) * 2 + ((full >> (n - 1 - 0)) & 1)
+    assert np.array_equal(sub.astype(np.int64), ref)
+
+
+def test_sampling_frequencies_follow_probabilities():
+    n = 5
+    psi = W.random_state(n, 33)
+    u = W.uniform_block(78, 0, 200000)
+    s = oracle.sample(psi, [1, 3], u).astype(np.int64)
+    freq = np.bincount(s, minlength=4) / len(u)
+    p = oracle.probabilities(psi, [1, 3])
+    assert np.max(np.abs(freq - p)) < 5 * np.sqrt(0.25 / len(u))
