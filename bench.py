@@ -304,6 +304,32 @@ def batch_solves(torch, reps=5):
     return out
 
 
+def sampling(torch, h, n, shots=1 << 20):
+    """Measurement of all n qubits of the QFT state already in `h`: 2^20 shots
+    from seeded uniforms (inverse CDF), and the probabilities of 3 qubits."""
+    import workloads as W
+    from paper_2202_07017_gb300 import (sv_probabilities, sv_profile_start, sv_profile_stop,
+                                        sv_sample)
+    u = W.uniform_block(4242, 0, shots)
+    q = list(range(n))
+    sv_sample(h, q, u[:1024])
+    torch.cuda.synchronize()
+    sv_profile_start()
+    t0 = time.perf_counter()
+    sv_sample(h, q, u)
+    t1 = time.perf_counter()
+    sv_probabilities(h, [0, 1, 2])
+    prof = sv_profile_stop()
+    cnt, ms = prof.get("kchunk_sums", (1, float("nan")))
+    pcnt, pms = prof.get("kprob_slices", (1, float("nan")))
+    return {"workload": f"qft n={n} complex64 state, {shots} shots of all qubits "
+                        "(inverse CDF, uniforms from the host)",
+            "sample_s": t1 - t0, "shots_per_s": shots / (t1 - t0),
+            "chunk_sum_gbs": 8 * 2 ** n / (ms / cnt / 1e3) / 1e9,
+            "probabilities_gbs": 8 * 2 ** n / (pms / pcnt / 1e3) / 1e9,
+            "kernels_ms": {k: v[1] for k, v in prof.items()}}
+
+
 def gate_table(n, dtype, reps=5):
     """Per-kernel bandwidth for single gates on every kind of bit position:
     H on bit p, controlled-U1 on bits (a, b), SWAP on (a, b).  Algorithmic
@@ -479,6 +505,7 @@ def main():
                    "ms_per_step": 1e3 * float(np.median(ts)),
                    "path": "sv_upload (pinned host) + sv_apply_circuit + sv_download"}
             del host, hv
+        meas = sampling(torch, h, n)
         adj = adjoint_ratio(torch)
         fused = None if args.no_fused else fused_layered(torch, n=args.fused_n)
         batch = None if args.no_batch else batch_solves(torch)
@@ -517,6 +544,7 @@ def main():
             "fused": fused,
             "batch": batch,
             "adjoint_n28": adj28,
+            "measure": meas,
         }
     sv_free(h)
     if out is not None:

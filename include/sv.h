@@ -226,6 +226,27 @@ sv_status sv_expval_noalloc(const void* dev_state, int n_qubits, sv_dtype dtype,
  * in and out must be distinct handles of equal n and dtype. Asynchronous. */
 sv_status sv_apply_pauli_sum(sv_state out, sv_state in, const sv_pauli_sum* H);
 
+/* ---- measurement (Sec. 3: sampling of measurements) -------------------- */
+
+/* Measuring qubits[0..n_meas-1] in the computational basis gives outcome
+ * r = sum_j b(qubits[j]) 2^(n_meas-1-j) (qubits[0] the most significant
+ * bit) with P(r) = sum of |psi_x|^2 over the x whose measured bits spell r.
+ *
+ * sv_probabilities writes P(0..2^n_meas-1) to the host array `out` (fp64
+ * sums in a fixed order; n_meas <= SV_MAX_MEASURE_PROBS); synchronises.
+ *
+ * sv_sample draws n_shots outcomes by the inverse CDF
+ * c(x) = sum_{y <= x} |psi_y|^2: shot s is the first x with
+ * c(x) > uniforms[s] * c(2^n - 1), projected onto the measured qubits.
+ * uniforms (host, in [0, 1)) are the caller's random numbers; out (host,
+ * n_shots) receives the outcomes; synchronises.  The state is not
+ * collapsed.  Errors: SV_ERR_INVALID (bad qubits, counts, uniforms). */
+#define SV_MAX_MEASURE_PROBS 24
+#define SV_MAX_SHOTS (1LL << 26)
+sv_status sv_probabilities(sv_state s, const int* qubits, int n_meas, double* out);
+sv_status sv_sample(sv_state s, const int* qubits, int n_meas, int64_t n_shots,
+                    const double* uniforms, uint64_t* out);
+
 /* ---- gradients --------------------------------------------------------- */
 
 /* Adjoint gradient of E(theta) = <psi_N|H|psi_N>, psi_N = U(theta) psi_0

@@ -54,6 +54,7 @@ EXPORTS = ("sv_alloc", "sv_wrap", "sv_free", "sv_set_stream", "sv_info", "sv_ini
            "sv_norm", "sv_expval", "sv_expval_async", "sv_apply_pauli_sum", "sv_adjoint",
            "sv_grad", "sv_sync", "sv_last_error", "sv_launch_count", "sv_version",
            "sv_profile_start", "sv_profile_stop", "sv_fusion_plan", "sv_expval_noalloc",
+           "sv_probabilities", "sv_sample",
            "sv_batch_create", "sv_batch_plan", "sv_batch_info", "sv_batch_run", "sv_batch_run_graph", "sv_batch_grad",
            "sv_batch_free")
 
@@ -97,6 +98,8 @@ def load(build: bool = True):
                     P(c_dbl), P(c_dbl)],
         "sv_sync": [c_vp],
         "sv_profile_start": [],
+        "sv_probabilities": [c_vp, P(ctypes.c_int), ctypes.c_int, P(c_dbl)],
+        "sv_sample": [c_vp, P(ctypes.c_int), ctypes.c_int, c_i64, P(c_dbl), P(c_u64)],
         "sv_batch_create": [P(SvCircuit), P(SvPauliSum), ctypes.c_int, P(c_i32), ctypes.c_int,
                             ctypes.c_int, P(c_vp)],
         "sv_batch_plan": [P(SvCircuit), P(SvPauliSum), ctypes.c_int, ctypes.c_int, P(c_i32)],
@@ -281,6 +284,24 @@ def sv_fusion_plan(circuit, theta=None, dtype: int = C64, fuse_k: int = 4):
     masks = [(int(staged[2 * i]) & 0xffffffff) | ((int(staged[2 * i + 1]) & 0xffffffff) << 32)
              for i in range(p)]
     return order[:pc.n_gates], pass_of[:pc.n_gates], p, masks
+
+
+def sv_probabilities(h: int, qubits: Sequence[int]) -> np.ndarray:
+    q = (ctypes.c_int * max(1, len(qubits)))(*qubits)
+    out = np.zeros(1 << len(qubits), np.float64)
+    _check(load().sv_probabilities(c_vp(h), q, len(qubits),
+                                   out.ctypes.data_as(ctypes.POINTER(c_dbl))))
+    return out
+
+
+def sv_sample(h: int, qubits: Sequence[int], uniforms) -> np.ndarray:
+    q = (ctypes.c_int * max(1, len(qubits)))(*qubits)
+    u = np.ascontiguousarray(uniforms, dtype=np.float64)
+    out = np.zeros(max(1, len(u)), np.uint64)
+    _check(load().sv_sample(c_vp(h), q, len(qubits), len(u),
+                            u.ctypes.data_as(ctypes.POINTER(c_dbl)),
+                            out.ctypes.data_as(ctypes.POINTER(c_u64))))
+    return out[:len(u)]
 
 
 def sv_norm(h: int) -> float:
