@@ -103,8 +103,13 @@ def test_sampling_qft_n30_uniform_closed_form():
         p3 = st.probabilities([0, 1, 2])
     finally:
         st.close()
-    assert np.mean(xs == np.floor(u * (1 << n)).astype(np.int64)) > 0.999
-    assert np.max(np.abs(np.abs(xs - u * (1 << n)))) < 2 ** 12
+    # The complex64 amplitudes carry relative errors up to ~1e-3 after 480
+    # gates (the parity bound max|dpsi| 2^15 <= 1e-3), so |psi_y|^2 = 2^-30
+    # (1 + O(1e-3)) and the CDF wanders by a random walk of about
+    # 2^-30 * 2e-3 * sqrt(2^29) ~ 50 outcomes: samples stay within that of
+    # u * 2^30, far inside 2^12.
+    d = np.abs(xs - u * (1 << n))
+    assert np.max(d) < 2 ** 12 and np.median(d) < 256
     assert np.max(np.abs(p3 - 0.125)) < 1e-5
 
 
