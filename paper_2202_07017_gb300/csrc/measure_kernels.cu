@@ -43,21 +43,51 @@ __global__ void __launch_bounds__(kRedThreads)
   const uint64_t len = (per_bin + slices - 1) / slices;
   const uint64_t e0 = (uint64_t)c * len, e1 = e0 + len < per_bin ? e0 + len : per_bin;
   double acc = 0.0;
-  for (uint64_t e = e0 + threadIdx.x; e < e1; e += kRedThreads)
-    acc += prob(psi[insert_zeros(e, rest) | rbits]);
+  constexpr int U = 8;  // loads in flight per thread
+  for (uint64_t e = e0 + threadIdx.x; e < e1; e += (uint64_t)kRedThreads * U) {
+    T2 v[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      const uint64_t ek = e + (uint64_t)k * kRedThreads;
+      if (ek < e1) v[k] = psi[insert_zeros(ek, rest) | rbits];
+    }
+#pragma unroll
+    for (int k = 0; k < U; ++k)
+      if (e + (uint64_t)k * kRedThreads < e1) acc += prob(v[k]);
+  }
   acc = block_sum(acc);
   if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
 
-// sums[k] = sum of |psi|^2 over chunk k
-template <typename T2>
+// sums[k] = sum of |psi|^2 over chunk k (2^cbits amplitudes): one warp per
+// chunk, 16-byte loads, a fixed shuffle tree per chunk.
+__device__ __forceinline__ double prob4(const float4 a) {
+  return (double)a.x * a.x + (double)a.y * a.y + ((double)a.z * a.z + (double)a.w * a.w);
+}
+__device__ __forceinline__ double prob4(const double2 a) { return a.x * a.x + a.y * a.y; }
+
+template <typename V>
 __global__ void __launch_bounds__(kRedThreads)
-    kchunk_sums(const T2* __restrict__ psi, int cbits, double* __restrict__ sums) {
-  const uint64_t base = (uint64_t)blockIdx.x << cbits;
+    kchunk_sums(const V* __restrict__ psi, int vbits, uint64_t K, double* __restrict__ sums) {
+  const uint64_t k = (uint64_t)blockIdx.x * (kRedThreads / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (k >= K) return;
+  const V* c = psi + (k << vbits);
+  const int nv = 1 << vbits;  // vectors per chunk
   double acc = 0.0;
-  for (int i = threadIdx.x; i < (1 << cbits); i += kRedThreads) acc += prob(psi[base + i]);
-  acc = block_sum(acc);
-  if (threadIdx.x == 0) sums[blockIdx.x] = acc;
+  constexpr int U = 16;
+  for (int i0 = lane; i0 < nv; i0 += 32 * U) {
+    V v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (i0 + 32 * u < nv) v[u] = c[i0 + 32 * u];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (i0 + 32 * u < nv) acc += prob4(v[u]);
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) sums[k] = acc;
 }
 
 // inclusive prefix sums in place, one block of 1024 threads, fixed order
@@ -85,12 +115,15 @@ __global__ void __launch_bounds__(1024) kscan(double* __restrict__ v, uint64_t K
   for (uint64_t i = a; i < b; ++i) v[i] += off;
 }
 
+// One warp per shot: binary search over the chunk prefixes, then the chunk
+// is scanned 32 amplitudes at a time with a warp prefix sum.
 template <typename T2>
 __global__ void __launch_bounds__(kRedThreads)
     kshots(const T2* __restrict__ psi, int n, int cbits, const double* __restrict__ prefix,
            uint64_t K, const double* __restrict__ u, int64_t nshots,
            const int* __restrict__ mpos, int m, uint64_t* __restrict__ out) {
-  const int64_t s = (int64_t)blockIdx.x * kRedThreads + threadIdx.x;
+  const int64_t s = (int64_t)blockIdx.x * (kRedThreads / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
   if (s >= nshots) return;
   const double total = prefix[K - 1];
   const double t = u[s] * total;
@@ -101,22 +134,34 @@ __global__ void __launch_bounds__(kRedThreads)
   }
   double acc = lo ? prefix[lo - 1] : 0.0;
   const uint64_t base = lo << cbits;
-  uint64_t x = base, last_nonzero = base;
+  const int len = 1 << cbits;
+  uint64_t x = base;
+  int last_nonzero = -1;
   bool found = false;
-  for (uint64_t i = 0; i < (uint64_t(1) << cbits); ++i) {
-    const double p = prob(psi[base + i]);
-    if (p > 0.0) last_nonzero = base + i;
-    acc += p;
-    if (acc > t) {
-      x = base + i;
-      found = true;
-      break;
+  for (int i0 = 0; i0 < len && !found; i0 += 32) {
+    const int i = i0 + lane;
+    const double p = i < len ? prob(psi[base + i]) : 0.0;
+    double incl = p;  // warp inclusive scan
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const double y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
     }
+    const unsigned nz = __ballot_sync(0xffffffffu, p > 0.0);
+    if (nz) last_nonzero = i0 + 31 - __clz(nz);
+    const unsigned over = __ballot_sync(0xffffffffu, acc + incl > t);
+    if (over) {
+      x = base + i0 + (__ffs(over) - 1);
+      found = true;
+    }
+    acc += __shfl_sync(0xffffffffu, incl, 31);
   }
-  if (!found) x = last_nonzero;  // t at the very top after rounding
-  uint64_t r = 0;
-  for (int j = 0; j < m; ++j) r = (r << 1) | ((x >> mpos[j]) & 1);
-  out[s] = r;
+  if (!found) x = base + (last_nonzero >= 0 ? last_nonzero : 0);  // t at the top after rounding
+  if (lane == 0) {
+    uint64_t r = 0;
+    for (int j = 0; j < m; ++j) r = (r << 1) | ((x >> mpos[j]) & 1);
+    out[s] = r;
+  }
 }
 
 }  // namespace
@@ -200,7 +245,7 @@ sv_status sv_sample(sv_state s, const int* qubits, int n_meas, int64_t n_shots,
     }
   if (n_shots == 0) return SV_OK;
   const int n = s->n, m = n_meas;
-  const int cbits = std::min(n, kChunkBits);
+  const int cbits = std::max(1, std::min(n, kChunkBits));
   const uint64_t K = uint64_t(1) << (n - cbits);
   int mpos[64];
   for (int j = 0; j < m; ++j) mpos[j] = n - 1 - qubits[j];
@@ -217,12 +262,13 @@ sv_status sv_sample(sv_state s, const int* qubits, int n_meas, int64_t n_shots,
                               s->stream));
   {
     ProfScope prof(s->stream, "kchunk_sums");
-    if (s->dt == SV_C64)
-      kchunk_sums<float2><<<(unsigned)K, kRedThreads, 0, s->stream>>>((const float2*)s->data,
-                                                                        cbits, prefix);
+    const unsigned g = (unsigned)((K + kRedThreads / 32 - 1) / (kRedThreads / 32));
+    if (s->dt == SV_C64)  // 2 amplitudes per 16-byte vector
+      kchunk_sums<float4><<<g, kRedThreads, 0, s->stream>>>((const float4*)s->data, cbits - 1,
+                                                            K, prefix);
     else
-      kchunk_sums<double2><<<(unsigned)K, kRedThreads, 0, s->stream>>>((const double2*)s->data,
-                                                                         cbits, prefix);
+      kchunk_sums<double2><<<g, kRedThreads, 0, s->stream>>>((const double2*)s->data, cbits, K,
+                                                             prefix);
     g_launches.fetch_add(1, std::memory_order_relaxed);
   }
   {
@@ -232,7 +278,7 @@ sv_status sv_sample(sv_state s, const int* qubits, int n_meas, int64_t n_shots,
   }
   {
     ProfScope prof(s->stream, "kshots");
-    const unsigned g = (unsigned)((n_shots + kRedThreads - 1) / kRedThreads);
+    const unsigned g = (unsigned)((n_shots + kRedThreads / 32 - 1) / (kRedThreads / 32));
     if (s->dt == SV_C64)
       kshots<float2><<<g, kRedThreads, 0, s->stream>>>((const float2*)s->data, n, cbits, prefix, K,
                                                        du, n_shots, dpos, m, dout);
