@@ -58,6 +58,8 @@ def lib():
         L.orc_expval.argtypes = [I, P, I, P, P, P, P, P, P, P]
         L.orc_probabilities.argtypes = [I, P, I, P, P]
         L.orc_sample.argtypes = [I, P, I, P, I, P, P]
+        L.orc_sample_exact.argtypes = [I, P, I, P, I, P, P]
+        L.orc_exact_total.argtypes = [I, P, P, P]
         L.orc_norm2.argtypes = [I, P]
         L.orc_norm2.restype = D
         L.orc_dot.argtypes = [I, P, P, P, P]
@@ -181,6 +183,28 @@ def sample(psi: np.ndarray, qubits: Sequence[int], uniforms: Sequence[float]) ->
     if lib().orc_sample(n, _ptr(a), len(q), _ptr(q), len(u), _ptr(u), _ptr(out)):
         raise ValueError("oracle rejected the sampling request")
     return out
+
+
+def sample_exact(psi: np.ndarray, qubits: Sequence[int], uniforms: Sequence[float]) -> np.ndarray:
+    """Inverse-CDF samples with the exact fixed-point CDF: q(v) = floor(v^2 2^120)
+    per real component, 128-bit integer sums, T = floor(u * total)."""
+    n = int(psi.size).bit_length() - 1
+    a = np.ascontiguousarray(psi, np.complex128)
+    q = np.ascontiguousarray(qubits, np.int32)
+    u = np.ascontiguousarray(uniforms, np.float64)
+    out = np.zeros(len(u), np.uint64)
+    if lib().orc_sample_exact(n, _ptr(a), len(q), _ptr(q), len(u), _ptr(u), _ptr(out)):
+        raise ValueError("oracle rejected the sampling request")
+    return out
+
+
+def exact_total(psi: np.ndarray) -> int:
+    """sum over amplitudes of floor(re^2 2^120) + floor(im^2 2^120)."""
+    n = int(psi.size).bit_length() - 1
+    a = np.ascontiguousarray(psi, np.complex128)
+    hi, lo = ctypes.c_uint64(), ctypes.c_uint64()
+    lib().orc_exact_total(n, _ptr(a), ctypes.byref(hi), ctypes.byref(lo))
+    return (hi.value << 64) | lo.value
 
 
 def norm2(psi: np.ndarray) -> float:

@@ -260,3 +260,74 @@ int orc_sample(int n, const cplx* psi, int m, const int* qubits, int nshots,
   free(cdf);
   return 0;
 }
+
+/* Exact sampling.  Each amplitude contributes q(re) + q(im) with
+ * q(v) = floor(v^2 * 2^120), an integer computed exactly from v's binary
+ * significand and exponent; cumulative sums of q are exact 128-bit
+ * integers, so the CDF does not depend on summation order.  A shot with
+ * uniform u in [0, 1) takes T = floor(u * total) (exact) and the smallest x
+ * whose cumulative sum exceeds T.  Requires sum |psi|^2 < 256. */
+typedef unsigned __int128 u128;
+
+static u128 q120(double v) {
+  if (v == 0.0) return 0;
+  int e;
+  double f = frexp(fabs(v), &e);                 /* |v| = f 2^e, f in [0.5, 1) */
+  uint64_t m = (uint64_t)ldexp(f, 53);           /* exact 53-bit significand */
+  int sh = 2 * (e - 53) + 120;                   /* v^2 2^120 = m^2 2^sh */
+  u128 m2 = (u128)m * m;                         /* < 2^106 */
+  if (sh >= 0) return sh >= 22 ? (m2 << 22) << (sh - 22) : m2 << sh;
+  return -sh >= 128 ? 0 : m2 >> -sh;
+}
+
+/* floor(u * t) for u in [0, 1) and t < 2^128, exactly */
+static u128 frac_mul(double u, u128 t) {
+  if (u <= 0.0) return 0;
+  int e;
+  double f = frexp(u, &e);
+  uint64_t m = (uint64_t)ldexp(f, 53);           /* u = m 2^(e - 53), e <= 0 */
+  const int s = 53 - e;                          /* >= 53 */
+  const uint64_t t_hi = (uint64_t)(t >> 64), t_lo = (uint64_t)t;
+  const u128 a = (u128)m * t_lo, b = (u128)m * t_hi;   /* m t = b 2^64 + a */
+  /* (b 2^64 + a) >> s with a 192-bit intermediate */
+  u128 lo = a + ((u128)(uint64_t)b << 64);
+  uint64_t top = (uint64_t)(b >> 64) + (lo < a ? 1 : 0);  /* bits 128..191 */
+  if (s >= 192) return 0;
+  if (s >= 128) return (u128)(top >> (s - 128));
+  if (s == 0) return lo;
+  return (lo >> s) | ((u128)top << (128 - s));
+}
+
+int orc_sample_exact(int n, const cplx* psi, int m, const int* qubits, int nshots,
+                     const double* u, uint64_t* out) {
+  if (m < 1 || m > n || n > 30) return 1;
+  const uint64_t dim = 1ull << n;
+  u128* cdf = (u128*)malloc(sizeof(u128) * dim);
+  if (!cdf) return 2;
+  u128 acc = 0;
+  for (uint64_t x = 0; x < dim; ++x) {
+    acc += q120(creal(psi[x])) + q120(cimag(psi[x]));
+    cdf[x] = acc;
+  }
+  for (int s = 0; s < nshots; ++s) {
+    const u128 T = frac_mul(u[s], acc);
+    uint64_t lo = 0, hi = dim - 1;  /* smallest x with cdf[x] > T */
+    while (lo < hi) {
+      uint64_t mid = lo + (hi - lo) / 2;
+      if (cdf[mid] > T) hi = mid; else lo = mid + 1;
+    }
+    uint64_t r = 0;
+    for (int j = 0; j < m; ++j) r = (r << 1) | ((lo >> (n - 1 - qubits[j])) & 1);
+    out[s] = r;
+  }
+  free(cdf);
+  return 0;
+}
+
+/* The exact total sum_x q(re) + q(im) as (hi, lo) 64-bit halves. */
+void orc_exact_total(int n, const cplx* psi, uint64_t* hi, uint64_t* lo) {
+  u128 acc = 0;
+  for (uint64_t x = 0; x < (1ull << n); ++x) acc += q120(creal(psi[x])) + q120(cimag(psi[x]));
+  *hi = (uint64_t)(acc >> 64);
+  *lo = (uint64_t)acc;
+}

@@ -369,3 +369,32 @@ def test_sampling_frequencies_follow_probabilities():
     freq = np.bincount(s, minlength=4) / len(u)
     p = oracle.probabilities(psi, [1, 3])
     assert np.max(np.abs(freq - p)) < 5 * np.sqrt(0.25 / len(u))
+
+
+def _q120_exact(v: float) -> int:
+    """floor(v^2 * 2^120) with Python's exact rationals."""
+    from fractions import Fraction
+    f = Fraction(v)
+    return (f * f * (1 << 120)).__floor__()
+
+
+def test_exact_sampling_against_python_integers():
+    n = 8
+    for psi in (W.random_state(n, 34), W.random_state(n, 35).astype(np.complex64).astype(np.complex128)):
+        q = [_q120_exact(float(a.real)) + _q120_exact(float(a.imag)) for a in psi]
+        cdf = np.cumsum(np.array(q, dtype=object))
+        total = int(cdf[-1])
+        assert oracle.exact_total(psi) == total
+        from fractions import Fraction
+        u = list(W.uniform_block(79, 0, 3000)) + [0.0, 0.999999999999, 5e-324, 0.5]
+        ref = []
+        for uu in u:
+            T = (Fraction(float(uu)) * total).__floor__()
+            ref.append(next(i for i, c in enumerate(cdf) if c > T))
+        got = oracle.sample_exact(psi, list(range(n)), u)
+        assert got.astype(np.int64).tolist() == ref
+    # small and large magnitudes: exact squares across the exponent range
+    for v in (1.0, 0.5, 2.0 ** -60, 3.0e-20, 0.7071067811865476, 1.9999999999999998):
+        psi = np.zeros(2, np.complex128)
+        psi[0] = v
+        assert oracle.exact_total(psi) == _q120_exact(v)
