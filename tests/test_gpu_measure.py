@@ -1,10 +1,10 @@
 """GPU parity of measurement (Sec. 3: sampling of measurements): outcome
 probabilities of qubit subsets against the oracle, and inverse-CDF samples
-for the same uniforms against the oracle's CDF.  Several outcomes are
-correct when u * total falls within rounding of a CDF step, so each GPU
-sample is checked to lie on the oracle's CDF step that contains u * total
-(with a relative slack of 1e-12), and the samples are compared exactly
-elsewhere; at n = 30 the QFT's uniform distribution gives a closed form."""
+for the same uniforms.  Both sides decide outcomes with the exact
+fixed-point CDF (q(v) = floor(v^2 2^120), 128-bit integer sums), so the GPU
+samples must equal the oracle's exactly; they must also lie on the step of
+the oracle's fp64 CDF containing u * total (relative slack 1e-12).  At
+n = 30 the QFT's uniform distribution gives a closed form."""
 import math
 
 import numpy as np
@@ -80,8 +80,11 @@ def test_sampling_against_oracle_cdf(dtype, n):
     finally:
         st.close()
     assert _valid(psi, u, full)
+    # both sides decide with the exact fixed-point CDF: identical outcomes
+    exact = oracle.sample_exact(psi, list(range(n)), u).astype(np.int64)
+    assert np.array_equal(full, exact)
     ref = oracle.sample(psi, list(range(n)), u).astype(np.int64)
-    assert np.mean(full != ref) <= 1e-3          # differ only at rounding ties
+    assert np.mean(full != ref) <= 1e-3          # the fp64 CDF differs only at rounding ties
     proj = np.zeros_like(full)
     for q in sub_q:
         proj = (proj << 1) | ((full >> (n - 1 - q)) & 1)
