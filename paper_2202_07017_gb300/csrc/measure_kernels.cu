@@ -225,6 +225,43 @@ __global__ void __launch_bounds__(1024) kscan(U128* __restrict__ v, uint64_t K) 
   for (uint64_t i = a; i < b; ++i) v[i] = add128(v[i], off);
 }
 
+// Block-local inclusive scan of 1024 entries; the block's total goes to
+// totals[blockIdx.x].
+__global__ void __launch_bounds__(1024) kscan_local(U128* __restrict__ v, uint64_t K,
+                                                    U128* __restrict__ totals) {
+  __shared__ U128 ws[32];
+  const uint64_t i = (uint64_t)blockIdx.x * 1024 + threadIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  U128 x = i < K ? v[i] : U128{0, 0};
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const U128 y = {__shfl_up_sync(0xffffffffu, x.lo, o), __shfl_up_sync(0xffffffffu, x.hi, o)};
+    if (lane >= o) x = add128(x, y);
+  }
+  if (lane == 31) ws[w] = x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    U128 run = {0, 0};
+    for (int k = 0; k < 32; ++k) {
+      const U128 t = ws[k];
+      ws[k] = run;
+      run = add128(run, t);
+    }
+    totals[blockIdx.x] = run;
+  }
+  __syncthreads();
+  x = add128(x, ws[w]);
+  if (i < K) v[i] = x;
+}
+
+// v[i] += inclusive prefix of the totals of the blocks before i's block
+__global__ void __launch_bounds__(1024) kscan_add(U128* __restrict__ v, uint64_t K,
+                                                  const U128* __restrict__ scanned_totals) {
+  const uint64_t i = (uint64_t)blockIdx.x * 1024 + threadIdx.x;
+  if (blockIdx.x == 0 || i >= K) return;
+  v[i] = add128(v[i], scanned_totals[blockIdx.x - 1]);
+}
+
 // One warp per shot.
 template <typename T2>
 __global__ void __launch_bounds__(kRedThreads)
@@ -355,14 +392,17 @@ sv_status sv_sample(sv_state s, const int* qubits, int n_meas, int64_t n_shots,
   const uint64_t K = uint64_t(1) << (n - cbits);
   int mpos[64];
   for (int j = 0; j < m; ++j) mpos[j] = n - 1 - qubits[j];
-  // prefix[K] (2 doubles each), uniforms[n_shots], outcomes[n_shots], positions
-  const size_t need = 2 * K + 2 * (size_t)n_shots + 64;
+  // prefix[K] (2 doubles each), uniforms[n_shots], outcomes[n_shots], positions,
+  // block totals of the scan
+  const uint64_t nb = (K + 1023) / 1024;
+  const size_t need = 2 * K + 2 * (size_t)n_shots + 64 + 2 * nb;
   sv_status st = ensure_partials(s, need);
   if (st) return st;
   U128* prefix = reinterpret_cast<U128*>(s->partials);
   double* du = s->partials + 2 * K;
   uint64_t* dout = reinterpret_cast<uint64_t*>(du + n_shots);
   int* dpos = reinterpret_cast<int*>(dout + n_shots);
+  U128* btot = reinterpret_cast<U128*>(reinterpret_cast<double*>(dout + n_shots) + 64);
   SV_CUDA_TRY(cudaMemcpyAsync(dpos, mpos, sizeof(int) * m, cudaMemcpyHostToDevice, s->stream));
   SV_CUDA_TRY(cudaMemcpyAsync(du, uniforms, sizeof(double) * n_shots, cudaMemcpyHostToDevice,
                               s->stream));
@@ -379,8 +419,15 @@ sv_status sv_sample(sv_state s, const int* qubits, int n_meas, int64_t n_shots,
   }
   {
     ProfScope prof(s->stream, "kscan");
-    kscan<<<1, 1024, 0, s->stream>>>(prefix, K);
-    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (nb == 1) {
+      kscan<<<1, 1024, 0, s->stream>>>(prefix, K);
+      g_launches.fetch_add(1, std::memory_order_relaxed);
+    } else {
+      kscan_local<<<(unsigned)nb, 1024, 0, s->stream>>>(prefix, K, btot);
+      kscan<<<1, 1024, 0, s->stream>>>(btot, nb);
+      kscan_add<<<(unsigned)nb, 1024, 0, s->stream>>>(prefix, K, btot);
+      g_launches.fetch_add(3, std::memory_order_relaxed);
+    }
   }
   {
     ProfScope prof(s->stream, "kshots");
