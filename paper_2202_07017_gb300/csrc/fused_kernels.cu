@@ -209,8 +209,10 @@ __device__ __forceinline__ void run_group(typename Cplx2<R>::T* sm, int m, const
 }
 
 // ---- the pass kernel ------------------------------------------------------------
-template <typename R>
-__global__ void __launch_bounds__(kFThreads)
+// KGF: register-group width of every group of the pass (the planner pads
+// groups to it); 3 resident blocks per SM for complex64, 2 for complex128.
+template <typename R, int KGF>
+__global__ void __launch_bounds__(kFThreads, sizeof(R) == 4 ? 3 : 2)
     kfused(typename Cplx2<R>::T* __restrict__ psi, uint64_t n_blocks,
            const __grid_constant__ FusedParams<R> P) {
   typedef typename Cplx2<R>::T V2;
@@ -232,7 +234,7 @@ __global__ void __launch_bounds__(kFThreads)
   constexpr int LAPC = APC == 2 ? 1 : 0;
   const int lcr = L - LAPC;  // log2 chunks per run
   const int nch = M / APC;
-  constexpr int U = 8;
+  constexpr int U = 4;  // 16-byte loads in flight per thread while staging
   for (uint64_t blk = blockIdx.x; blk < n_blocks; blk += gridDim.x) {
     const uint64_t base = insert_zeros(blk, P.blk);
     for (int c0 = threadIdx.x; c0 < nch; c0 += kFThreads * U) {
@@ -260,12 +262,7 @@ __global__ void __launch_bounds__(kFThreads)
     for (int g = 0; g < P.ngroups; ++g) {
       const uint8_t* gb = P.gbits[g];
       const int o0 = P.gop[g], o1 = P.gop[g + 1];
-      switch (P.gk[g]) {
-        case 1: run_group<1, R>(sm, P.m, gb, P.ops, o0, o1); break;
-        case 2: run_group<2, R>(sm, P.m, gb, P.ops, o0, o1); break;
-        case 3: run_group<3, R>(sm, P.m, gb, P.ops, o0, o1); break;
-        default: run_group<4, R>(sm, P.m, gb, P.ops, o0, o1); break;
-      }
+      run_group<KGF, R>(sm, P.m, gb, P.ops, o0, o1);
       __syncthreads();
     }
     for (int c0 = threadIdx.x; c0 < nch; c0 += kFThreads * U) {
@@ -364,15 +361,23 @@ sv_status run_pass(void* data, int n, cudaStream_t st, const FusedPass& pass) {
     return SV_ERR_INVALID;
   }
   const size_t smem = (sizeof(R) * 2 << P.m) + (sizeof(uint64_t) << (P.m - P.L));
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(kfused<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_set = true;
+  const int kg = pass.groups.empty() ? 1 : pass.groups[0].k;
+  for (const FusedGroup& g : pass.groups)
+    if (g.k != kg) {
+      set_error("fused pass: groups of unequal width");
+      return SV_ERR_INVALID;
+    }
+  typedef void (*Kern)(typename Cplx2<R>::T*, uint64_t, const FusedParams<R>);
+  Kern kern = kg <= 1 ? kfused<R, 1> : kg == 2 ? kfused<R, 2> : kg == 3 ? kfused<R, 3> : kfused<R, 4>;
+  static bool attr_set[5] = {false, false, false, false, false};
+  if (!attr_set[kg]) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set[kg] = true;
   }
   const uint64_t nblk = uint64_t(1) << (n - P.m);
   const uint64_t grid = std::min<uint64_t>(nblk, 152 * 16);
   ProfScope prof(st, sizeof(R) == 4 ? "kfused_c64" : "kfused_c128");
-  kfused<R><<<(unsigned)grid, kFThreads, smem, st>>>(
+  kern<<<(unsigned)grid, kFThreads, smem, st>>>(
       reinterpret_cast<typename Cplx2<R>::T*>(data), nblk, P);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   return check_launch("fused pass kernel");

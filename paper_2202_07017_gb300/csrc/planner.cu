@@ -212,6 +212,13 @@ bool plan_fusion(const sv_circuit* c, const double* theta, const FusionConfig& c
           rest.push_back(j);
         }
       }
+      // pad every group to the same width (one kernel instantiation per
+      // pass; padded bits only widen the thread's tile)
+      const int width = std::min<int>(cfg.fuse_k, (int)P.S.size());
+      for (int b : P.S) {
+        if (popc(gq) >= width) break;
+        gq |= uint64_t(1) << b;
+      }
       FusedGroup grp;
       for (int b = 0; b < n; ++b)
         if ((gq >> b) & 1) grp.bits[grp.k++] = local_of(P.S, b);
