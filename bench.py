@@ -38,6 +38,22 @@ N_QFT = 30
 SEED_QFT = 1001
 
 
+def job_totals(secs: float, units: float, world: int, device: str = "cpu"):
+    """Whole-job timing over ranks: the slowest rank's seconds and the units
+    of all ranks (replicas: no data-path collective, only this aggregation).
+    Returns (max seconds, total units); world == 1 returns the inputs."""
+    if world <= 1:
+        return secs, units
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([secs], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.barrier()
+    return float(t.item()), float(u.item())
+
+
 def hbm_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -446,12 +462,8 @@ def main():
     launches = sv_launch_count() - l0
     clk = clocks.stop()
     secs = e0.elapsed_time(e1) / 1e3
-    if world > 1:
-        t = torch.tensor([secs], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.barrier()
-        secs = float(t.item())
-    value = world * n_gates * args.steps / secs
+    secs, units = job_totals(secs, n_gates * args.steps, world, "cuda")
+    value = units / secs
 
     # roofline of the dominant kernel, from the live per-launch events
     peak, peak_kind = hbm_peak()
