@@ -60,6 +60,7 @@ def lib():
         L.orc_sample.argtypes = [I, P, I, P, I, P, P]
         L.orc_sample_exact.argtypes = [I, P, I, P, I, P, P]
         L.orc_exact_total.argtypes = [I, P, P, P]
+        L.orc_pauli_rotation.argtypes = [I, P, I, P, P, D]
         L.orc_norm2.argtypes = [I, P]
         L.orc_norm2.restype = D
         L.orc_dot.argtypes = [I, P, P, P, P]
@@ -205,6 +206,35 @@ def exact_total(psi: np.ndarray) -> int:
     hi, lo = ctypes.c_uint64(), ctypes.c_uint64()
     lib().orc_exact_total(n, _ptr(a), ctypes.byref(hi), ctypes.byref(lo))
     return (hi.value << 64) | lo.value
+
+
+def pauli_rotation(psi: np.ndarray, term_ops, a: float) -> np.ndarray:
+    """exp(-i a P) psi for the Pauli string P = ((qubit, letter), ...)."""
+    n = int(psi.size).bit_length() - 1
+    out = np.array(psi, dtype=np.complex128, copy=True)
+    q = np.ascontiguousarray([t[0] for t in term_ops] or [0], np.int32)
+    L = np.ascontiguousarray([ord(t[1]) for t in term_ops] or [0], np.uint8)
+    if lib().orc_pauli_rotation(n, _ptr(out), len(term_ops), _ptr(q), _ptr(L), float(a)):
+        raise ValueError("oracle rejected the Pauli rotation")
+    return out
+
+
+def trotter(psi: np.ndarray, terms, t: float, steps: int, order: int = 1) -> np.ndarray:
+    """Trotter product for exp(-i t H), H = sum_k c_k P_k: per step of
+    dt = t / steps, first order applies exp(-i c_k dt P_k) for k = 1..K;
+    second order applies exp(-i c_k dt/2 P_k) for k = 1..K, then k = K..1."""
+    dt = t / steps
+    out = np.array(psi, dtype=np.complex128, copy=True)
+    for _ in range(steps):
+        if order == 1:
+            for c, ops in terms:
+                out = pauli_rotation(out, ops, c * dt)
+        else:
+            for c, ops in terms:
+                out = pauli_rotation(out, ops, 0.5 * c * dt)
+            for c, ops in reversed(terms):
+                out = pauli_rotation(out, ops, 0.5 * c * dt)
+    return out
 
 
 def norm2(psi: np.ndarray) -> float:

@@ -331,3 +331,29 @@ void orc_exact_total(int n, const cplx* psi, uint64_t* hi, uint64_t* lo) {
   *hi = (uint64_t)(acc >> 64);
   *lo = (uint64_t)acc;
 }
+
+/* exp(-i a P) psi for a Pauli string P (Sec. 3: Hamiltonians and time
+ * evolution with the Trotter decomposition).  Since P^2 = I,
+ * exp(-i a P) = cos(a) I - i sin(a) P; P psi is formed by applying the
+ * string's single-qubit factors to a copy of psi with orc_apply. */
+int orc_pauli_rotation(int n, cplx* psi, int nops, const int* qubits, const char* letters,
+                       double a) {
+  const uint64_t dim = 1ull << n;
+  cplx* phi = (cplx*)malloc(sizeof(cplx) * dim);
+  if (!phi) return 2;
+  memcpy(phi, psi, sizeof(cplx) * dim);
+  for (int j = 0; j < nops; ++j) {
+    cplx P[16];
+    const char L = letters[j];
+    const int kind = L == 'X' ? K_X : L == 'Y' ? K_Y : L == 'Z' ? K_Z : -1;
+    if (kind < 0) { free(phi); return 1; }
+    gate_matrix(kind, 0.0, P);
+    int q = qubits[j];
+    int rc = orc_apply(n, phi, 1, &q, 0, NULL, P);
+    if (rc) { free(phi); return rc; }
+  }
+  const double c = cos(a), s = sin(a);
+  for (uint64_t x = 0; x < dim; ++x) psi[x] = c * psi[x] - I * s * phi[x];
+  free(phi);
+  return 0;
+}

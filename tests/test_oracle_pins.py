@@ -398,3 +398,35 @@ def test_exact_sampling_against_python_integers():
         psi = np.zeros(2, np.complex128)
         psi[0] = v
         assert oracle.exact_total(psi) == _q120_exact(v)
+
+
+# --------------------------------------------------------------------------
+# Pauli rotations and Trotter evolution (Sec. 3: time evolution, Trotter)
+def test_pauli_rotation_against_expm():
+    n = 5
+    rng = W.SplitMix64(5)
+    psi = W.random_state(n, 40)
+    for c, ops in W.random_pauli_sum(n, 12, 41):
+        if not ops:
+            continue
+        a = 2 * np.pi * rng.uniform() - np.pi
+        P = pauli_operator(n, [(1.0, ops)])
+        ref = scipy.linalg.expm(-1j * a * P) @ psi
+        assert np.max(np.abs(oracle.pauli_rotation(psi, ops, a) - ref)) < 1e-13
+    # single-qubit cases are the rotation gates: exp(-i a X) = RX(2a)
+    ref = oracle.run(W.Circuit(n, [W.Gate("RX", (2,), (), -1, 1.1)], 0), None, psi)
+    assert np.max(np.abs(oracle.pauli_rotation(psi, ((2, "X"),), 0.55) - ref)) < 1e-14
+
+
+def test_trotter_exact_for_commuting_terms_and_converges_otherwise():
+    n = 4
+    psi = W.random_state(n, 42)
+    zz = [(0.8, ((i, "Z"), (i + 1, "Z"))) for i in range(n - 1)] + [(0.3, ((1, "Z"),))]
+    ref = scipy.linalg.expm(-1j * 0.9 * pauli_operator(n, zz)) @ psi
+    assert np.max(np.abs(oracle.trotter(psi, zz, 0.9, 3) - ref)) < 1e-13
+    H = W.tfim(n)
+    ref = scipy.linalg.expm(-1j * 0.7 * pauli_operator(n, H)) @ psi
+    e1 = [np.linalg.norm(oracle.trotter(psi, H, 0.7, s, 1) - ref) for s in (8, 16)]
+    e2 = [np.linalg.norm(oracle.trotter(psi, H, 0.7, s, 2) - ref) for s in (8, 16)]
+    assert 1.8 < e1[0] / e1[1] < 2.2      # first order: error ~ dt
+    assert 3.6 < e2[0] / e2[1] < 4.4      # second order: error ~ dt^2
