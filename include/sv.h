@@ -226,6 +226,21 @@ sv_status sv_expval_noalloc(const void* dev_state, int n_qubits, sv_dtype dtype,
  * in and out must be distinct handles of equal n and dtype. Asynchronous. */
 sv_status sv_apply_pauli_sum(sv_state out, sv_state in, const sv_pauli_sum* H);
 
+/* ---- Pauli rotations and time evolution (Sec. 3: Hamiltonians, Trotter) - */
+
+/* psi <- exp(-i theta P) psi for the Pauli string P = (xmask, zmask) (mask
+ * convention as in sv_pauli_sum); exp(-i theta P) = cos(theta) I -
+ * i sin(theta) P.  One HBM pass.  Asynchronous.  SV_ERR_INVALID for mask
+ * bits beyond n or a non-finite angle. */
+sv_status sv_pauli_rotation(sv_state s, uint64_t xmask, uint64_t zmask, double theta);
+
+/* psi <- (Trotter product for exp(-i t H)) psi, H = sum_k c_k P_k, with
+ * `steps` steps of dt = t / steps.  order 1: exp(-i c_k dt P_k) for
+ * k = 0..K-1 per step; order 2: exp(-i c_k dt/2 P_k) for k = 0..K-1 and
+ * then k = K-1..0 per step.  Runs of consecutive diagonal (Z-only) terms
+ * commute and are applied in one pass.  Asynchronous. */
+sv_status sv_trotter(sv_state s, const sv_pauli_sum* H, double t, int steps, int order);
+
 /* ---- measurement (Sec. 3: sampling of measurements) -------------------- */
 
 /* Measuring qubits[0..n_meas-1] in the computational basis gives outcome

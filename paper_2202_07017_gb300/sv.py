@@ -54,7 +54,7 @@ EXPORTS = ("sv_alloc", "sv_wrap", "sv_free", "sv_set_stream", "sv_info", "sv_ini
            "sv_norm", "sv_expval", "sv_expval_async", "sv_apply_pauli_sum", "sv_adjoint",
            "sv_grad", "sv_sync", "sv_last_error", "sv_launch_count", "sv_version",
            "sv_profile_start", "sv_profile_stop", "sv_fusion_plan", "sv_expval_noalloc",
-           "sv_probabilities", "sv_sample",
+           "sv_probabilities", "sv_sample", "sv_pauli_rotation", "sv_trotter",
            "sv_batch_create", "sv_batch_plan", "sv_batch_info", "sv_batch_run", "sv_batch_run_graph", "sv_batch_grad",
            "sv_batch_free")
 
@@ -98,6 +98,8 @@ def load(build: bool = True):
                     P(c_dbl), P(c_dbl)],
         "sv_sync": [c_vp],
         "sv_profile_start": [],
+        "sv_pauli_rotation": [c_vp, c_u64, c_u64, c_dbl],
+        "sv_trotter": [c_vp, P(SvPauliSum), c_dbl, ctypes.c_int, ctypes.c_int],
         "sv_probabilities": [c_vp, P(ctypes.c_int), ctypes.c_int, P(c_dbl)],
         "sv_sample": [c_vp, P(ctypes.c_int), ctypes.c_int, c_i64, P(c_dbl), P(c_u64)],
         "sv_batch_create": [P(SvCircuit), P(SvPauliSum), ctypes.c_int, P(c_i32), ctypes.c_int,
@@ -284,6 +286,18 @@ def sv_fusion_plan(circuit, theta=None, dtype: int = C64, fuse_k: int = 4):
     masks = [(int(staged[2 * i]) & 0xffffffff) | ((int(staged[2 * i + 1]) & 0xffffffff) << 32)
              for i in range(p)]
     return order[:pc.n_gates], pass_of[:pc.n_gates], p, masks
+
+
+def sv_pauli_rotation(h: int, term_ops, theta: float) -> None:
+    """psi <- exp(-i theta P), P = ((qubit, letter), ...)."""
+    pp = pack_pauli([(1.0, tuple(term_ops))], _n_of(h))
+    _check(load().sv_pauli_rotation(c_vp(h), c_u64(int(pp.x[0])), c_u64(int(pp.z[0])),
+                                    float(theta)))
+
+
+def sv_trotter(h: int, terms, t: float, steps: int, order: int = 1) -> None:
+    pp = pack_pauli(terms, _n_of(h))
+    _check(load().sv_trotter(c_vp(h), ctypes.byref(pp.s), float(t), int(steps), int(order)))
 
 
 def sv_probabilities(h: int, qubits: Sequence[int]) -> np.ndarray:
