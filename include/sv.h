@@ -76,13 +76,13 @@ enum {
 
 #define SV_MAX_QUBITS 34
 #define SV_MAX_TARGETS 5
-#define SV_MAX_CONTROLS 16
+#define SV_MAX_CONTROLS 33  /* n - 1 at the largest state */
 #define SV_MAX_PAULI_TERMS 4096
 
 typedef struct sv_state_s* sv_state;   /* opaque handle */
 
 /* One gate of a circuit (Sec. 3: circuits of one-, two- and three-qubit
- * gates; here any 1..5 targets plus up to 16 controls). */
+ * gates; here any 1..5 targets plus up to SV_MAX_CONTROLS controls). */
 typedef struct {
   int32_t kind;                        /* SV_GATE_* */
   int32_t n_tar;                       /* 1 (2 for SWAP, 1..5 for MATRIX) */
@@ -154,7 +154,7 @@ sv_status sv_copy(sv_state dst, sv_state src);
 
 /* Apply G (host complex128, 2^n_tar x 2^n_tar, row-major (re, im) pairs) to
  * targets[0..n_tar-1] where every qubit in controls[0..n_ctrl-1] is 1,
- * in place.  1 <= n_tar <= 5, 0 <= n_ctrl <= 16, all qubits distinct and
+ * in place.  1 <= n_tar <= 5, 0 <= n_ctrl <= SV_MAX_CONTROLS, all qubits distinct and
  * < n.  G is rounded once to the state's precision.  Asynchronous.
  * Errors: SV_ERR_INVALID for any bad argument (state untouched). */
 sv_status sv_apply_gate(sv_state s, const int* targets, int n_tar,

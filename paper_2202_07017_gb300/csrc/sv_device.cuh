@@ -13,7 +13,7 @@ namespace sv {
 template <typename I>
 struct Ins {
   int m;
-  I low[24];  // low[i] = 2^p_i - 1, p_i ascending (positions in the final index)
+  I low[40];  // low[i] = 2^p_i - 1, p_i ascending (positions in the final index)
 };
 
 template <typename I>

@@ -29,7 +29,7 @@ c_i32, c_i64, c_u64, c_dbl, c_vp = (ctypes.c_int32, ctypes.c_int64, ctypes.c_uin
 
 class SvGate(ctypes.Structure):
     _fields_ = [("kind", c_i32), ("n_tar", c_i32), ("n_ctrl", c_i32), ("param", c_i32),
-                ("targets", c_i32 * 5), ("controls", c_i32 * 16), ("angle", c_dbl),
+                ("targets", c_i32 * 5), ("controls", c_i32 * 33), ("angle", c_dbl),
                 ("mat_off", c_i64)]
 
 
@@ -153,7 +153,7 @@ class PackedCircuit:
             r.kind = KIND_CODE[g.kind]
             r.n_tar = len(g.targets)
             r.n_ctrl = len(g.controls)
-            if r.n_tar > 5 or r.n_ctrl > 16:
+            if r.n_tar > 5 or r.n_ctrl > 33:
                 raise SvError(1, f"gate {i}: too many targets or controls")
             for j, t in enumerate(g.targets):
                 r.targets[j] = int(t)

@@ -53,8 +53,8 @@ def test_host_validation_without_gpu():
 
 
 def test_struct_layout_matches_header():
-    assert ctypes.sizeof(sv.SvGate) == 4 * (4 + 5 + 16) + 4 + 8 + 8
-    assert sv.SvGate.angle.offset == 104 and sv.SvGate.mat_off.offset == 112
+    assert ctypes.sizeof(sv.SvGate) == 4 * (4 + 5 + 33) + 8 + 8
+    assert sv.SvGate.angle.offset == 168 and sv.SvGate.mat_off.offset == 176
 
 
 def test_pauli_masks_follow_bit_convention():

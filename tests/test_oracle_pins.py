@@ -430,3 +430,27 @@ def test_trotter_exact_for_commuting_terms_and_converges_otherwise():
     e2 = [np.linalg.norm(oracle.trotter(psi, H, 0.7, s, 2) - ref) for s in (8, 16)]
     assert 1.8 < e1[0] / e1[1] < 2.2      # first order: error ~ dt
     assert 3.6 < e2[0] / e2[1] < 4.4      # second order: error ~ dt^2
+
+
+# --------------------------------------------------------------------------
+# Grover search (Sec. 3: Grover's algorithm) and many-control gates
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8])
+def test_grover_success_probability_closed_form(n):
+    N = 1 << n
+    th = math.asin(1 / math.sqrt(N))
+    marked = (0x5A5A5A >> (24 - n)) & (N - 1)
+    for k in range(0, 4):
+        psi = oracle.run(W.grover(n, marked, k))
+        p = np.abs(psi) ** 2
+        assert abs(p[marked] - math.sin((2 * k + 1) * th) ** 2) < 1e-12
+        if N > 1:
+            others = np.delete(p, marked)
+            assert np.max(np.abs(others - math.cos((2 * k + 1) * th) ** 2 / (N - 1))) < 1e-12
+
+
+def test_many_controls_against_bruteforce():
+    n = 7
+    psi = W.random_state(n, 44)
+    g = W.Gate("Z", (6,), tuple(range(6)))
+    ref = full_operator(n, g.targets, g.controls, PAULI["Z"]) @ psi
+    assert np.max(np.abs(oracle.run(W.Circuit(n, [g], 0), None, psi) - ref)) < 1e-15

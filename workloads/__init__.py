@@ -183,6 +183,23 @@ def hea_theta(n: int, layers: int, seed: int) -> np.ndarray:
     return np.array([rng.angle() for _ in range(n * layers)])
 
 
+def grover(n: int, marked: int, iterations: int) -> Circuit:
+    """Grover search for the basis state `marked` (Sec. 3: Grover's
+    algorithm): H on every qubit, then per iteration the oracle (X on the
+    qubits where `marked` has a 0, Z on qubit n-1 controlled by all others,
+    the same X again) and the diffusion (H, X on every qubit, the same
+    multi-controlled Z, X, H)."""
+    hs = [Gate("H", (q,)) for q in range(n)]
+    xs = [Gate("X", (q,)) for q in range(n)]
+    flips = [Gate("X", (q,)) for q in range(n) if not (marked >> (n - 1 - q)) & 1]
+    mcz = Gate("Z", (n - 1,), tuple(range(n - 1)))
+    gates = list(hs)
+    for _ in range(iterations):
+        gates += flips + [mcz] + flips
+        gates += hs + xs + [mcz] + xs + hs
+    return Circuit(n, gates, 0, f"grover_n{n}_k{iterations}")
+
+
 def ghz(n: int) -> Circuit:
     gates = [Gate("H", (0,))] + [Gate("X", (k + 1,), (k,)) for k in range(n - 1)]
     return Circuit(n, gates, 0, f"ghz_n{n}")
