@@ -49,9 +49,16 @@ def test_grover_n20_closed_form(fuse_k):
         p = st.probabilities(list(range(n)))
     finally:
         st.close()
-    assert abs(p[marked] - math.sin((2 * k + 1) * th) ** 2) < 1e-3
-    assert p[marked] > 0.999
-    assert abs(p.sum() - 1) < 1e-4
+    # complex64 rounds 1/sqrt2 to h with 2h^2 = 1 - 3.4e-8, so every
+    # Hadamard scales ||psi||^2 by 2h^2; unfused Grover at n = 20 applies
+    # 40 per iteration (804 iterations): ||psi||^2 ~ 0.9989.  The
+    # distribution itself is checked normalised.
+    h = float(np.float32(1 / math.sqrt(2)))
+    n_h = sum(1 for g in c.gates if g.kind == "H")
+    norm_model = (2 * h * h) ** n_h
+    total = p.sum()
+    assert abs(p[marked] / total - math.sin((2 * k + 1) * th) ** 2) < 1e-4
+    assert norm_model - 1e-4 <= total <= 1 + 1e-5
 
 
 def test_grover_small_against_oracle():
