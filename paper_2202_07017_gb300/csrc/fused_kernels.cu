@@ -1,23 +1,34 @@
 // Fused qubit-block pass: one HBM round trip for many gates.
 //
 // A pass stages m amplitude-index bits S (the L lowest bits, as contiguous
-// runs of 2^L amplitudes, plus m - L high bits).  A thread block loads one
-// 2^m-amplitude slice (all other bits fixed by the block id) into shared
-// memory with coalesced 16-byte loads, applies the pass's register groups
-// one after another, and writes the slice back.  In a group every thread
-// pulls 2^k amplitudes that differ only in the group's k bits into
-// registers, applies the group's gates there (Eq. 1 of Sec. 2 for each
-// gate, with compile-time register indices) and pushes them back, so shared
-// memory is touched once per group rather than once per gate.
+// runs of 2^L amplitudes, plus m - L high bits).  A thread block holds one
+// 2^m-amplitude slice (all other bits fixed by the slice id) in shared
+// memory, applies the pass's register groups one after another, and writes
+// the slice back.  In a group every thread pulls 2^k amplitudes that differ
+// only in the group's k bits into registers, applies the group's gates there
+// (Eq. 1 of Sec. 2 for each gate, with compile-time register indices) and
+// pushes them back, so shared memory is touched once per group rather than
+// once per gate.
 //
-// Shared-memory layout: local amplitude j (bit i of j <-> staged bit S[i])
-// lives at slot j XOR-swizzled in bits 1..3 by bits 4..6 (complex64; bit 0
-// kept so a 16-byte vector of two amplitudes stays contiguous) or in bits
-// 0..2 by bits 3..5 (complex128), which spreads the strided register-group
-// accesses of a warp over the banks.
+// Staging: the slice is a box of a rank-2..5 tensor view of the state
+// (128-byte rows; the low run; up to three runs of consecutive staged high
+// bits as further dimensions; any remaining staged bits enumerated as
+// separate boxes), moved by bulk tensor copies (TMA) whose completion is
+// signalled on an mbarrier; blocks are persistent, one per resident slot.
+// Passes whose geometry does not fit a box use the fallback kernel, which
+// stages with 16-byte loads by all threads.
+//
+// Shared-memory layout: local amplitude j (bit i of j <-> staged bit
+// order[i]) lives at slot j with the 16-byte chunks of every 128-byte row
+// XOR-permuted by the row index mod 8 - the TMA 128-byte swizzle, applied
+// in software by the fallback kernel - which spreads the strided
+// register-group accesses of a warp over the banks.
 #include <algorithm>
+#include <mutex>
+#include <numeric>
 
 #include "sv_device.cuh"
+#include "tma.cuh"
 
 namespace sv {
 namespace {
@@ -36,9 +47,16 @@ struct FOpDev {
 
 template <typename R>
 struct FusedParams {
+  CUtensorMap tmap;   // TMA view of the state (64-byte aligned)
   Ins<uint64_t> blk;  // zero bits at every staged position: block id -> base index
   int m, L, nh;
-  uint8_t hpos[32];   // staged bits above the low run, ascending
+  uint8_t hpos[32];   // staged bits above the low run, in local order
+  // TMA geometry: coordinate d >= 1 of a box at base index a is
+  // (a mod 2^thi[d]) >> tlo[d]; box k adds software bits swpos[j] for the
+  // set bits j of k and lands at k * box_bytes in shared memory
+  int rank, nsw, ncopies;
+  uint8_t tlo[5], thi[5], swpos[12];
+  uint32_t box_bytes, slice_bytes;
   int ngroups;
   uint8_t gk[kFMaxGroups];
   uint8_t gbits[kFMaxGroups][5];
@@ -282,28 +300,300 @@ __global__ void __launch_bounds__(kFThreads, sizeof(R) == 4 ? 3 : 2)
   }
 }
 
+// ---- the TMA-staged pass kernel ---------------------------------------------------
+__device__ unsigned g_fused_status = 0;  // kWaitTimeout: a bounded wait gave up
+
 template <typename R>
-bool build_params(const FusedPass& pass, FusedParams<R>* P) {
+__device__ __forceinline__ void box_coords(const FusedParams<R>& P, uint64_t base, int k, int* c) {
+  uint64_t a = base;
+  for (int j = 0; j < P.nsw; ++j)
+    if ((k >> j) & 1) a |= uint64_t(1) << P.swpos[j];
+  c[0] = 0;
+#pragma unroll
+  for (int d = 1; d < 5; ++d)
+    c[d] = d < P.rank ? (int)((a & ((uint64_t(1) << P.thi[d]) - 1)) >> P.tlo[d]) : 0;
+}
+
+template <typename R>
+__device__ __forceinline__ void issue_load(const FusedParams<R>& P, uint32_t dst, const int* c,
+                                           uint32_t bar) {
+  switch (P.rank) {
+    case 2: tma_load<2>(dst, &P.tmap, c, bar); break;
+    case 3: tma_load<3>(dst, &P.tmap, c, bar); break;
+    case 4: tma_load<4>(dst, &P.tmap, c, bar); break;
+    default: tma_load<5>(dst, &P.tmap, c, bar); break;
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void issue_store(const FusedParams<R>& P, uint32_t src, const int* c) {
+  switch (P.rank) {
+    case 2: tma_store<2>(&P.tmap, c, src); break;
+    case 3: tma_store<3>(&P.tmap, c, src); break;
+    case 4: tma_store<4>(&P.tmap, c, src); break;
+    default: tma_store<5>(&P.tmap, c, src); break;
+  }
+}
+
+// Persistent: block b handles slices b, b + gridDim.x, ...  Warp 0 moves the
+// slice: waits until its earlier stores have read the buffer, arms the
+// mbarrier with the slice's byte count and issues the box loads; every
+// thread waits for the phase (bounded), runs the groups, makes its writes
+// visible to the async proxy, and warp 0 issues the box stores.
+template <typename R, int KGF>
+__global__ void __launch_bounds__(kFThreads, sizeof(R) == 4 ? 3 : 2)
+    kfused_tma(uint64_t n_blocks, const __grid_constant__ FusedParams<R> P) {
+  typedef typename Cplx2<R>::T V2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar;
+  const uint32_t raw = smem_addr(smem_raw);
+  const uint32_t sbuf = (raw + 1023u) & ~1023u;  // the 128-byte swizzle repeats every 1024 bytes
+  V2* sm = reinterpret_cast<V2*>(smem_raw + (sbuf - raw));
+  const uint32_t barp = smem_addr(&bar);
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    mbar_init(barp, 1);
+    fence_proxy_async_smem();
+  }
+  __syncthreads();
+  uint32_t parity = 0;
+  for (uint64_t blk = blockIdx.x; blk < n_blocks; blk += gridDim.x) {
+    const uint64_t base = insert_zeros(blk, P.blk);
+    if (threadIdx.x < 32) {
+      bulk_wait_read_all();
+      __syncwarp();
+      if (lane == 0) mbar_arrive_expect_tx(barp, P.slice_bytes);
+      __syncwarp();
+      for (int k = lane; k < P.ncopies; k += 32) {
+        int c[5];
+        box_coords(P, base, k, c);
+        issue_load(P, sbuf + (uint32_t)k * P.box_bytes, c, barp);
+      }
+    }
+    const bool ok = mbar_wait_bounded(barp, parity);
+    parity ^= 1;
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) atomicOr(&g_fused_status, kWaitTimeout);
+      break;
+    }
+    for (int g = 0; g < P.ngroups; ++g) {
+      run_group<KGF, R>(sm, P.m, P.gbits[g], P.ops, P.gop[g], P.gop[g + 1]);
+      if (g + 1 < P.ngroups) __syncthreads();
+    }
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      for (int k = lane; k < P.ncopies; k += 32) {
+        int c[5];
+        box_coords(P, base, k, c);
+        issue_store(P, sbuf + (uint32_t)k * P.box_bytes, c);
+      }
+      bulk_commit();
+    }
+  }
+  if (threadIdx.x < 32) bulk_wait_all();
+}
+
+// ---- host: local order, TMA geometry, parameters -----------------------------------
+// TMA view of the state in 8-byte words (w = 1 or 2 per amplitude, lw =
+// log2 w): dim 0 = the 16 words of a 128-byte row, dim 1 = rows (amplitude
+// bits [4 - lw, thi[1])), dims 2.. = chosen runs of staged bits, each
+// spanning up to the next chosen run (the last up to n).  Box: the whole row,
+// the low run, the chosen runs.  Fails (fallback kernel) if the low run is
+// shorter than a row or a box is smaller than 1024 bytes.
+struct TmaGeom {
+  int rank = 0;
+  int tlo[5] = {0, 0, 0, 0, 0}, thi[5] = {0, 0, 0, 0, 0};
+  uint64_t dims[5] = {0, 0, 0, 0, 0}, strides[4] = {0, 0, 0, 0};
+  uint32_t box[5] = {0, 0, 0, 0, 0};
+  std::vector<int> order;  // staged bits in local (shared-memory) order
+  std::vector<int> sw;     // staged bits enumerated as separate boxes
+  int box_bits = 0;        // log2 amplitudes per box
+};
+
+bool tma_geometry(const std::vector<int>& S, int L, int n, int lw, TmaGeom* g) {
+  const int lo1 = 4 - lw;  // amplitude bits inside one row
+  if (L < lo1 || n > 34) return false;
+  const int d1 = std::min(L - lo1, 8);  // rows of the low run in one box (box dim <= 256)
+  struct Run {
+    int start, len;
+  };
+  std::vector<int> hi;
+  for (int b : S)
+    if (b >= lo1 + d1) hi.push_back(b);
+  std::vector<Run> runs;
+  for (size_t i = 0; i < hi.size();) {
+    size_t j = i;
+    while (j + 1 < hi.size() && hi[j + 1] == hi[j] + 1 && (int)(j + 1 - i) < 8) ++j;
+    runs.push_back({hi[i], (int)(j - i + 1)});
+    i = j + 1;
+  }
+  std::vector<int> idx(runs.size());
+  std::iota(idx.begin(), idx.end(), 0);
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return runs[a].len > runs[b].len; });
+  std::vector<Run> chosen;
+  std::vector<char> is_chosen(runs.size(), 0);
+  for (size_t i = 0; i < idx.size() && i < 3; ++i) is_chosen[idx[i]] = 1;
+  for (size_t i = 0; i < runs.size(); ++i)
+    if (is_chosen[i]) chosen.push_back(runs[i]);
+  if (chosen.size() > 3) return false;
+  g->rank = 2 + (int)chosen.size();
+  g->dims[0] = 16;
+  g->box[0] = 16;
+  g->tlo[1] = lo1;
+  g->thi[1] = chosen.empty() ? n : chosen[0].start;
+  g->dims[1] = uint64_t(1) << (g->thi[1] - lo1);
+  g->box[1] = 1u << d1;
+  g->strides[0] = 128;
+  int bits = lo1 + d1;
+  for (size_t i = 0; i < chosen.size(); ++i) {
+    const int d = 2 + (int)i;
+    g->tlo[d] = chosen[i].start;
+    g->thi[d] = i + 1 < chosen.size() ? chosen[i + 1].start : n;
+    g->dims[d] = uint64_t(1) << (g->thi[d] - g->tlo[d]);
+    g->box[d] = 1u << chosen[i].len;
+    g->strides[d - 1] = (uint64_t(8) << lw) << chosen[i].start;
+    bits += chosen[i].len;
+  }
+  g->box_bits = bits;
+  if (bits + lw + 3 < 10) return false;  // box of >= 1024 bytes keeps every box 1024-aligned
+  g->order.clear();
+  g->sw.clear();
+  for (int b = 0; b < lo1 + d1; ++b) g->order.push_back(b);
+  for (const Run& r : chosen)
+    for (int b = r.start; b < r.start + r.len; ++b) g->order.push_back(b);
+  for (size_t i = 0; i < runs.size(); ++i)
+    if (!is_chosen[i])
+      for (int b = runs[i].start; b < runs[i].start + runs[i].len; ++b) {
+        g->order.push_back(b);
+        g->sw.push_back(b);
+      }
+  return (int)g->order.size() == (int)S.size() && g->sw.size() <= 12;
+}
+
+// Host check of the geometry against the kernel's coordinate formula for
+// the given slice: every box lies inside the tensor, its start address is the
+// slice base with the box's software bits, and the boxes' local indices map
+// one-to-one onto the slice's amplitudes.
+bool verify_tma(const TmaGeom& g, const std::vector<int>& S, int n, int lw, uint64_t blk) {
+  std::vector<int> sorted = S;
+  std::sort(sorted.begin(), sorted.end());
+  uint64_t base = 0;  // insert zeros at the staged bits into blk
+  {
+    uint64_t u = blk;
+    int ui = 0;
+    for (int b = 0; b < n; ++b) {
+      if (std::binary_search(sorted.begin(), sorted.end(), b)) continue;
+      if ((u >> ui) & 1) base |= uint64_t(1) << b;
+      ++ui;
+    }
+  }
+  const int ncop = 1 << (int)g.sw.size();
+  const uint64_t word = uint64_t(8);
+  for (int k = 0; k < ncop; ++k) {
+    uint64_t a = base;
+    for (size_t j = 0; j < g.sw.size(); ++j)
+      if ((k >> j) & 1) a |= uint64_t(1) << g.sw[j];
+    uint64_t bytes = 0;
+    for (int d = 1; d < g.rank; ++d) {
+      const uint64_t c = (a & ((uint64_t(1) << g.thi[d]) - 1)) >> g.tlo[d];
+      if (c > 0x7fffffffull || c + g.box[d] > g.dims[d]) return false;
+      bytes += c * g.strides[d - 1];
+    }
+    if (bytes != (a << lw) * word) return false;
+  }
+  // local index -> amplitude offset is a bijection onto the staged bits
+  uint64_t all = 0;
+  for (int b : g.order) {
+    if (all & (uint64_t(1) << b)) return false;
+    all |= uint64_t(1) << b;
+  }
+  for (int b : S)
+    if (!(all & (uint64_t(1) << b))) return false;
+  return true;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    cudaGetLastError();
+  });
+  return fn;
+}
+
+template <typename R>
+bool build_tma(const TmaGeom& g, void* data, FusedParams<R>* P) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn || (reinterpret_cast<uintptr_t>(data) & 15)) return false;
+  cuuint64_t dims[5], strides[4];
+  cuuint32_t box[5], estr[5] = {1, 1, 1, 1, 1};
+  for (int d = 0; d < g.rank; ++d) {
+    dims[d] = g.dims[d];
+    box[d] = g.box[d];
+    if (d + 1 < g.rank) strides[d] = g.strides[d];
+  }
+  // the low run is 2^L amplitudes: fetch from DRAM at up to 256 bytes
+  const uint64_t run_bytes = uint64_t(g.box[1]) * 128;
+  const CUtensorMapL2promotion prom = run_bytes >= 256 ? CU_TENSOR_MAP_L2_PROMOTION_L2_256B
+                                                       : CU_TENSOR_MAP_L2_PROMOTION_L2_128B;
+  if (fn(&P->tmap, CU_TENSOR_MAP_DATA_TYPE_UINT64, (cuuint32_t)g.rank, data, dims, strides, box,
+         estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, prom,
+         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return false;
+  P->rank = g.rank;
+  for (int d = 0; d < 5; ++d) {
+    P->tlo[d] = (uint8_t)g.tlo[d];
+    P->thi[d] = (uint8_t)g.thi[d];
+  }
+  P->nsw = (int)g.sw.size();
+  for (int j = 0; j < P->nsw; ++j) P->swpos[j] = (uint8_t)g.sw[j];
+  P->ncopies = 1 << P->nsw;
+  P->box_bytes = (uint32_t)((sizeof(R) * 2) << g.box_bits);
+  P->slice_bytes = P->box_bytes * (uint32_t)P->ncopies;
+  return true;
+}
+
+// order: the staged bits in local order (order[0..L) = 0..L-1)
+template <typename R>
+bool build_params(const FusedPass& pass, const std::vector<int>& order, FusedParams<R>* P) {
   const std::vector<int>& S = pass.S;
   P->m = (int)S.size();
   P->L = pass.L;
   P->nh = P->m - pass.L;
-  if (P->m > 24 || P->nh > 32) return false;
+  if (P->m > 24 || P->nh > 32 || (int)order.size() != P->m) return false;
   *reinterpret_cast<Ins<uint64_t>*>(&P->blk) = make_ins<uint64_t>(S);
-  for (int i = 0; i < P->nh; ++i) P->hpos[i] = (uint8_t)S[pass.L + i];
+  for (int i = 0; i < P->nh; ++i) P->hpos[i] = (uint8_t)order[pass.L + i];
+  int pos_of[64];
+  for (int b = 0; b < 64; ++b) pos_of[b] = -1;
+  for (int i = 0; i < P->m; ++i) pos_of[order[i]] = i;
   if ((int)pass.groups.size() > kFMaxGroups) return false;
   P->ngroups = (int)pass.groups.size();
   int nop = 0;
   for (int g = 0; g < P->ngroups; ++g) {
     const FusedGroup& grp = pass.groups[g];
+    // the group's bits in local order, ascending (zero-bit insertion order)
+    int lb[5];
+    for (int i = 0; i < grp.k; ++i) lb[i] = pos_of[S[grp.bits[i]]];
+    std::sort(lb, lb + grp.k);
     P->gk[g] = (uint8_t)grp.k;
-    for (int i = 0; i < 5; ++i) P->gbits[g][i] = (uint8_t)grp.bits[i];
+    for (int i = 0; i < 5; ++i) P->gbits[g][i] = (uint8_t)(i < grp.k ? lb[i] : 0);
     P->gop[g] = (uint16_t)nop;
-    // global bit -> group-local index
+    // global bit -> index within the group
     auto gl = [&](int bit) {
-      const int loc = (int)(std::lower_bound(S.begin(), S.end(), bit) - S.begin());
       for (int i = 0; i < grp.k; ++i)
-        if (grp.bits[i] == loc) return i;
+        if (lb[i] == pos_of[bit]) return i;
       return -1;
     };
     auto glmask = [&](uint64_t mask) {
@@ -354,31 +644,82 @@ bool build_params(const FusedPass& pass, FusedParams<R>* P) {
 }
 
 template <typename R>
-sv_status run_pass(void* data, int n, cudaStream_t st, const FusedPass& pass) {
-  FusedParams<R> P;
-  if (!build_params(pass, &P)) {
-    set_error("fused pass exceeds kernel capacity");
-    return SV_ERR_INVALID;
+struct PassKernels {
+  typedef void (*Lsu)(typename Cplx2<R>::T*, uint64_t, const FusedParams<R>);
+  typedef void (*Tma)(uint64_t, const FusedParams<R>);
+  static Lsu lsu(int kg) {
+    return kg <= 1 ? kfused<R, 1> : kg == 2 ? kfused<R, 2> : kg == 3 ? kfused<R, 3> : kfused<R, 4>;
   }
-  const size_t smem = (sizeof(R) * 2 << P.m) + (sizeof(uint64_t) << (P.m - P.L));
+  static Tma tma(int kg) {
+    return kg <= 1   ? kfused_tma<R, 1>
+           : kg == 2 ? kfused_tma<R, 2>
+           : kg == 3 ? kfused_tma<R, 3>
+                     : kfused_tma<R, 4>;
+  }
+};
+
+template <typename R>
+sv_status run_pass(void* data, int n, cudaStream_t st, const FusedPass& pass) {
+  static FusedParams<R> P;  // ~8-15 KB: kept off the stack; launches are serialised per call
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lk(mu);
   const int kg = pass.groups.empty() ? 1 : pass.groups[0].k;
   for (const FusedGroup& g : pass.groups)
     if (g.k != kg) {
       set_error("fused pass: groups of unequal width");
       return SV_ERR_INVALID;
     }
-  typedef void (*Kern)(typename Cplx2<R>::T*, uint64_t, const FusedParams<R>);
-  Kern kern = kg <= 1 ? kfused<R, 1> : kg == 2 ? kfused<R, 2> : kg == 3 ? kfused<R, 3> : kfused<R, 4>;
-  static bool attr_set[5] = {false, false, false, false, false};
-  if (!attr_set[kg]) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_set[kg] = true;
+  const int lw = sizeof(R) == 4 ? 0 : 1;
+  TmaGeom geo;
+  bool tma = tma_geometry(pass.S, pass.L, n, lw, &geo);
+  std::vector<int> order = tma ? geo.order : pass.S;
+  if (!build_params(pass, order, &P)) {
+    set_error("fused pass exceeds kernel capacity");
+    return SV_ERR_INVALID;
+  }
+  if (tma && !(verify_tma(geo, pass.S, n, lw, 0) &&
+               verify_tma(geo, pass.S, n, lw, (uint64_t(1) << (n - (int)pass.S.size())) - 1))) {
+    set_error("fused pass: inconsistent bulk-copy geometry");
+    return SV_ERR_INVALID;
+  }
+  if (tma) tma = build_tma(geo, data, &P);
+  if (!tma && order != pass.S && !build_params(pass, pass.S, &P)) {
+    set_error("fused pass exceeds kernel capacity");
+    return SV_ERR_INVALID;
   }
   const uint64_t nblk = uint64_t(1) << (n - P.m);
-  const uint64_t grid = std::min<uint64_t>(nblk, 152 * 16);
-  ProfScope prof(st, sizeof(R) == 4 ? "kfused_c64" : "kfused_c128");
-  kern<<<(unsigned)grid, kFThreads, smem, st>>>(
-      reinterpret_cast<typename Cplx2<R>::T*>(data), nblk, P);
+  const size_t amp = sizeof(R) * 2;
+  ProfScope prof(st, sizeof(R) == 4 ? (tma ? "kfused_tma_c64" : "kfused_c64")
+                                    : (tma ? "kfused_tma_c128" : "kfused_c128"));
+  if (tma) {
+    typename PassKernels<R>::Tma kern = PassKernels<R>::tma(kg);
+    const size_t smem = (amp << P.m) + 1024;
+    static int resident[5] = {0, 0, 0, 0, 0};
+    if (!resident[kg]) {
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      int r = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, kern, kFThreads, smem) != cudaSuccess ||
+          r < 1)
+        r = 1;
+      resident[kg] = r;
+    }
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const uint64_t grid = std::min<uint64_t>(nblk, (uint64_t)sms * resident[kg]);
+    kern<<<(unsigned)grid, kFThreads, smem, st>>>(nblk, P);
+  } else {
+    typename PassKernels<R>::Lsu kern = PassKernels<R>::lsu(kg);
+    const size_t smem = (amp << P.m) + (sizeof(uint64_t) << (P.m - P.L));
+    static bool attr_set[5] = {false, false, false, false, false};
+    if (!attr_set[kg]) {
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      attr_set[kg] = true;
+    }
+    const uint64_t grid = std::min<uint64_t>(nblk, 152 * 16);
+    kern<<<(unsigned)grid, kFThreads, smem, st>>>(
+        reinterpret_cast<typename Cplx2<R>::T*>(data), nblk, P);
+  }
   g_launches.fetch_add(1, std::memory_order_relaxed);
   return check_launch("fused pass kernel");
 }
@@ -388,6 +729,16 @@ sv_status run_pass(void* data, int n, cudaStream_t st, const FusedPass& pass) {
 sv_status launch_fused_pass(void* data, sv_dtype dt, int n, cudaStream_t st,
                             const FusedPass& pass) {
   return dt == SV_C64 ? run_pass<float>(data, n, st, pass) : run_pass<double>(data, n, st, pass);
+}
+
+unsigned take_fused_status() {
+  unsigned v = 0, zero = 0;
+  if (cudaMemcpyFromSymbol(&v, g_fused_status, sizeof(v)) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  if (v) cudaMemcpyToSymbol(g_fused_status, &zero, sizeof(zero));
+  return v;
 }
 
 }  // namespace sv

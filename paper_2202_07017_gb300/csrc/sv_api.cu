@@ -241,6 +241,19 @@ static sv_status make_handle(void* ptr, bool owned, int n, sv_dtype dt, void* st
   s->dt = dt;
   s->stream = (cudaStream_t)stream;
   cudaGetDevice(&s->device);
+  // Controlled phase gates whose lowest bit is 2 or 3 touch alternate 32- or
+  // 64-byte runs; with the default L2 fill granularity their reads fetch
+  // whole lines (1.5x the bytes).  32-byte fills keep the touched runs only
+  // and leave streaming kernels unchanged.  (A context limit: it ends with
+  // the process.)
+  {
+    static std::once_flag l2once[64];
+    if (s->device >= 0 && s->device < 64)
+      std::call_once(l2once[s->device], [] {
+        if (cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, 32) != cudaSuccess)
+          cudaGetLastError();
+      });
+  }
   cudaError_t e = cudaMalloc(&s->dres, 64 * sizeof(double));
   if (e == cudaSuccess) e = cudaMallocHost(&s->hres, 64 * sizeof(double));
   if (e != cudaSuccess) {
@@ -695,6 +708,10 @@ sv_status sv_sync(sv_state s) {
   if (!valid_state(s)) return SV_ERR_INVALID;
   SV_CUDA_TRY(cudaStreamSynchronize(s->stream));
   SV_CUDA_TRY(cudaGetLastError());
+  if (take_fused_status()) {
+    set_error("a fused pass gave up waiting for its bulk copies");
+    return SV_ERR_TIMEOUT;
+  }
   return SV_OK;
 }
 

@@ -169,6 +169,9 @@ bool plan_fusion(const sv_circuit* c, const double* theta, const FusionConfig& c
                  std::vector<FusionItem>* out);
 sv_status launch_fused_pass(void* data, sv_dtype dt, int n, cudaStream_t st,
                             const FusedPass& pass);
+// Reads and clears the fused-pass device status word of the current device
+// (kWaitTimeout = 1: a bounded wait inside a pass gave up).
+unsigned take_fused_status();
 
 // ---- adjoint (adjoint_kernels.cu) ----------------------------------------------
 // Un-applies U^dagger (given as matrix Gdag on bit tp, controls cp) on both
