@@ -24,6 +24,7 @@
 // in software by the fallback kernel - which spreads the strided
 // register-group accesses of a warp over the banks.
 #include <algorithm>
+#include <map>
 #include <mutex>
 #include <numeric>
 
@@ -36,6 +37,8 @@ namespace {
 constexpr int kFThreads = 256;
 constexpr int kFMaxOps = 200;
 constexpr int kFMaxGroups = 64;
+constexpr int kFMaxLayers = 128;
+constexpr int kFCoefBytes = 12288;  // layer coefficients of one pass
 
 template <typename R>
 struct FOpDev {
@@ -43,6 +46,16 @@ struct FOpDev {
   uint8_t cls;                  // FG_1Q: MK_* arithmetic class; FG_PHASE: 1 if the phase is -1
   uint8_t pad[3];
   R m[8];                       // FG_1Q: G00 G01 G10 G11 (re, im); FG_PHASE: m[0..1]
+};
+
+// One layer of a layered group: a dense 2x2 on every group bit i with bit i
+// of u1 set (the 2x2s act on different bits and commute), then a diagonal
+// over the group's 2^k local indices (dk: 0 none, 1 real, 2 complex).
+// Coefficients at coef[off...]: the 2x2s in bit order (8 values each,
+// row-major re/im), then the diagonal (2^k real or 2^k re/im pairs).
+struct FLayerDev {
+  uint8_t u1, dk;
+  uint16_t off;
 };
 
 template <typename R>
@@ -61,6 +74,11 @@ struct FusedParams {
   uint8_t gk[kFMaxGroups];
   uint8_t gbits[kFMaxGroups][5];
   uint16_t gop[kFMaxGroups + 1];
+  uint8_t gkind[kFMaxGroups];        // 1: the group runs as layers glay[g]..glay[g+1]
+  uint16_t glay[kFMaxGroups + 1];
+  int ncoef;                         // coefficients in coef[] (elements of R)
+  FLayerDev layers[kFMaxLayers];
+  R coef[kFCoefBytes / sizeof(R)];
   FOpDev<R> ops[kFMaxOps];
 };
 
@@ -226,6 +244,140 @@ __device__ __forceinline__ void run_group(typename Cplx2<R>::T* sm, int m, const
   }
 }
 
+// (a, b) <- G (a, b) on every register pair of compile-time group bit B,
+// G read from shared memory (8 values, 16-byte aligned)
+template <int KG, int B, typename R>
+__device__ __forceinline__ void dense_bit(const R* c, R (&re)[1 << KG], R (&im)[1 << KG]) {
+  M2<R> g;
+  if constexpr (sizeof(R) == 4) {
+    const float4 x = reinterpret_cast<const float4*>(c)[0];
+    const float4 y = reinterpret_cast<const float4*>(c)[1];
+    g.r[0] = x.x; g.i[0] = x.y; g.r[1] = x.z; g.i[1] = x.w;
+    g.r[2] = y.x; g.i[2] = y.y; g.r[3] = y.z; g.i[3] = y.w;
+  } else {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const double2 x = reinterpret_cast<const double2*>(c)[e];
+      g.r[e] = x.x;
+      g.i[e] = x.y;
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < (1 << KG); ++r) {
+    if (r & (1 << B)) continue;
+    const int r1 = r | (1 << B);
+    mv2<MK_DENSE, R>(g, re[r], im[r], re[r1], im[r1]);
+  }
+}
+
+// The group as a layer program (see FLayerDev): no per-gate dispatch, every
+// register index fixed at compile time.
+// slot offset of register r: XOR of the swizzled group-bit offsets sw[i]
+// over the set bits i of r (at most two 3-input XORs)
+template <int KG>
+__device__ __forceinline__ int reg_off(int r, const int (&sw)[KG]) {
+  int o = 0;
+#pragma unroll
+  for (int i = 0; i < KG; ++i)
+    if ((r >> i) & 1) o ^= sw[i];
+  return o;
+}
+
+template <int KG, typename R, bool TABLE>
+__device__ __forceinline__ void run_layers(typename Cplx2<R>::T* sm, int m, const uint8_t* gb,
+                                           const FLayerDev* lay, int l0, int l1, const R* coef) {
+  typedef typename Cplx2<R>::T V2;
+  constexpr int D = 1 << KG;
+  int sw[KG];
+#pragma unroll
+  for (int i = 0; i < KG; ++i) sw[i] = swz<R>(1 << gb[i]);
+  int soff[TABLE ? D : 1];
+  if constexpr (TABLE) {
+    soff[0] = 0;
+#pragma unroll
+    for (int r = 1; r < D; ++r) soff[r] = soff[r & (r - 1)] ^ sw[lowbit(r)];
+  }
+  auto off = [&](int r) -> int {
+    if constexpr (TABLE)
+      return soff[r];
+    else
+      return reg_off<KG>(r, sw);
+  };
+  int lm[KG];
+#pragma unroll
+  for (int i = 0; i < KG; ++i) lm[i] = (1 << gb[i]) - 1;
+  const int nsub = 1 << (m - KG);
+  for (int s = threadIdx.x; s < nsub; s += kFThreads) {
+    int b = s;
+#pragma unroll
+    for (int i = 0; i < KG; ++i) b = ((b & ~lm[i]) << 1) | (b & lm[i]);
+    const int sb = swz<R>(b);
+    R re[D], im[D];
+#pragma unroll
+    for (int r = 0; r < D; ++r) {
+      const V2 v = sm[sb ^ off(r)];
+      re[r] = v.x;
+      im[r] = v.y;
+    }
+    for (int l = l0; l < l1; ++l) {
+      const FLayerDev L = lay[l];
+      const R* c = coef + L.off;
+#pragma unroll
+      for (int i = 0; i < KG; ++i) {
+        if (L.u1 & (1 << i)) {
+          if (i == 0) dense_bit<KG, 0, R>(c, re, im);
+          if constexpr (KG > 1) if (i == 1) dense_bit<KG, (KG > 1 ? 1 : 0), R>(c, re, im);
+          if constexpr (KG > 2) if (i == 2) dense_bit<KG, (KG > 2 ? 2 : 0), R>(c, re, im);
+          if constexpr (KG > 3) if (i == 3) dense_bit<KG, (KG > 3 ? 3 : 0), R>(c, re, im);
+          c += 8;
+        }
+      }
+      // diagonal: 16-byte loads of the entries
+      typedef typename Cplx2<R>::T V2c;
+      if (L.dk == 1) {
+        if constexpr (sizeof(R) == 4) {
+#pragma unroll
+          for (int r = 0; r < D; r += 4) {
+            const float4 d = *reinterpret_cast<const float4*>(c + r);
+            const float dd[4] = {d.x, d.y, d.z, d.w};
+#pragma unroll
+            for (int e = 0; e < 4 && r + e < D; ++e) {
+              re[r + e] *= dd[e];
+              im[r + e] *= dd[e];
+            }
+          }
+        } else {
+#pragma unroll
+          for (int r = 0; r < D; r += 2) {
+            const double2 d = *reinterpret_cast<const double2*>(c + r);
+            re[r] *= d.x;
+            im[r] *= d.x;
+            if (r + 1 < D) {
+              re[r + 1] *= d.y;
+              im[r + 1] *= d.y;
+            }
+          }
+        }
+      } else if (L.dk == 2) {
+#pragma unroll
+        for (int r = 0; r < D; ++r) {
+          const V2c d = *reinterpret_cast<const V2c*>(c + 2 * r);
+          const R xr = re[r], xi = im[r];
+          re[r] = d.x * xr - d.y * xi;
+          im[r] = d.x * xi + d.y * xr;
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < D; ++r) {
+      V2 v;
+      v.x = re[r];
+      v.y = im[r];
+      sm[sb ^ off(r)] = v;
+    }
+  }
+}
+
 // ---- the pass kernel ------------------------------------------------------------
 // KGF: register-group width of every group of the pass (the planner pads
 // groups to it); 3 resident blocks per SM for complex64, 2 for complex128.
@@ -240,6 +392,8 @@ __global__ void __launch_bounds__(kFThreads, sizeof(R) == 4 ? 3 : 2)
   uint64_t* runoff = reinterpret_cast<uint64_t*>(sm + M);
   const int L = P.L;
   const int nruns = 1 << (P.m - L);
+  R* csm = reinterpret_cast<R*>(runoff + ((nruns + 1) & ~1));
+  for (int i = threadIdx.x; i < P.ncoef; i += kFThreads) csm[i] = P.coef[i];
   for (int r = threadIdx.x; r < nruns; r += kFThreads) {
     uint64_t o = 0;
     for (int i = 0; i < P.nh; ++i)
@@ -279,8 +433,10 @@ __global__ void __launch_bounds__(kFThreads, sizeof(R) == 4 ? 3 : 2)
     __syncthreads();
     for (int g = 0; g < P.ngroups; ++g) {
       const uint8_t* gb = P.gbits[g];
-      const int o0 = P.gop[g], o1 = P.gop[g + 1];
-      run_group<KGF, R>(sm, P.m, gb, P.ops, o0, o1);
+      if (P.gkind[g])
+        run_layers<KGF, R, true>(sm, P.m, gb, P.layers, P.glay[g], P.glay[g + 1], csm);
+      else
+        run_group<KGF, R>(sm, P.m, gb, P.ops, P.gop[g], P.gop[g + 1]);
       __syncthreads();
     }
     for (int c0 = threadIdx.x; c0 < nch; c0 += kFThreads * U) {
@@ -340,8 +496,10 @@ __device__ __forceinline__ void issue_store(const FusedParams<R>& P, uint32_t sr
 // mbarrier with the slice's byte count and issues the box loads; every
 // thread waits for the phase (bounded), runs the groups, makes its writes
 // visible to the async proxy, and warp 0 issues the box stores.
-template <typename R, int KGF>
-__global__ void __launch_bounds__(kFThreads, sizeof(R) == 4 ? 3 : 2)
+// MODE: 0 every group a gate list, 1 mixed, 3 every group a layer program
+// (shared-memory addresses recomputed per access instead of tabulated)
+template <typename R, int KGF, int MINB, int MODE>
+__global__ void __launch_bounds__(kFThreads, MINB)
     kfused_tma(uint64_t n_blocks, const __grid_constant__ FusedParams<R> P) {
   typedef typename Cplx2<R>::T V2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -351,6 +509,8 @@ __global__ void __launch_bounds__(kFThreads, sizeof(R) == 4 ? 3 : 2)
   V2* sm = reinterpret_cast<V2*>(smem_raw + (sbuf - raw));
   const uint32_t barp = smem_addr(&bar);
   const int lane = threadIdx.x & 31;
+  R* csm = reinterpret_cast<R*>(smem_raw + (sbuf - raw) + P.slice_bytes);
+  for (int i = threadIdx.x; i < P.ncoef; i += kFThreads) csm[i] = P.coef[i];
   if (threadIdx.x == 0) {
     mbar_init(barp, 1);
     fence_proxy_async_smem();
@@ -377,7 +537,12 @@ __global__ void __launch_bounds__(kFThreads, sizeof(R) == 4 ? 3 : 2)
       break;
     }
     for (int g = 0; g < P.ngroups; ++g) {
-      run_group<KGF, R>(sm, P.m, P.gbits[g], P.ops, P.gop[g], P.gop[g + 1]);
+      if (MODE == 3)
+        run_layers<KGF, R, false>(sm, P.m, P.gbits[g], P.layers, P.glay[g], P.glay[g + 1], csm);
+      else if (MODE == 1 && P.gkind[g])
+        run_layers<KGF, R, true>(sm, P.m, P.gbits[g], P.layers, P.glay[g], P.glay[g + 1], csm);
+      else
+        run_group<KGF, R>(sm, P.m, P.gbits[g], P.ops, P.gop[g], P.gop[g + 1]);
       if (g + 1 < P.ngroups) __syncthreads();
     }
     fence_proxy_async_smem();
@@ -558,11 +723,151 @@ bool build_tma(const TmaGeom& g, void* data, FusedParams<R>* P) {
     P->thi[d] = (uint8_t)g.thi[d];
   }
   P->nsw = (int)g.sw.size();
+  if (P->nsw > 12) return false;
   for (int j = 0; j < P->nsw; ++j) P->swpos[j] = (uint8_t)g.sw[j];
   P->ncopies = 1 << P->nsw;
   P->box_bytes = (uint32_t)((sizeof(R) * 2) << g.box_bits);
   P->slice_bytes = P->box_bytes * (uint32_t)P->ncopies;
   return true;
+}
+
+// Rewrites every group whose gates are uncontrolled 1-qubit gates and
+// diagonal gates (phases on subspaces, controlled diagonal 1-qubit gates) as
+// a layer program: a 1-qubit gate joins the open layer unless the layer's
+// diagonal already touches its bit (then a new layer starts); consecutive
+// 1-qubit gates on one bit multiply; diagonal gates multiply into the
+// layer's diagonal.  All products in fp64.  Other groups keep their gate
+// list.
+template <typename R>
+void build_layers(const FusedPass& pass, const int* pos_of, FusedParams<R>* P) {
+  struct LayerH {
+    int u1 = 0, dtouch = 0;
+    cd U[5][4];
+    cd Dg[32];
+    LayerH() {
+      for (int r = 0; r < 32; ++r) Dg[r] = {1.0, 0.0};
+    }
+    bool empty() const { return !u1 && !dtouch; }
+  };
+  auto cmul = [](cd a, cd b) { return cd{a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; };
+  int nl = 0, nc = 0;
+  const int cap = (int)(sizeof(P->coef) / sizeof(R));
+  for (int g = 0; g < P->ngroups; ++g) {
+    P->gkind[g] = 0;
+    P->glay[g] = (uint16_t)nl;
+    const FusedGroup& grp = pass.groups[g];
+    const int k = grp.k, D = 1 << k;
+    // convertible: uncontrolled or diagonal 1-qubit gates and phases only
+    bool conv = true;
+    for (int oi : grp.ops) {
+      const FGate& f = pass.gates[oi];
+      const bool diag1 = f.type == FG_1Q && f.m[1].re == 0 && f.m[1].im == 0 && f.m[2].re == 0 &&
+                         f.m[2].im == 0;
+      if (!(f.type == FG_PHASE || (f.type == FG_1Q && (f.cmask == 0 || diag1)))) conv = false;
+    }
+    if (!conv) continue;
+    int lb[5];
+    for (int i = 0; i < k; ++i) lb[i] = pos_of[pass.S[grp.bits[i]]];
+    std::sort(lb, lb + k);
+    auto gl = [&](int bit) {
+      for (int i = 0; i < k; ++i)
+        if (lb[i] == pos_of[bit]) return i;
+      return -1;
+    };
+    auto glmask = [&](uint64_t mask) {
+      int r = 0;
+      for (int b = 0; b < 64; ++b)
+        if ((mask >> b) & 1) r |= 1 << gl(b);
+      return r;
+    };
+    std::vector<LayerH> L(1);
+    bool ok = true;
+    for (int oi : grp.ops) {
+      const FGate& f = pass.gates[oi];
+      LayerH* cur = &L.back();
+      if (f.type == FG_1Q) {
+        const int t = gl(f.t), cm = glmask(f.cmask);
+        const bool diag = f.m[1].re == 0 && f.m[1].im == 0 && f.m[2].re == 0 && f.m[2].im == 0;
+        if (diag) {
+          for (int r = 0; r < D; ++r)
+            if ((r & cm) == cm) cur->Dg[r] = cmul(((r >> t) & 1) ? f.m[3] : f.m[0], cur->Dg[r]);
+          cur->dtouch |= cm | (1 << t);
+        } else if (cm == 0) {
+          if ((cur->dtouch >> t) & 1) {
+            L.emplace_back();
+            cur = &L.back();
+          }
+          if ((cur->u1 >> t) & 1) {
+            cd r4[4];
+            for (int i = 0; i < 2; ++i)
+              for (int j = 0; j < 2; ++j) {
+                const cd a = cmul(f.m[i * 2], cur->U[t][j]), b = cmul(f.m[i * 2 + 1], cur->U[t][2 + j]);
+                r4[i * 2 + j] = {a.re + b.re, a.im + b.im};
+              }
+            for (int e = 0; e < 4; ++e) cur->U[t][e] = r4[e];
+          } else {
+            for (int e = 0; e < 4; ++e) cur->U[t][e] = f.m[e];
+            cur->u1 |= 1 << t;
+          }
+        } else {
+          ok = false;
+        }
+      } else if (f.type == FG_PHASE) {
+        const int cm = glmask(f.cmask);
+        for (int r = 0; r < D; ++r)
+          if ((r & cm) == cm) cur->Dg[r] = cmul(f.m[0], cur->Dg[r]);
+        cur->dtouch |= cm;
+      } else {
+        ok = false;
+      }
+      if (!ok) break;
+    }
+    if (!ok) continue;
+    if (L.back().empty()) L.pop_back();
+    // coefficient count and capacity
+    int need = 0;
+    std::vector<int> dks;
+    for (const LayerH& h : L) {
+      bool one = true, real = true;
+      for (int r = 0; r < D; ++r) {
+        if (h.Dg[r].re != 1.0 || h.Dg[r].im != 0.0) one = false;
+        if (h.Dg[r].im != 0.0) real = false;
+      }
+      const int dk = one ? 0 : real ? 1 : 2;
+      dks.push_back(dk);
+      need += 8 * __builtin_popcount(h.u1);
+      need += dk == 0 ? 0 : dk == 1 ? D : 2 * D;
+      need = (need + 3) & ~3;  // 16-byte alignment of the next layer (float)
+    }
+    if (nl + (int)L.size() > kFMaxLayers || nc + need > cap) continue;
+    for (size_t li = 0; li < L.size(); ++li) {
+      const LayerH& h = L[li];
+      FLayerDev& d = P->layers[nl++];
+      d.u1 = (uint8_t)h.u1;
+      d.dk = (uint8_t)dks[li];
+      d.off = (uint16_t)nc;
+      for (int i = 0; i < k; ++i)
+        if ((h.u1 >> i) & 1)
+          for (int e = 0; e < 4; ++e) {
+            P->coef[nc++] = (R)h.U[i][e].re;
+            P->coef[nc++] = (R)h.U[i][e].im;
+          }
+      if (dks[li] == 1)
+        for (int r = 0; r < D; ++r) P->coef[nc++] = (R)h.Dg[r].re;
+      else if (dks[li] == 2)
+        for (int r = 0; r < D; ++r) {
+          P->coef[nc++] = (R)h.Dg[r].re;
+          P->coef[nc++] = (R)h.Dg[r].im;
+        }
+      while (nc & 3) P->coef[nc++] = 0;
+    }
+    P->gkind[g] = 1;
+    P->glay[g + 1] = (uint16_t)nl;
+  }
+  for (int g = 0; g < P->ngroups; ++g)
+    if (!P->gkind[g]) P->glay[g + 1] = P->glay[g];
+  P->glay[P->ngroups] = (uint16_t)nl;
+  P->ncoef = nc;
 }
 
 // order: the staged bits in local order (order[0..L) = 0..L-1)
@@ -576,7 +881,7 @@ bool build_params(const FusedPass& pass, const std::vector<int>& order, FusedPar
   *reinterpret_cast<Ins<uint64_t>*>(&P->blk) = make_ins<uint64_t>(S);
   for (int i = 0; i < P->nh; ++i) P->hpos[i] = (uint8_t)order[pass.L + i];
   int pos_of[64];
-  for (int b = 0; b < 64; ++b) pos_of[b] = -1;
+  for (int b = 0; b < 64; ++b) pos_of[b] = 0;
   for (int i = 0; i < P->m; ++i) pos_of[order[i]] = i;
   if ((int)pass.groups.size() > kFMaxGroups) return false;
   P->ngroups = (int)pass.groups.size();
@@ -640,6 +945,7 @@ bool build_params(const FusedPass& pass, const std::vector<int>& order, FusedPar
     }
   }
   P->gop[P->ngroups] = (uint16_t)nop;
+  build_layers(pass, pos_of, P);
   return true;
 }
 
@@ -650,11 +956,19 @@ struct PassKernels {
   static Lsu lsu(int kg) {
     return kg <= 1 ? kfused<R, 1> : kg == 2 ? kfused<R, 2> : kg == 3 ? kfused<R, 3> : kfused<R, 4>;
   }
-  static Tma tma(int kg) {
-    return kg <= 1   ? kfused_tma<R, 1>
-           : kg == 2 ? kfused_tma<R, 2>
-           : kg == 3 ? kfused_tma<R, 3>
-                     : kfused_tma<R, 4>;
+  template <int KG, int MINB>
+  static Tma pick(int mode) {
+    return mode == 3   ? kfused_tma<R, KG, MINB, 3>
+           : mode == 1 ? kfused_tma<R, KG, MINB, 1>
+                       : kfused_tma<R, KG, MINB, 0>;
+  }
+  // mode 0: gate lists, 1: mixed, 3: layer programs only.  Measured on
+  // GB300 (complex64, 4-bit groups): layer programs run fastest with the
+  // register budget of 2 blocks per SM, gate lists with 3.
+  static Tma tma(int kg, int mode) {
+    constexpr int MB = sizeof(R) == 4 ? 3 : 2;
+    if (kg == 4) return mode == 3 ? pick<4, 2>(mode) : pick<4, MB>(mode);
+    return kg <= 1 ? pick<1, MB>(mode) : kg == 2 ? pick<2, MB>(mode) : pick<3, MB>(mode);
   }
 };
 
@@ -692,25 +1006,31 @@ sv_status run_pass(void* data, int n, cudaStream_t st, const FusedPass& pass) {
   ProfScope prof(st, sizeof(R) == 4 ? (tma ? "kfused_tma_c64" : "kfused_c64")
                                     : (tma ? "kfused_tma_c128" : "kfused_c128"));
   if (tma) {
-    typename PassKernels<R>::Tma kern = PassKernels<R>::tma(kg);
-    const size_t smem = (amp << P.m) + 1024;
-    static int resident[5] = {0, 0, 0, 0, 0};
-    if (!resident[kg]) {
+    int nlay = 0;
+    for (int g = 0; g < P.ngroups; ++g) nlay += P.gkind[g];
+    const int mode = nlay == 0 ? 0 : nlay == P.ngroups ? 3 : 1;
+    typename PassKernels<R>::Tma kern = PassKernels<R>::tma(kg, mode);
+    const size_t smem = (amp << P.m) + 1024 + sizeof(R) * (size_t)P.ncoef;
+    // resident blocks per SM for this kernel and shared-memory size
+    static std::map<std::pair<const void*, size_t>, int> resident;
+    int& res = resident[{reinterpret_cast<const void*>(kern), smem}];
+    if (!res) {
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      int r = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, kern, kFThreads, smem) != cudaSuccess ||
-          r < 1)
-        r = 1;
-      resident[kg] = r;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&res, kern, kFThreads, smem) != cudaSuccess ||
+          res < 1) {
+        cudaGetLastError();
+        res = 1;
+      }
     }
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const uint64_t grid = std::min<uint64_t>(nblk, (uint64_t)sms * resident[kg]);
+    const uint64_t grid = std::min<uint64_t>(nblk, (uint64_t)sms * res);
     kern<<<(unsigned)grid, kFThreads, smem, st>>>(nblk, P);
   } else {
     typename PassKernels<R>::Lsu kern = PassKernels<R>::lsu(kg);
-    const size_t smem = (amp << P.m) + (sizeof(uint64_t) << (P.m - P.L));
+    const size_t smem = (amp << P.m) + (sizeof(uint64_t) * (((size_t(1) << (P.m - P.L)) + 1) & ~size_t(1))) +
+                        sizeof(R) * (size_t)P.ncoef;
     static bool attr_set[5] = {false, false, false, false, false};
     if (!attr_set[kg]) {
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);

@@ -78,3 +78,29 @@ def test_fused_layered_n33_inverse_and_unfused_prefix():
     assert abs(1 - nrm) <= 1e-5 and abs(1 - nrm2) <= 1e-5
     assert max_err(amps, ref) <= 1e-5
     assert max_err(fused, unfused) <= 1e-5
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("make", [lambda: W.random_layered(20, 6, 9), lambda: (W.qft(20), np.zeros(0)),
+                                  lambda: W.random_gates(16, 150, 77, max_tar=3, max_ctrl=2)],
+                         ids=["layered", "qft", "random"])
+def test_fused_passes_use_bulk_tensor_staging(dtype, make):
+    """At n >= 10 every fused pass is staged by bulk tensor copies (the
+    kfused_tma kernels): layer programs for the layered circuit, mixed
+    groups for the QFT (its final SWAPs), gate lists for controlled gates;
+    results equal the unfused path."""
+    from paper_2202_07017_gb300 import State, sv_profile_start, sv_profile_stop
+    c, theta = make()
+    psi = rounded(W.random_state(c.n_qubits, 31), dtype)
+    unfused = gpu_run(c, theta, psi, dtype, fuse_k=0)
+    st = State(c.n_qubits, dtype).load(psi)
+    try:
+        sv_profile_start()
+        st.apply_circuit(c, theta, 4)
+        prof = sv_profile_stop()
+        got = st.numpy()
+    finally:
+        st.close()
+    fused = {k: v for k, v in prof.items() if k.startswith("kfused")}
+    assert set(fused) == {f"kfused_tma_{dtype}"}, prof
+    assert max_err(got, unfused) <= TOL[dtype]
