@@ -314,7 +314,8 @@ def batch_solves(torch, reps=5):
                        "energy + adjoint gradient, complex64, one persistent launch (CUDA graph)",
            "items": len(items), "ms_per_launch": 1e3 * secs, "items_per_s": len(items) / secs,
            "gradients_per_s": len(theta) / secs,
-           "tile": {"k": b.k, "threads": b.threads, "blocks": b.blocks},
+           "tile": {"k": b.k, "threads": b.threads, "blocks": b.blocks, "cluster": b.cluster,
+                    "smem_states": b.smem_states},
            "create_and_tune_s": t_create}
     b.close()
     return out
@@ -502,7 +503,7 @@ def main():
             host.zero_()
             host[x] = 1.0
             hv = host.numpy()
-            for i in range(1 + 2):
+            for i in range(1 + 4):
                 t0 = time.perf_counter()
                 sv_upload(h, hv)
                 sv_apply_circuit(h, pc, None, 0)

@@ -307,10 +307,18 @@ sv_status sv_grad(sv_state s, const sv_circuit* c, const double* theta,
  * start at the sum of the parameter counts of items 0..i-1 (sv_batch_info
  * gives the total).  Gradients use the same packing.
  *
- * sv_batch_create uploads the descriptors and allocates the workspace; with
- * tune != 0 its autotuner times every (register-group width k in {2,3,4},
- * threads per block in {128,256,512}, blocks per SM in {1,2,4}) on the batch
- * and keeps the fastest (this synchronises the device).  The handle is
+ * sv_batch_create uploads the descriptors and allocates the workspace.
+ * tune = 0: single blocks of 256 threads, 2 per SM, register groups of k = 4
+ * qubits, states in a global workspace slot per block.  tune = 1: the
+ * autotuner times every (register-group width k in {2,3,4}, kernel: those
+ * single blocks with 128/256/512 threads and 1/2/4/8 blocks per SM, single
+ * blocks of 512 threads keeping psi (and lambda up to 13 qubits) in shared
+ * memory up to 14 qubits, or two-block clusters of 512 threads that split each item's psi and lambda by
+ * their top bit over the pair and keep them in shared memory up to 14 qubits,
+ * k <= 3) on the batch and keeps the fastest (this synchronises the device).
+ * tune = 2: the cluster kernel with k = 3 (the tune = 0 tile if a gate has 3
+ * controls); tune = 3: single blocks of 512 threads with states in shared
+ * memory, k = 4.  Other values: SV_ERR_INVALID.  The handle is
  * library-owned; sv_batch_free releases it. */
 #define SV_BATCH_MAX_QUBITS 18
 typedef struct sv_batch_s* sv_batch;
@@ -328,6 +336,12 @@ sv_status sv_batch_plan(const sv_circuit* circuits, const sv_pauli_sum* hamilton
 
 /* Chosen tile (k, threads per block, blocks) and total parameter count. */
 sv_status sv_batch_info(sv_batch b, int* k, int* threads, int* blocks, int* total_params);
+
+/* The chosen kernel: cluster_size 2 for the two-block cluster kernel (each
+ * item's psi and lambda split by their top bit over the pair), else 1;
+ * smem_states 1 if the kernel keeps small items' states in shared memory.
+ * SV_ERR_INVALID for a null handle or output. */
+sv_status sv_batch_kernel(sv_batch b, int* cluster_size, int* smem_states);
 
 /* One persistent launch (a queue reset plus the kernel) on cuda_stream;
  * dev_theta, dev_energy (n_items) and dev_grad (total_params) are device

@@ -14,7 +14,7 @@ import numpy as np
 
 from .sv import (C64, C128, EXPORTS, PackedBatch, sv_batch_create, sv_batch_free, sv_batch_grad,
                  sv_batch_plan,
-                 sv_batch_info, sv_batch_run, sv_batch_run_graph, PackedCircuit, PackedPauli, SvError, load, pack_circuit,
+                 sv_batch_info, sv_batch_kernel, sv_batch_run, sv_batch_run_graph, PackedCircuit, PackedPauli, SvError, load, pack_circuit,
                  pack_pauli, sv_adjoint, sv_alloc, sv_apply_circuit, sv_apply_gate,
                  sv_apply_pauli_sum, sv_copy, sv_download, sv_expval, sv_expval_async, sv_free,
                  sv_fusion_plan, sv_pauli_rotation, sv_probabilities, sv_sample, sv_trotter,
@@ -121,9 +121,10 @@ class Batch:
     launch (complex64, fp64 accumulation).  theta / energy / grad are torch
     CUDA float64 tensors; parameters are packed per item in item order."""
 
-    def __init__(self, circuits, hamiltonians, item_circuit, tune: bool = True):
+    def __init__(self, circuits, hamiltonians, item_circuit, tune=True):
         self.h, self.packed = sv_batch_create(circuits, hamiltonians, item_circuit, tune)
         self.k, self.threads, self.blocks, self.total_params = sv_batch_info(self.h)
+        self.cluster, self.smem_states = sv_batch_kernel(self.h)
         self.n_items = len(self.packed.items)
 
     def run(self, theta, energy=None, grad=None, graph: bool = False, stream=None):

@@ -25,6 +25,8 @@
 #include <mutex>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "sv_device.cuh"
 
 namespace sv {
@@ -309,16 +311,23 @@ __device__ void group_bwd(float2* psi, float2* lam, int n, const BGroup& g, cons
   }
 }
 
-template <int K, int MAXT, int MINB>
+// SMS: the block also owns kBSmemStateBytes of dynamic shared memory and
+// keeps psi there for items of up to 14 qubits (and lambda beside it for up
+// to 13), the rest in its global workspace slot.
+constexpr int kBSmemQubits = 14;
+constexpr size_t kBSmemStateBytes = sizeof(float2) << kBSmemQubits;
+
+template <int K, int MAXT, int MINB, bool SMS = false>
 __global__ void __launch_bounds__(MAXT, MINB) kbatch(const BatchArgs A) {
   __shared__ float mats[8 * kBMaxGates];
   __shared__ double wpart[(MAXT / 32) * kBMaxParams];
   __shared__ double red[MAXT / 32];
   __shared__ int s_item;
+  extern __shared__ __align__(16) float2 dyn_state[];
   const int nwarps = blockDim.x >> 5;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float2* psi = A.work + (size_t)blockIdx.x * (size_t(2) << A.nmax);
-  float2* lam = psi + (size_t(1) << A.nmax);
+  float2* const gpsi = A.work + (size_t)blockIdx.x * (size_t(2) << A.nmax);
+  float2* const glam = gpsi + (size_t(1) << A.nmax);
   while (true) {
     if (threadIdx.x == 0) s_item = atomicAdd(A.queue, 1);
     __syncthreads();
@@ -328,6 +337,12 @@ __global__ void __launch_bounds__(MAXT, MINB) kbatch(const BatchArgs A) {
     const BCirc C = A.circs[A.item_circ[item]];
     const double* th = A.theta + A.theta_off[item];
     const int dim = 1 << C.n;
+    float2* psi = gpsi;
+    float2* lam = glam;
+    if constexpr (SMS) {
+      if (C.n <= kBSmemQubits) psi = dyn_state;
+      if (C.n < kBSmemQubits) lam = dyn_state + (1 << (kBSmemQubits - 1));
+    }
     // gate matrices (fp64 trigonometry, rounded once), psi = |0...0>, zero partials
     for (int gi = threadIdx.x; gi < C.ngates; gi += blockDim.x) {
       const BGateDesc d = A.gates[C.gate0 + gi];
@@ -404,6 +419,329 @@ __global__ void __launch_bounds__(MAXT, MINB) kbatch(const BatchArgs A) {
   }
 }
 
+// ---- two-block clusters: each item's states split over the pair ----------------------
+// A cluster of two blocks (one per SM) runs one item at a time.  Block c
+// holds the amplitudes whose top bit (n - 1) is c, of both psi and lambda: in
+// its shared memory when n <= kClSmemQubits (2 x 64 KiB at n = 14), else in
+// the cluster's global workspace slot.  A register group that does not touch
+// bit n - 1 runs on each block's own half; a group that does ("split") gives
+// each block half of the sub-blocks and reaches the partner's half through
+// distributed shared memory (or global memory), with cluster barriers before
+// and after.  Energy and gradient partials are summed per block, then block 0
+// adds the partner's partials in a fixed order.
+constexpr int kClSmemQubits = 14;
+constexpr int kClThreads = 512;
+
+// amplitude x of the whole state: its block's half, offset inside the half
+struct Halves {
+  float2* h0;
+  float2* h1;
+  int hn;  // qubits per half (n - 1)
+  __device__ __forceinline__ float2& at(int x) const {
+    return ((x >> hn) ? h1 : h0)[x & ((1 << hn) - 1)];
+  }
+};
+
+template <int K>
+__device__ __forceinline__ void cl_group_fwd(const Halves& P, float2* own, int rank, int n,
+                                             bool split, const BGroup& g, const BOp* ops,
+                                             const float* mats) {
+  int off[1 << K], lm[K];
+  group_offsets<K>(g, off, lm);
+  const int kk = g.k, width = 1 << kk;
+  if (!split) {
+    const int nsub = 1 << (P.hn - kk);
+    for (int s = threadIdx.x; s < nsub; s += kClThreads) {
+      const int b = sub_base<K>(s, lm, kk);
+      float re[1 << K], im[1 << K];
+#pragma unroll
+      for (int r = 0; r < (1 << K); ++r)
+        if (r < width) {
+          const float2 v = own[b | off[r]];
+          re[r] = v.x;
+          im[r] = v.y;
+        }
+      for (int o = g.op0; o < g.op1; ++o) {
+        const BOp op = ops[o];
+        const float* M = mats + 8 * op.gi;
+#define SV_FWD(BB) \
+  if constexpr (BB < K) pair_apply<K, BB>(op.cls, M, op.cm, re, im)
+        SV_BIT_SWITCH(op.b0, SV_FWD)
+#undef SV_FWD
+      }
+#pragma unroll
+      for (int r = 0; r < (1 << K); ++r)
+        if (r < width) own[b | off[r]] = make_float2(re[r], im[r]);
+    }
+  } else {
+    const int nsub = 1 << (n - kk);  // sub-blocks s = rank, rank + 2, ...
+    for (int s = rank + 2 * (int)threadIdx.x; s < nsub; s += 2 * kClThreads) {
+      const int b = sub_base<K>(s, lm, kk);
+      float re[1 << K], im[1 << K];
+#pragma unroll
+      for (int r = 0; r < (1 << K); ++r)
+        if (r < width) {
+          const float2 v = P.at(b | off[r]);
+          re[r] = v.x;
+          im[r] = v.y;
+        }
+      for (int o = g.op0; o < g.op1; ++o) {
+        const BOp op = ops[o];
+        const float* M = mats + 8 * op.gi;
+#define SV_FWD(BB) \
+  if constexpr (BB < K) pair_apply<K, BB>(op.cls, M, op.cm, re, im)
+        SV_BIT_SWITCH(op.b0, SV_FWD)
+#undef SV_FWD
+      }
+#pragma unroll
+      for (int r = 0; r < (1 << K); ++r)
+        if (r < width) P.at(b | off[r]) = make_float2(re[r], im[r]);
+    }
+  }
+}
+
+template <int K, bool split>
+__device__ __forceinline__ void cl_group_bwd(const Halves& Pp, const Halves& Pl, float2* ownp,
+                                             float2* ownl, int rank, int n, const BGroup& g,
+                                             const BOp* ops, const float* mats, double* wpart) {
+  int off[1 << K], lm[K];
+  group_offsets<K>(g, off, lm);
+  const int kk = g.k, width = 1 << kk;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nsub = split ? 1 << (n - kk) : 1 << (Pp.hn - kk);
+  const int first = split ? rank : 0, step = split ? 2 : 1;
+  // every lane of a warp runs the same number of iterations (warp sums)
+  const int mine = split ? (nsub - rank + 1) / 2 : nsub;
+  const int iters = (mine + kClThreads - 1) / kClThreads;
+  for (int it = 0; it < iters; ++it) {
+    const int t = threadIdx.x + it * kClThreads;
+    const bool live = t < mine;
+    const int s = first + step * t;
+    const int b = live ? sub_base<K>(s, lm, kk) : 0;
+    float pr[1 << K], pi[1 << K], lr[1 << K], li[1 << K];
+#pragma unroll
+    for (int r = 0; r < (1 << K); ++r) {
+      pr[r] = pi[r] = lr[r] = li[r] = 0.f;
+      if (live && r < width) {
+        const int x = b | off[r];
+        float2 v, w;
+        if constexpr (split) {
+          v = Pp.at(x);
+          w = Pl.at(x);
+        } else {
+          v = ownp[x];
+          w = ownl[x];
+        }
+        pr[r] = v.x;
+        pi[r] = v.y;
+        lr[r] = w.x;
+        li[r] = w.y;
+      }
+    }
+    for (int o = g.op1 - 1; o >= g.op0; --o) {
+      const BOp op = ops[o];
+      const float* M = mats + 8 * op.gi;
+      if (op.pauli) {
+        float c = 0.f;
+#define SV_GRAD(BB) \
+  if constexpr (BB < K) c = pair_grad<K, BB>(op.pauli, op.cm, pr, pi, lr, li)
+        SV_BIT_SWITCH(op.b0, SV_GRAD)
+#undef SV_GRAD
+        c = warp_sum_f(c);
+        if (lane == 0) wpart[warp * kBMaxParams + op.param] += (double)c;
+      }
+#define SV_BWD(BB)                                   \
+  if constexpr (BB < K) {                            \
+    pair_apply_dag<K, BB>(op.cls, M, op.cm, pr, pi); \
+    pair_apply_dag<K, BB>(op.cls, M, op.cm, lr, li); \
+  }
+      SV_BIT_SWITCH(op.b0, SV_BWD)
+#undef SV_BWD
+    }
+    if (live) {
+#pragma unroll
+      for (int r = 0; r < (1 << K); ++r)
+        if (r < width) {
+          const int x = b | off[r];
+          if constexpr (split) {
+            Pp.at(x) = make_float2(pr[r], pi[r]);
+            Pl.at(x) = make_float2(lr[r], li[r]);
+          } else {
+            ownp[x] = make_float2(pr[r], pi[r]);
+            ownl[x] = make_float2(lr[r], li[r]);
+          }
+        }
+    }
+  }
+}
+
+__device__ __forceinline__ bool group_is_split(const BGroup& g, int hn) {
+  if (hn < g.k) return true;
+  for (int i = 0; i < g.k; ++i)
+    if (g.bits[i] == hn) return true;
+  return false;
+}
+
+// Dynamic shared memory: psi half, lambda half (2^13 amplitudes each), gate
+// matrices, per-warp gradient partials.
+constexpr size_t kClSmemBytes = (sizeof(float2) << kClSmemQubits) + sizeof(float) * 8 * kBMaxGates +
+                                sizeof(double) * (kClThreads / 32) * kBMaxParams;
+
+template <int K>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kClThreads, 1)
+    kbatch_cl(const BatchArgs A) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char cl_smem[];
+  float2* sh_psi = reinterpret_cast<float2*>(cl_smem);
+  float2* sh_lam = sh_psi + (1 << (kClSmemQubits - 1));
+  float* mats = reinterpret_cast<float*>(sh_lam + (1 << (kClSmemQubits - 1)));
+  double* wpart = reinterpret_cast<double*>(mats + 8 * kBMaxGates);
+  __shared__ double red[kClThreads / 32];
+  __shared__ int s_item;
+  const int rank = (int)cluster.block_rank();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int nwarps = kClThreads / 32;
+  const size_t cid = blockIdx.x / 2;
+  float2* gw = A.work + cid * (size_t(2) << A.nmax);  // global slot: psi, then lambda
+  int* partner_item = cluster.map_shared_rank(&s_item, 1);
+  while (true) {
+    if (rank == 0 && threadIdx.x == 0) {
+      const int v = atomicAdd(A.queue, 1);
+      s_item = v;
+      *partner_item = v;
+    }
+    cluster.sync();
+    const int slot = s_item;
+    if (slot >= A.n_items) break;
+    const int item = A.order[slot];
+    const BCirc C = A.circs[A.item_circ[item]];
+    const double* th = A.theta + A.theta_off[item];
+    const int n = C.n, hn = n - 1, hdim = 1 << hn;
+    const bool in_smem = n <= kClSmemQubits;
+    Halves Pp, Pl;
+    Pp.hn = Pl.hn = hn;
+    if (in_smem) {
+      Pp.h0 = cluster.map_shared_rank(sh_psi, 0);
+      Pp.h1 = cluster.map_shared_rank(sh_psi, 1);
+      Pl.h0 = cluster.map_shared_rank(sh_lam, 0);
+      Pl.h1 = cluster.map_shared_rank(sh_lam, 1);
+    } else {
+      Pp.h0 = gw;
+      Pp.h1 = gw + hdim;
+      Pl.h0 = gw + (size_t(1) << A.nmax);
+      Pl.h1 = Pl.h0 + hdim;
+    }
+    float2* ownp = in_smem ? sh_psi : (rank ? Pp.h1 : Pp.h0);
+    float2* ownl = in_smem ? sh_lam : (rank ? Pl.h1 : Pl.h0);
+    for (int gi = threadIdx.x; gi < C.ngates; gi += kClThreads) {
+      const BGateDesc d = A.gates[C.gate0 + gi];
+      const double a = d.param >= 0 ? th[d.param] : d.angle;
+      double sn, cs;
+      sincos(0.5 * a, &sn, &cs);
+      double m[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      const double r2 = 0.70710678118654752440;
+      switch (d.kind) {
+        case SV_GATE_H: m[0] = r2; m[2] = r2; m[4] = r2; m[6] = -r2; break;
+        case SV_GATE_X: m[2] = 1; m[4] = 1; break;
+        case SV_GATE_Y: m[3] = -1; m[5] = 1; break;
+        case SV_GATE_Z: m[0] = 1; m[6] = -1; break;
+        case SV_GATE_RX: m[0] = cs; m[3] = -sn; m[5] = -sn; m[6] = cs; break;
+        case SV_GATE_RY: m[0] = cs; m[2] = -sn; m[4] = sn; m[6] = cs; break;
+        case SV_GATE_RZ: m[0] = cs; m[1] = -sn; m[6] = cs; m[7] = sn; break;
+        default: {  // U1: diag(1, e^{ia})
+          double sa, ca;
+          sincos(a, &sa, &ca);
+          m[0] = 1; m[6] = ca; m[7] = sa;
+        }
+      }
+      for (int e = 0; e < 8; ++e) mats[8 * gi + e] = (float)m[e];
+    }
+    for (int x = threadIdx.x; x < hdim; x += kClThreads)
+      ownp[x] = make_float2(rank == 0 && x == 0 ? 1.f : 0.f, 0.f);
+    for (int i = threadIdx.x; i < nwarps * kBMaxParams; i += kClThreads) wpart[i] = 0.0;
+    __syncthreads();
+    // forward
+    bool synced = false;  // true right after a cluster barrier
+    for (int gg = 0; gg < C.ngroups; ++gg) {
+      const BGroup G = A.groups[C.group0 + gg];
+      const bool split = group_is_split(G, hn);
+      if (split && !synced) cluster.sync();
+      cl_group_fwd<K>(Pp, ownp, rank, n, split, G, A.ops, mats);
+      if (split) {
+        cluster.sync();
+        synced = true;
+      } else {
+        __syncthreads();
+        synced = false;
+      }
+    }
+    if (!synced) cluster.sync();
+    // lambda = H psi on this block's half, E = Re <psi|lambda>
+    double e = 0.0;
+    for (int xl = threadIdx.x; xl < hdim; xl += kClThreads) {
+      const int x = (rank << hn) | xl;
+      float orr = 0.f, oi = 0.f;
+      for (int t = 0; t < C.nterms; ++t) {
+        const BTerm T = A.terms[C.term0 + t];
+        const float2 b = Pp.at(x ^ (int)T.xm);
+        const float cr = (float)T.cre, ci = (float)T.cim;
+        const float sr = cr * b.x - ci * b.y, si = cr * b.y + ci * b.x;
+        if (__popcll(((uint64_t)x ^ T.xm) & T.zm) & 1) {
+          orr -= sr;
+          oi -= si;
+        } else {
+          orr += sr;
+          oi += si;
+        }
+      }
+      ownl[xl] = make_float2(orr, oi);
+      const float2 a = ownp[xl];
+      e += (double)(a.x * orr + a.y * oi);
+    }
+    e = warp_sum_d(e);
+    if (lane == 0) red[warp] = e;
+    cluster.sync();  // lambda complete; nobody still reads the partner's psi
+    // reverse sweep
+    synced = true;
+    for (int gg = C.ngroups - 1; gg >= 0; --gg) {
+      const BGroup G = A.groups[C.group0 + gg];
+      const bool split = group_is_split(G, hn);
+      if (split && !synced) cluster.sync();
+      if (split)
+        cl_group_bwd<K, true>(Pp, Pl, ownp, ownl, rank, n, G, A.ops, mats, wpart);
+      else
+        cl_group_bwd<K, false>(Pp, Pl, ownp, ownl, rank, n, G, A.ops, mats, wpart);
+      if (split) {
+        cluster.sync();
+        synced = true;
+      } else {
+        __syncthreads();
+        synced = false;
+      }
+    }
+    cluster.sync();  // both blocks' partials final
+    if (rank == 0) {
+      const double* pw = cluster.map_shared_rank(wpart, 1);
+      const double* pred = cluster.map_shared_rank(red, 1);
+      const int toff = A.theta_off[item];
+      for (int p = threadIdx.x; p < C.nparams; p += kClThreads) {
+        double g = 0.0;
+        for (int w = 0; w < nwarps; ++w) g += wpart[w * kBMaxParams + p];
+        for (int w = 0; w < nwarps; ++w) g += pw[w * kBMaxParams + p];
+        A.grad[toff + p] = g;
+      }
+      if (threadIdx.x == 0) {
+        double E = 0.0;
+        for (int w = 0; w < nwarps; ++w) E += red[w];
+        for (int w = 0; w < nwarps; ++w) E += pred[w];
+        A.energy[item] = E;
+      }
+    }
+    // the next item's barrier orders block 0's reads before block 1 reuses its partials
+  }
+}
+
 }  // namespace
 }  // namespace sv
 
@@ -411,6 +749,8 @@ __global__ void __launch_bounds__(MAXT, MINB) kbatch(const BatchArgs A) {
 struct sv_batch_s {
   int n_items = 0, nmax = 0, total_params = 0;
   int k = 4, threads = 256, blocks = 0;  // chosen tile
+  bool cluster = false;                  // two-block cluster kernel
+  bool smem_states = false;              // single-block kernel with states in shared memory
   int sms = 152;
   // device buffers
   sv::BCirc* circs = nullptr;
@@ -552,6 +892,9 @@ void free_batch(sv_batch b) {
 typedef void (*BatchKernel)(const BatchArgs);
 // Kernel variants by (group width, threads per block, resident blocks per
 // SM): more resident blocks need fewer registers and less shared memory.
+BatchKernel smem_kernel_for(int k) {
+  return k == 2 ? kbatch<2, 512, 1, true> : k == 3 ? kbatch<3, 512, 1, true> : kbatch<4, 512, 1, true>;
+}
 BatchKernel kernel_for(int k, int threads, int per_sm) {
   if (threads >= 512) return k == 2 ? kbatch<2, 512, 1> : k == 3 ? kbatch<3, 512, 1> : kbatch<4, 512, 1>;
   if (threads <= 128) return k == 2 ? kbatch<2, 128, 8> : kbatch<3, 128, 8>;
@@ -559,8 +902,11 @@ BatchKernel kernel_for(int k, int threads, int per_sm) {
   return k == 2 ? kbatch<2, 256, 2> : k == 3 ? kbatch<3, 256, 2> : kbatch<4, 256, 2>;
 }
 
+// register groups of 2 or 3 qubits (4 would spill at 512 threads per block)
+BatchKernel cluster_kernel_for(int k) { return k == 2 ? kbatch_cl<2> : kbatch_cl<3>; }
+
 sv_status launch_batch(sv_batch b, const double* theta, double* energy, double* grad,
-                       cudaStream_t st, int k, int threads, int blocks) {
+                       cudaStream_t st, int k, int threads, int blocks, bool cl, bool sms) {
   BatchArgs A;
   A.circs = b->circs;
   A.gates = b->gates;
@@ -578,6 +924,32 @@ sv_status launch_batch(sv_batch b, const double* theta, double* energy, double* 
   A.work = b->work;
   A.queue = b->queue;
   SV_CUDA_TRY(cudaMemsetAsync(b->queue, 0, sizeof(int), st));
+  if (cl) {
+    BatchKernel kern = cluster_kernel_for(k);
+    static bool attr[5] = {false, false, false, false, false};
+    if (!attr[k]) {
+      SV_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kClSmemBytes));
+      attr[k] = true;
+    }
+    ProfScope prof(st, "kbatch_cl");
+    kern<<<blocks, kClThreads, kClSmemBytes, st>>>(A);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return check_launch("batch cluster kernel");
+  }
+  if (sms) {
+    BatchKernel kern = smem_kernel_for(k);
+    static bool attr[5] = {false, false, false, false, false};
+    if (!attr[k]) {
+      SV_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kBSmemStateBytes));
+      attr[k] = true;
+    }
+    ProfScope prof(st, "kbatch_smem");
+    kern<<<blocks, 512, kBSmemStateBytes, st>>>(A);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return check_launch("batch kernel (shared-memory states)");
+  }
   ProfScope prof(st, "kbatch");
   kernel_for(k, threads, std::max(1, blocks / std::max(1, b->sms)))<<<blocks, threads, 0, st>>>(A);
   g_launches.fetch_add(1, std::memory_order_relaxed);
@@ -674,7 +1046,7 @@ sv_status sv_batch_plan(const sv_circuit* circuits, const sv_pauli_sum* hamilton
 sv_status sv_batch_create(const sv_circuit* circuits, const sv_pauli_sum* hamiltonians,
                           int n_circuits, const int32_t* item_circuit, int n_items, int tune,
                           sv_batch* out) {
-  if (!item_circuit || !out || n_items < 1) {
+  if (!item_circuit || !out || n_items < 1 || tune < 0 || tune > 3) {
     set_error("sv_batch_create: bad arguments");
     return SV_ERR_INVALID;
   }
@@ -714,15 +1086,25 @@ sv_status sv_batch_create(const sv_circuit* circuits, const sv_pauli_sum* hamilt
   // candidates: group width k, threads per block, blocks per SM
   struct Cand {
     int k, threads, per_sm;
+    bool cl;          // two-block clusters (per_sm = 1, threads = kClThreads)
+    bool sms = false; // states in shared memory up to 14 qubits (512 threads, 1 per SM)
   };
   std::vector<Cand> cands;
-  if (tune) {
-    const Cand all[] = {{2, 512, 1}, {3, 512, 1}, {4, 512, 1}, {2, 256, 2}, {3, 256, 2},
-                        {4, 256, 2}, {2, 256, 4}, {3, 256, 4}, {2, 128, 8}, {3, 128, 8}};
+  if (tune == 1) {
+    const Cand all[] = {{2, 512, 1, false, true}, {3, 512, 1, false, true}, {4, 512, 1, false, true},
+                        {2, kClThreads, 1, true}, {3, kClThreads, 1, true},
+                        {2, 512, 1, false}, {3, 512, 1, false}, {4, 512, 1, false},
+                        {2, 256, 2, false}, {3, 256, 2, false}, {4, 256, 2, false},
+                        {2, 256, 4, false}, {3, 256, 4, false}, {2, 128, 8, false},
+                        {3, 128, 8, false}};
     for (const Cand& c : all)
       if (c.k >= width) cands.push_back(c);
+  } else if (tune == 2 && width <= 3) {
+    cands.push_back({3, kClThreads, 1, true});
+  } else if (tune == 3) {
+    cands.push_back({std::max(4, width), 512, 1, false, true});
   } else {
-    cands.push_back({std::max(4, width), 256, 2});
+    cands.push_back({std::max(4, width), 256, 2, false});
   }
   int max_per = 1;
   for (auto& c : cands) max_per = std::max(max_per, c.per_sm);
@@ -786,11 +1168,11 @@ sv_status sv_batch_create(const sv_circuit* circuits, const sv_pauli_sum* hamilt
         built = c.k;
         if (st) break;
       }
-      const int blocks = sms * c.per_sm;
-      st = launch_batch(b, th, en, gr, 0, c.k, c.threads, blocks);  // warm-up
+      const int blocks = c.cl ? 2 * (sms / 2) : sms * c.per_sm;
+      st = launch_batch(b, th, en, gr, 0, c.k, c.threads, blocks, c.cl, c.sms);  // warm-up
       if (st) break;
       cudaEventRecord(e0, 0);
-      st = launch_batch(b, th, en, gr, 0, c.k, c.threads, blocks);
+      st = launch_batch(b, th, en, gr, 0, c.k, c.threads, blocks, c.cl, c.sms);
       cudaEventRecord(e1, 0);
       if (cudaEventSynchronize(e1) != cudaSuccess) {
         set_error("sv_batch_create: tuning run failed: %s", cudaGetErrorString(cudaGetLastError()));
@@ -804,6 +1186,8 @@ sv_status sv_batch_create(const sv_circuit* circuits, const sv_pauli_sum* hamilt
         b->k = c.k;
         b->threads = c.threads;
         b->blocks = blocks;
+        b->cluster = c.cl;
+        b->smem_states = c.sms;
       }
     }
     cudaEventDestroy(e0);
@@ -811,7 +1195,9 @@ sv_status sv_batch_create(const sv_circuit* circuits, const sv_pauli_sum* hamilt
   } else if (!st) {
     b->k = cands[0].k;
     b->threads = cands[0].threads;
-    b->blocks = sms * cands[0].per_sm;
+    b->cluster = cands[0].cl;
+    b->smem_states = cands[0].sms;
+    b->blocks = cands[0].cl ? 2 * (sms / 2) : sms * cands[0].per_sm;
   }
   if (th) cudaFree(th);
   if (en) cudaFree(en);
@@ -845,6 +1231,16 @@ sv_status sv_batch_info(sv_batch b, int* k, int* threads, int* blocks, int* tota
   return SV_OK;
 }
 
+sv_status sv_batch_kernel(sv_batch b, int* cluster_size, int* smem_states) {
+  if (!b || !cluster_size || !smem_states) {
+    set_error("sv_batch_kernel: bad arguments");
+    return SV_ERR_INVALID;
+  }
+  *cluster_size = b->cluster ? 2 : 1;
+  *smem_states = (b->cluster || b->smem_states) ? 1 : 0;
+  return SV_OK;
+}
+
 sv_status sv_batch_run(sv_batch b, const double* dev_theta, double* dev_energy, double* dev_grad,
                        void* cuda_stream) {
   if (!b || !dev_theta || !dev_energy || !dev_grad) {
@@ -852,7 +1248,7 @@ sv_status sv_batch_run(sv_batch b, const double* dev_theta, double* dev_energy, 
     return SV_ERR_INVALID;
   }
   return launch_batch(b, dev_theta, dev_energy, dev_grad, (cudaStream_t)cuda_stream, b->k,
-                      b->threads, b->blocks);
+                      b->threads, b->blocks, b->cluster, b->smem_states);
 }
 
 sv_status sv_batch_run_graph(sv_batch b, const double* dev_theta, double* dev_energy,
@@ -874,7 +1270,8 @@ sv_status sv_batch_run_graph(sv_batch b, const double* dev_theta, double* dev_en
     cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     sv_status s2 = SV_OK;
     if (e == cudaSuccess) {
-      s2 = launch_batch(b, dev_theta, dev_energy, dev_grad, cap, b->k, b->threads, b->blocks);
+      s2 = launch_batch(b, dev_theta, dev_energy, dev_grad, cap, b->k, b->threads, b->blocks,
+                        b->cluster, b->smem_states);
       e = cudaStreamEndCapture(cap, &g);
     }
     if (e == cudaSuccess && s2 == SV_OK) e = cudaGraphInstantiate(&b->gexec, g, 0);

@@ -55,7 +55,7 @@ EXPORTS = ("sv_alloc", "sv_wrap", "sv_free", "sv_set_stream", "sv_info", "sv_ini
            "sv_grad", "sv_sync", "sv_last_error", "sv_launch_count", "sv_version",
            "sv_profile_start", "sv_profile_stop", "sv_fusion_plan", "sv_expval_noalloc",
            "sv_probabilities", "sv_sample", "sv_pauli_rotation", "sv_trotter",
-           "sv_batch_create", "sv_batch_plan", "sv_batch_info", "sv_batch_run", "sv_batch_run_graph", "sv_batch_grad",
+           "sv_batch_create", "sv_batch_plan", "sv_batch_info", "sv_batch_kernel", "sv_batch_run", "sv_batch_run_graph", "sv_batch_grad",
            "sv_batch_free")
 
 _lib = None
@@ -106,6 +106,7 @@ def load(build: bool = True):
                             ctypes.c_int, P(c_vp)],
         "sv_batch_plan": [P(SvCircuit), P(SvPauliSum), ctypes.c_int, ctypes.c_int, P(c_i32)],
         "sv_batch_info": [c_vp, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int)],
+        "sv_batch_kernel": [c_vp, P(ctypes.c_int)],
         "sv_batch_run": [c_vp, c_vp, c_vp, c_vp, c_vp],
         "sv_batch_run_graph": [c_vp, c_vp, c_vp, c_vp, c_vp],
         "sv_batch_grad": [P(SvCircuit), P(SvPauliSum), ctypes.c_int, P(c_i32), ctypes.c_int,
@@ -424,12 +425,14 @@ class PackedBatch:
         self.total_params = int(sum(self.n_params[i] for i in self.items))
 
 
-def sv_batch_create(circuits, hamiltonians, item_circuit, tune: bool = False):
+def sv_batch_create(circuits, hamiltonians, item_circuit, tune=False):
+    """tune: False/0 default tile, True/1 autotune, 2 the two-block cluster kernel,
+    3 single blocks with states in shared memory."""
     pb = PackedBatch(circuits, hamiltonians, item_circuit)
     h = c_vp()
     _check(load().sv_batch_create(pb.carr, pb.harr, len(pb.pcs),
                                   pb.items.ctypes.data_as(ctypes.POINTER(c_i32)), len(pb.items),
-                                  int(bool(tune)), ctypes.byref(h)))
+                                  int(tune), ctypes.byref(h)))
     return h.value, pb
 
 
@@ -447,6 +450,13 @@ def sv_batch_info(h: int):
     _check(load().sv_batch_info(c_vp(h), ctypes.byref(k), ctypes.byref(t), ctypes.byref(b),
                                 ctypes.byref(p)))
     return k.value, t.value, b.value, p.value
+
+
+def sv_batch_kernel(h: int):
+    """(blocks per cluster, states in shared memory) of the chosen batch kernel."""
+    c, m = ctypes.c_int(), ctypes.c_int()
+    _check(load().sv_batch_kernel(c_vp(h), ctypes.byref(c), ctypes.byref(m)))
+    return c.value, bool(m.value)
 
 
 def sv_batch_run(h: int, dev_theta: int, dev_energy: int, dev_grad: int, stream: int = 0) -> None:

@@ -42,7 +42,7 @@ def _small_batch():
     return circuits, hams, items, thetas
 
 
-@pytest.mark.parametrize("tune", [False, True])
+@pytest.mark.parametrize("tune", [0, 1, 2, 3], ids=["default", "tuned", "cluster", "smem-states"])
 def test_batch_against_oracle(tune):
     from paper_2202_07017_gb300 import Batch
     circuits, hams, items, thetas = _small_batch()
@@ -128,3 +128,42 @@ def test_batch_hea14_and_mixed_shapes():
         ref = oracle.grad_param_shift(c, th, H, params=ps)
         gi = g[offs[i]:offs[i + 1]]
         assert np.max(np.abs(gi[ps] - ref[ps])) <= 1e-5 * max(1.0, np.max(np.abs(ref[ps])))
+
+
+@pytest.mark.parametrize("mode,cl,sm", [(0, 1, False), (2, 2, True), (3, 1, True)],
+                         ids=["single-block", "cluster", "smem-states"])
+def test_batch_kernel_choice_and_both_state_homes(mode, cl, sm):
+    """tune = 0 runs single blocks on global workspace; tune = 2 runs
+    two-block clusters (items up to 14 qubits keep psi and lambda split over
+    the pair's shared memory, larger ones in the cluster's global slot), a
+    gate with 3 controls falling back to the single-block kernel; tune = 3
+    runs single blocks with psi (and lambda up to 13 qubits) in shared
+    memory.  Checked against the single-state adjoint."""
+    from paper_2202_07017_gb300 import Batch, State
+    mixed = W.mixed_batch(40, 2024)
+    big = [m for m in mixed if m[0].n_qubits >= 15][:3] + [m for m in mixed if m[0].n_qubits <= 10][:3]
+    c3, th3 = W.random_gates(9, 60, 5, max_tar=1, max_ctrl=3, kinds=ONEQ)
+    cases = [([m[0] for m in big], [m[2] for m in big], [m[1] for m in big], (cl, sm)),
+             ([c3], [W.random_pauli_sum(9, 10, 5)], [th3], (1, mode == 3))]
+    for circuits, hams, thetas, want in cases:
+        items = list(range(len(circuits)))
+        b = Batch(circuits, hams, items, tune=mode)
+        assert (b.cluster, b.smem_states) == want
+        e, g = b.run(torch.tensor(np.concatenate(thetas), dtype=torch.float64, device="cuda"))
+        torch.cuda.synchronize()
+        e, g = e.cpu().numpy(), g.cpu().numpy()
+        b.close()
+        off = 0
+        for i, (c, H, th) in enumerate(zip(circuits, hams, thetas)):
+            st = State(c.n_qubits, "c64").init(0)
+            st.apply_circuit(c, th)
+            e_ref, g_ref = st.adjoint(c, th, H)
+            st.close()
+            scale = sum(abs(t[0]) for t in H)
+            assert abs(e[i] - e_ref) <= 2e-5 * scale
+            if c.n_params:
+                # normwise, with a floor for circuits whose gradient vanishes
+                # (parameters on rotations whose controls are rarely set)
+                err = np.max(np.abs(g[off:off + c.n_params] - g_ref))
+                assert err <= 2e-5 * max(np.max(np.abs(g_ref)), 0.05 * scale), (i, err)
+            off += c.n_params
