@@ -196,8 +196,39 @@ def adjoint_ratio(torch, reps=3):
     finally:
         sv_free(h)
     f, gm = float(np.median(fw)), float(np.median(gr))
+    fused = _fused_grad_times(torch, c, theta, pc, pp, [], reps)
     return {"workload": "hardware-efficient ansatz n=20 L=10 (200 params), TFIM, complex64",
             "forward_ms": 1e3 * f, "grad_ms": 1e3 * gm, "grad_over_forward": gm / f,
+            "energy": e, "fused": {k: (1e3 * v if k.endswith("_s") else v)
+                                   for k, v in fused.items()}}
+
+
+def _fused_grad_times(torch, c, theta, pc, pp, ck, reps):
+    """Forward (init + fused circuit, k = 4 + energy) and forward + gradient
+    through sv_grad_fused (fused forward and fused reverse sweep)."""
+    from paper_2202_07017_gb300 import (C64, sv_alloc, sv_apply_circuit, sv_expval, sv_free,
+                                        sv_grad_fused, sv_init)
+    h = sv_alloc(c.n_qubits, C64, torch.cuda.current_stream().cuda_stream)
+    try:
+        sv_init(h, 0)
+        sv_grad_fused(h, pc, theta, pp, ck, 4)  # warm-up (work states, checkpoints)
+        fw, fg = [], []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sv_init(h, 0)
+            sv_apply_circuit(h, pc, theta, 4)
+            sv_expval(h, pp)
+            t1 = time.perf_counter()
+            sv_init(h, 0)
+            e, g = sv_grad_fused(h, pc, theta, pp, ck, 4)
+            t2 = time.perf_counter()
+            fw.append(t1 - t0)
+            fg.append(t2 - t1)
+    finally:
+        sv_free(h)
+    f, t = float(np.median(fw)), float(np.median(fg))
+    return {"forward_s": f, "forward_plus_grad_s": t, "grad_over_forward": (t - f) / f,
             "energy": e}
 
 
@@ -273,10 +304,12 @@ def layered_adjoint(torch, n=28, depth=40):
         t2 = time.perf_counter()
     finally:
         sv_free(h)
+    fused = _fused_grad_times(torch, c, theta, pc, pp, ck, 2)
     return {"workload": f"random layered n={n} complex64 depth {depth} ({len(c.gates)} gates, "
                         f"{c.n_params} params), <sum Z>, checkpoints every 10 layers",
             "forward_s": t1 - t0, "forward_plus_grad_s": t2 - t1,
-            "grad_over_forward": (t2 - t1 - (t1 - t0)) / (t1 - t0), "energy": e2}
+            "grad_over_forward": (t2 - t1 - (t1 - t0)) / (t1 - t0), "energy": e2,
+            "fused": fused}
 
 
 def batch_solves(torch, reps=5):

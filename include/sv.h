@@ -287,6 +287,20 @@ sv_status sv_grad(sv_state s, const sv_circuit* c, const double* theta,
                   const sv_pauli_sum* H, const int32_t* checkpoint_gates,
                   int n_checkpoints, double* energy, double* grad);
 
+/* sv_grad with the forward circuit and the reverse sweep run as fused
+ * qubit-block passes.  fuse_k as in sv_apply_circuit (0: exactly sv_grad;
+ * 2..5).  Checkpoints split the circuit into segments that are fused
+ * separately, so no gate moves across a checkpoint.  A reverse pass stages
+ * psi and lambda together (one staged bit fewer than a forward pass,
+ * register groups of at most 3 qubits); before un-applying each
+ * parameterised gate it accumulates that gate's Im<lambda|P|psi> per block
+ * in fp64, and a fixed-order finish adds the block sums.  States of fewer
+ * than 10 qubits, or passes without a bulk-copy geometry, take the unfused
+ * sweep.  Outputs, checkpoints and errors as sv_grad. */
+sv_status sv_grad_fused(sv_state s, const sv_circuit* c, const double* theta,
+                        const sv_pauli_sum* H, const int32_t* checkpoint_gates,
+                        int n_checkpoints, int fuse_k, double* energy, double* grad);
+
 /* ---- batched energies and gradients (one persistent launch) ------------ */
 
 /* Many small variational circuits at once (Sec. 3: variational layers and

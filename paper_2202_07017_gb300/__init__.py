@@ -18,7 +18,7 @@ from .sv import (C64, C128, EXPORTS, PackedBatch, sv_batch_create, sv_batch_free
                  pack_pauli, sv_adjoint, sv_alloc, sv_apply_circuit, sv_apply_gate,
                  sv_apply_pauli_sum, sv_copy, sv_download, sv_expval, sv_expval_async, sv_free,
                  sv_fusion_plan, sv_pauli_rotation, sv_probabilities, sv_sample, sv_trotter,
-                 sv_grad, sv_info, sv_init, sv_last_error, sv_launch_count, sv_norm, sv_profile_start,
+                 sv_grad, sv_grad_fused, sv_info, sv_init, sv_last_error, sv_launch_count, sv_norm, sv_profile_start,
                  sv_profile_stop, sv_set_stream,
                  sv_sync, sv_upload, sv_version, sv_wrap)
 
@@ -109,7 +109,12 @@ class State:
     def adjoint(self, circuit, theta, terms):
         return sv_adjoint(self.h, circuit, theta, pack_pauli(terms, self.n))
 
-    def grad(self, circuit, theta, terms, checkpoint_gates=()):
+    def grad(self, circuit, theta, terms, checkpoint_gates=(), fuse_k=0):
+        """Forward pass from the current state plus adjoint gradient; fuse_k >= 2
+        runs both as fused qubit-block passes."""
+        if fuse_k:
+            return sv_grad_fused(self.h, circuit, theta, pack_pauli(terms, self.n),
+                                 checkpoint_gates, fuse_k)
         return sv_grad(self.h, circuit, theta, pack_pauli(terms, self.n), checkpoint_gates)
 
     def sync(self):

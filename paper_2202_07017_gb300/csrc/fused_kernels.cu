@@ -61,6 +61,7 @@ struct FLayerDev {
 template <typename R>
 struct FusedParams {
   CUtensorMap tmap;   // TMA view of the state (64-byte aligned)
+  CUtensorMap tmap2;  // reverse sweeps: the same view of lambda
   Ins<uint64_t> blk;  // zero bits at every staged position: block id -> base index
   int m, L, nh;
   uint8_t hpos[32];   // staged bits above the low run, in local order
@@ -71,6 +72,8 @@ struct FusedParams {
   uint8_t tlo[5], thi[5], swpos[12];
   uint32_t box_bytes, slice_bytes;
   int ngroups;
+  int ngrad;            // reverse sweeps: gradient operations of the pass
+  int gslot[kFMaxOps];  // their gradient slots
   uint8_t gk[kFMaxGroups];
   uint8_t gbits[kFMaxGroups][5];
   uint16_t gop[kFMaxGroups + 1];
@@ -559,6 +562,212 @@ __global__ void __launch_bounds__(kFThreads, MINB)
   if (threadIdx.x < 32) bulk_wait_all();
 }
 
+// ---- reverse sweep pass: psi and lambda together ---------------------------------------
+// Gradient of U = exp(-i theta P / 2) at its place in the reverse sweep:
+// Im <lambda|P|psi> (P a Pauli, or for pauli = 0 the Hermitian generator
+// [[a, b], [conj b, d]] in gm = (a, d, re b, im b) that a pending un-apply
+// W turns P into: W^dagger P W) over the register pairs of group bit B inside the
+// control mask cm, in the state's precision (a thread's 2^(KG-1) pairs;
+// the warp's sum is then added to an fp64 accumulator).
+template <int KG, int B, typename R>
+__device__ __forceinline__ R grad_pairs(int pauli, int cm, const R* gm, const R (&pr)[1 << KG],
+                                        const R (&pi)[1 << KG], const R (&lr)[1 << KG],
+                                        const R (&li)[1 << KG]) {
+  R acc = 0;
+  const R ga = gm[0], gd = gm[1], gbr = gm[2], gbi = gm[3];
+#pragma unroll
+  for (int r = 0; r < (1 << KG); ++r) {
+    if (r & (1 << B)) continue;
+    if ((r & cm) != cm) continue;
+    const int r1 = r | (1 << B);
+    const R p0r = pr[r], p0i = pi[r], p1r = pr[r1], p1i = pi[r1];
+    const R l0r = lr[r], l0i = li[r], l1r = lr[r1], l1i = li[r1];
+    R c;
+    if (pauli == 0) {  // M = [[a, b], [conj b, d]]: terms of conj(l_r) M_rs p_s
+      const R z00i = l0r * p0i - l0i * p0r, z11i = l1r * p1i - l1i * p1r;
+      const R z01r = l0r * p1r + l0i * p1i, z01i = l0r * p1i - l0i * p1r;
+      const R z10r = l1r * p0r + l1i * p0i, z10i = l1r * p0i - l1i * p0r;
+      c = ga * z00i + gd * z11i + gbr * (z01i + z10i) + gbi * (z01r - z10r);
+    } else if (pauli == 1)  // P psi = (p1, p0)
+      c = (l0r * p1i - l0i * p1r) + (l1r * p0i - l1i * p0r);
+    else if (pauli == 2)  // (-i p1, i p0)
+      c = -(l0r * p1r + l0i * p1i) + (l1r * p0r + l1i * p0i);
+    else  // (p0, -p1)
+      c = (l0r * p0i - l0i * p0r) - (l1r * p1i - l1i * p1r);
+    acc += c;
+  }
+  return acc;
+}
+
+// One register group over both slices: gradient operations accumulate into
+// this warp's fp64 slots gw[0..ngrad), every other operation is applied to
+// psi and lambda.  All lanes of a warp run the same iterations (warp sums).
+template <int KG, typename R>
+__device__ __forceinline__ void run_group_adj(typename Cplx2<R>::T* smp,
+                                              typename Cplx2<R>::T* sml, int m,
+                                              const uint8_t* gb, const FOpDev<R>* ops, int o0,
+                                              int o1, double* gw) {
+  typedef typename Cplx2<R>::T V2;
+  constexpr int D = 1 << KG;
+  int soff[D];
+  soff[0] = 0;
+#pragma unroll
+  for (int r = 1; r < D; ++r) soff[r] = soff[r & (r - 1)] ^ swz<R>(1 << gb[lowbit(r)]);
+  int lm[KG];
+#pragma unroll
+  for (int i = 0; i < KG; ++i) lm[i] = (1 << gb[i]) - 1;
+  const int nsub = 1 << (m - KG);
+  const int iters = (nsub + kFThreads - 1) / kFThreads;
+  const int lane = threadIdx.x & 31;
+  for (int it = 0; it < iters; ++it) {
+    const int s = threadIdx.x + it * kFThreads;
+    const bool live = s < nsub;
+    int b = live ? s : 0;
+#pragma unroll
+    for (int i = 0; i < KG; ++i) b = ((b & ~lm[i]) << 1) | (b & lm[i]);
+    const int sb = swz<R>(b);
+    R pr[D], pi[D], lr[D], li[D];
+#pragma unroll
+    for (int r = 0; r < D; ++r) {
+      const V2 v = smp[sb ^ soff[r]], w = sml[sb ^ soff[r]];
+      pr[r] = v.x;
+      pi[r] = v.y;
+      lr[r] = w.x;
+      li[r] = w.y;
+    }
+    for (int o = o0; o < o1; ++o) {
+      const FOpDev<R>& op = ops[o];
+      if (op.type == FG_GRAD) {
+        R c = 0;
+        if (live) {
+          const int cm = op.cmask, pa = op.cls;
+          switch (op.b0) {
+            case 0: c = grad_pairs<KG, 0, R>(pa, cm, op.m, pr, pi, lr, li); break;
+            case 1: if constexpr (KG > 1) c = grad_pairs<KG, (KG > 1 ? 1 : 0), R>(pa, cm, op.m, pr, pi, lr, li); break;
+            case 2: if constexpr (KG > 2) c = grad_pairs<KG, (KG > 2 ? 2 : 0), R>(pa, cm, op.m, pr, pi, lr, li); break;
+            default: if constexpr (KG > 3) c = grad_pairs<KG, (KG > 3 ? 3 : 0), R>(pa, cm, op.m, pr, pi, lr, li); break;
+          }
+        }
+#pragma unroll
+        for (int d = 16; d; d >>= 1) c += __shfl_xor_sync(0xffffffffu, c, d);
+        if (lane == 0) gw[op.pad[0] | (op.pad[1] << 8)] += (double)c;
+      } else {
+        apply_op<KG, R>(op, pr, pi);
+        apply_op<KG, R>(op, lr, li);
+      }
+    }
+    if (live) {
+#pragma unroll
+      for (int r = 0; r < D; ++r) {
+        V2 v, w;
+        v.x = pr[r];
+        v.y = pi[r];
+        w.x = lr[r];
+        w.y = li[r];
+        smp[sb ^ soff[r]] = v;
+        sml[sb ^ soff[r]] = w;
+      }
+    }
+  }
+}
+
+template <int RANK>
+__device__ __forceinline__ void load_pair(uint32_t d1, uint32_t d2, const CUtensorMap* m1,
+                                          const CUtensorMap* m2, const int* c, uint32_t bar) {
+  tma_load<RANK>(d1, m1, c, bar);
+  tma_load<RANK>(d2, m2, c, bar);
+}
+
+template <int RANK>
+__device__ __forceinline__ void store_pair(uint32_t s1, uint32_t s2, const CUtensorMap* m1,
+                                           const CUtensorMap* m2, const int* c) {
+  tma_store<RANK>(m1, c, s1);
+  tma_store<RANK>(m2, c, s2);
+}
+
+// Reverse-sweep pass: as kfused_tma, staging the psi slice (tmap) and the
+// lambda slice (tmap2) on one mbarrier.  Gradient sums: per warp and
+// gradient operation in shared memory, then per block (warps in order) into
+// partials[gslot[j] * pstride + blockIdx.x].
+template <typename R, int KGF, int MINB>
+__global__ void __launch_bounds__(kFThreads, MINB)
+    kfused_adj(uint64_t n_blocks, const __grid_constant__ FusedParams<R> P,
+               double* __restrict__ partials, int pstride) {
+  typedef typename Cplx2<R>::T V2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar;
+  const uint32_t raw = smem_addr(smem_raw);
+  const uint32_t sbuf = (raw + 1023u) & ~1023u;
+  const uint32_t sbuf2 = sbuf + P.slice_bytes;  // slice bytes are a multiple of 1024
+  V2* smp = reinterpret_cast<V2*>(smem_raw + (sbuf - raw));
+  V2* sml = reinterpret_cast<V2*>(smem_raw + (sbuf2 - raw));
+  double* gacc = reinterpret_cast<double*>(smem_raw + (sbuf2 - raw) + P.slice_bytes);
+  constexpr int nw = kFThreads / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < nw * P.ngrad; i += kFThreads) gacc[i] = 0.0;
+  const uint32_t barp = smem_addr(&bar);
+  if (threadIdx.x == 0) {
+    mbar_init(barp, 1);
+    fence_proxy_async_smem();
+  }
+  __syncthreads();
+  uint32_t parity = 0;
+  for (uint64_t blk = blockIdx.x; blk < n_blocks; blk += gridDim.x) {
+    const uint64_t base = insert_zeros(blk, P.blk);
+    if (threadIdx.x < 32) {
+      bulk_wait_read_all();
+      __syncwarp();
+      if (lane == 0) mbar_arrive_expect_tx(barp, 2 * P.slice_bytes);
+      __syncwarp();
+      for (int k = lane; k < P.ncopies; k += 32) {
+        int c[5];
+        box_coords(P, base, k, c);
+        const uint32_t off = (uint32_t)k * P.box_bytes;
+        switch (P.rank) {
+          case 2: load_pair<2>(sbuf + off, sbuf2 + off, &P.tmap, &P.tmap2, c, barp); break;
+          case 3: load_pair<3>(sbuf + off, sbuf2 + off, &P.tmap, &P.tmap2, c, barp); break;
+          case 4: load_pair<4>(sbuf + off, sbuf2 + off, &P.tmap, &P.tmap2, c, barp); break;
+          default: load_pair<5>(sbuf + off, sbuf2 + off, &P.tmap, &P.tmap2, c, barp); break;
+        }
+      }
+    }
+    const bool ok = mbar_wait_bounded(barp, parity);
+    parity ^= 1;
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) atomicOr(&g_fused_status, kWaitTimeout);
+      break;
+    }
+    for (int g = 0; g < P.ngroups; ++g) {
+      run_group_adj<KGF, R>(smp, sml, P.m, P.gbits[g], P.ops, P.gop[g], P.gop[g + 1],
+                            gacc + warp * P.ngrad);
+      if (g + 1 < P.ngroups) __syncthreads();
+    }
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      for (int k = lane; k < P.ncopies; k += 32) {
+        int c[5];
+        box_coords(P, base, k, c);
+        const uint32_t off = (uint32_t)k * P.box_bytes;
+        switch (P.rank) {
+          case 2: store_pair<2>(sbuf + off, sbuf2 + off, &P.tmap, &P.tmap2, c); break;
+          case 3: store_pair<3>(sbuf + off, sbuf2 + off, &P.tmap, &P.tmap2, c); break;
+          case 4: store_pair<4>(sbuf + off, sbuf2 + off, &P.tmap, &P.tmap2, c); break;
+          default: store_pair<5>(sbuf + off, sbuf2 + off, &P.tmap, &P.tmap2, c); break;
+        }
+      }
+      bulk_commit();
+    }
+  }
+  if (threadIdx.x < 32) bulk_wait_all();
+  __syncthreads();
+  for (int j = threadIdx.x; j < P.ngrad; j += kFThreads) {
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t += gacc[w * P.ngrad + j];
+    partials[(size_t)P.gslot[j] * pstride + blockIdx.x] = t;
+  }
+}
+
 // ---- host: local order, TMA geometry, parameters -----------------------------------
 // TMA view of the state in 8-byte words (w = 1 or 2 per amplitude, lw =
 // log2 w): dim 0 = the 16 words of a 128-byte row, dim 1 = rows (amplitude
@@ -699,9 +908,10 @@ EncodeTiledFn encode_fn() {
 }
 
 template <typename R>
-bool build_tma(const TmaGeom& g, void* data, FusedParams<R>* P) {
+bool build_tma(const TmaGeom& g, void* data, FusedParams<R>* P, CUtensorMap* map = nullptr) {
   EncodeTiledFn fn = encode_fn();
   if (!fn || (reinterpret_cast<uintptr_t>(data) & 15)) return false;
+  if (!map) map = &P->tmap;
   cuuint64_t dims[5], strides[4];
   cuuint32_t box[5], estr[5] = {1, 1, 1, 1, 1};
   for (int d = 0; d < g.rank; ++d) {
@@ -713,7 +923,7 @@ bool build_tma(const TmaGeom& g, void* data, FusedParams<R>* P) {
   const uint64_t run_bytes = uint64_t(g.box[1]) * 128;
   const CUtensorMapL2promotion prom = run_bytes >= 256 ? CU_TENSOR_MAP_L2_PROMOTION_L2_256B
                                                        : CU_TENSOR_MAP_L2_PROMOTION_L2_128B;
-  if (fn(&P->tmap, CU_TENSOR_MAP_DATA_TYPE_UINT64, (cuuint32_t)g.rank, data, dims, strides, box,
+  if (fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, (cuuint32_t)g.rank, data, dims, strides, box,
          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, prom,
          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return false;
@@ -873,6 +1083,7 @@ void build_layers(const FusedPass& pass, const int* pos_of, FusedParams<R>* P) {
 // order: the staged bits in local order (order[0..L) = 0..L-1)
 template <typename R>
 bool build_params(const FusedPass& pass, const std::vector<int>& order, FusedParams<R>* P) {
+  P->ngrad = 0;
   const std::vector<int>& S = pass.S;
   P->m = (int)S.size();
   P->L = pass.L;
@@ -937,6 +1148,20 @@ bool build_params(const FusedPass& pass, const std::vector<int>& order, FusedPar
         o.m[0] = (R)f.m[0].re;
         o.m[1] = (R)f.m[0].im;
         o.cls = (f.m[0].re == -1.0 && f.m[0].im == 0.0) ? 1 : 0;
+      } else if (f.type == FG_GRAD) {
+        // generator on bit t within the control mask; local gradient index in pad
+        o.b0 = (uint8_t)gl(f.t);
+        o.cls = (uint8_t)f.pauli;
+        if (!f.pauli) {  // Hermitian generator [[a, b], [conj b, d]]
+          o.m[0] = (R)f.m[0].re;
+          o.m[1] = (R)f.m[3].re;
+          o.m[2] = (R)f.m[1].re;
+          o.m[3] = (R)f.m[1].im;
+        }
+        const int j = P->ngrad++;
+        o.pad[0] = (uint8_t)(j & 0xff);
+        o.pad[1] = (uint8_t)(j >> 8);
+        P->gslot[j] = f.slot;
       } else {
         const int x = gl(f.a), y = gl(f.b);
         o.b0 = (uint8_t)std::min(x, y);
@@ -1044,7 +1269,79 @@ sv_status run_pass(void* data, int n, cudaStream_t st, const FusedPass& pass) {
   return check_launch("fused pass kernel");
 }
 
+template <typename R>
+bool adj_pass_ok(int n, const FusedPass& pass) {
+  TmaGeom geo;
+  return tma_geometry(pass.S, pass.L, n, sizeof(R) == 4 ? 0 : 1, &geo);
+}
+
+template <typename R>
+sv_status run_adj_pass(void* psi, void* lam, int n, cudaStream_t st, const FusedPass& pass,
+                       double* partials, int pstride) {
+  static FusedParams<R> P;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lk(mu);
+  const int kg = pass.groups.empty() ? 1 : pass.groups[0].k;
+  for (const FusedGroup& g : pass.groups)
+    if (g.k != kg) {
+      set_error("fused reverse pass: groups of unequal width");
+      return SV_ERR_INVALID;
+    }
+  const int lw = sizeof(R) == 4 ? 0 : 1;
+  TmaGeom geo;
+  if (!tma_geometry(pass.S, pass.L, n, lw, &geo) || !build_params(pass, geo.order, &P) ||
+      !verify_tma(geo, pass.S, n, lw, 0) ||
+      !verify_tma(geo, pass.S, n, lw, (uint64_t(1) << (n - (int)pass.S.size())) - 1) ||
+      !build_tma(geo, psi, &P) || !build_tma(geo, lam, &P, &P.tmap2)) {
+    set_error("fused reverse pass: no bulk-copy geometry for this pass");
+    return SV_ERR_UNSUPPORTED;
+  }
+  typedef void (*Kern)(uint64_t, const FusedParams<R>, double*, int);
+  constexpr int MB = sizeof(R) == 4 ? 2 : 1;
+  const Kern kern = kg <= 1   ? kfused_adj<R, 1, MB>
+                    : kg == 2 ? kfused_adj<R, 2, MB>
+                              : kfused_adj<R, 3, MB>;
+  if (kg > 3) {
+    set_error("fused reverse pass: register groups wider than 3 qubits");
+    return SV_ERR_INVALID;
+  }
+  const size_t smem =
+      1024 + 2 * (size_t)P.slice_bytes + sizeof(double) * (kFThreads / 32) * P.ngrad;
+  static std::map<std::pair<const void*, size_t>, int> resident;
+  int& res = resident[{reinterpret_cast<const void*>(kern), smem}];
+  if (!res) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&res, kern, kFThreads, smem) != cudaSuccess ||
+        res < 1) {
+      cudaGetLastError();
+      res = 1;
+    }
+  }
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const uint64_t nblk = uint64_t(1) << (n - P.m);
+  const uint64_t grid = std::min<uint64_t>({nblk, (uint64_t)sms * res, (uint64_t)pstride});
+  ProfScope prof(st, sizeof(R) == 4 ? "kfused_adj_c64" : "kfused_adj_c128");
+  kern<<<(unsigned)grid, kFThreads, smem, st>>>(nblk, P, partials, pstride);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return check_launch("fused reverse pass kernel");
+}
+
+static_assert(sizeof(FusedParams<double>) <= 32000, "kernel parameters above the launch limit");
+static_assert(sizeof(FusedParams<float>) <= 32000, "kernel parameters above the launch limit");
+
 }  // namespace
+
+bool fused_reverse_ok(sv_dtype dt, int n, const FusedPass& pass) {
+  return dt == SV_C64 ? adj_pass_ok<float>(n, pass) : adj_pass_ok<double>(n, pass);
+}
+
+sv_status launch_fused_reverse_pass(void* psi, void* lam, sv_dtype dt, int n, cudaStream_t st,
+                                    const FusedPass& pass, double* partials, int pstride) {
+  return dt == SV_C64 ? run_adj_pass<float>(psi, lam, n, st, pass, partials, pstride)
+                      : run_adj_pass<double>(psi, lam, n, st, pass, partials, pstride);
+}
 
 sv_status launch_fused_pass(void* data, sv_dtype dt, int n, cudaStream_t st,
                             const FusedPass& pass) {

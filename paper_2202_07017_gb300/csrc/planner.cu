@@ -51,6 +51,71 @@ void mul2_left(const cd* b, cd* a) {
   for (int e = 0; e < 4; ++e) a[e] = r[e];
 }
 
+// The FGate of circuit gate g (index i) with matrix G, in bit positions.
+FGate classify(const sv_gate& g, int i, int n, const HostMatrix& G, int kmax) {
+  FGate f;
+  f.orig = i;
+  f.origs.push_back(i);
+  int tp[SV_MAX_TARGETS];
+  uint64_t cm = 0;
+  for (int j = 0; j < g.n_tar; ++j) {
+    tp[j] = n - 1 - g.targets[j];
+    f.qmask |= uint64_t(1) << tp[j];
+  }
+  for (int j = 0; j < g.n_ctrl; ++j) cm |= uint64_t(1) << (n - 1 - g.controls[j]);
+  f.qmask |= cm;
+  const int k = g.n_tar, d = 1 << k;
+  bool diag = true, ones = true;
+  for (int r = 0; r < d; ++r)
+    for (int q = 0; q < d; ++q)
+      if (r != q && !is_zero(G.at(r, q))) diag = false;
+  for (int r = 0; r + 1 < d; ++r)
+    if (!is_one(G.at(r, r))) ones = false;
+  bool swap = k == 2;
+  if (swap) {
+    static const int perm[4] = {0, 2, 1, 3};
+    for (int r = 0; r < 4; ++r)
+      for (int q = 0; q < 4; ++q)
+        if (q == perm[r] ? !is_one(G.at(r, q)) : !is_zero(G.at(r, q))) swap = false;
+  }
+  if (diag && ones) {
+    f.type = FG_PHASE;
+    f.cmask = f.qmask;
+    f.m[0] = G.at(d - 1, d - 1);
+  } else if (swap) {
+    f.type = FG_SWAP;
+    f.a = tp[0];
+    f.b = tp[1];
+    f.cmask = cm;
+  } else if (k == 1) {
+    f.type = FG_1Q;
+    f.t = tp[0];
+    f.cmask = cm;
+    for (int e = 0; e < 4; ++e) f.m[e] = G.m[e];
+  } else {
+    f.type = FG_ALONE;
+  }
+  if (popc(f.qmask) > kmax) f.type = FG_ALONE;
+  return f;
+}
+
+// Appends f, multiplying an uncontrolled 1-qubit gate into the previous
+// operation on its qubit when that is an uncontrolled 1-qubit gate.
+void push_fgate(FGate f, std::vector<int>* last, std::vector<FGate>* out) {
+  if (f.type == FG_1Q && f.cmask == 0) {
+    const int p = (*last)[f.t];
+    if (p >= 0 && (*out)[p].type == FG_1Q && (*out)[p].cmask == 0 && (*out)[p].t == f.t) {
+      mul2_left(f.m, (*out)[p].m);
+      (*out)[p].origs.push_back(f.orig);
+      (*out)[p].orig = f.orig;
+      return;
+    }
+  }
+  out->push_back(std::move(f));
+  for (int b = 0; b < 64; ++b)
+    if ((out->back().qmask >> b) & 1) (*last)[b] = (int)out->size() - 1;
+}
+
 bool to_fgates(const sv_circuit* c, const double* theta, int kmax, std::vector<FGate>* out) {
   const int n = c->n_qubits;
   std::vector<int> last(64, -1);
@@ -61,62 +126,131 @@ bool to_fgates(const sv_circuit* c, const double* theta, int kmax, std::vector<F
       set_error("gate %d: cannot build matrix", i);
       return false;
     }
+    push_fgate(classify(g, i, n, G, kmax), &last, out);
+  }
+  return true;
+}
+
+// 2x2 complex products (row-major)
+void mul2(const cd* a, const cd* b, cd* out) {  // out = a b
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) {
+      double re = 0, im = 0;
+      for (int k = 0; k < 2; ++k) {
+        const cd x = a[i * 2 + k], y = b[k * 2 + j];
+        re += x.re * y.re - x.im * y.im;
+        im += x.re * y.im + x.im * y.re;
+      }
+      out[i * 2 + j] = {re, im};
+    }
+}
+
+// Reverse sweep over [lo, hi): gate hi-1 first, each as its adjoint, a
+// parameterised gate preceded by its FG_GRAD.  Uncontrolled 1-qubit
+// adjoints are kept pending per qubit (their product W, not yet applied)
+// until another kind of gate touches the qubit; a gradient met while W is
+// pending is evaluated on the untransformed states with the generator
+// W^dagger P W (Im<W lambda|P|W psi> = Im<lambda|W^dagger P W|psi>), so a
+// run RZ, RY, RX on one qubit costs one un-apply.  A parameterised gate
+// wider than kmax stays unfused with its gradient.
+bool to_fgates_reverse(const sv_circuit* c, const double* theta, int lo, int hi,
+                       const std::vector<int>& slot_of, int kmax, std::vector<FGate>* out) {
+  const int n = c->n_qubits;
+  std::vector<int> last(64, -1);
+  struct Pend {
+    bool on = false;
+    cd W[4];
+    int orig = -1;
+  };
+  std::vector<Pend> pend(64);
+  auto flush = [&](int t) {
+    if (!pend[t].on) return;
     FGate f;
-    f.orig = i;
-    f.origs.push_back(i);
-    int tp[SV_MAX_TARGETS];
-    uint64_t cm = 0;
-    for (int j = 0; j < g.n_tar; ++j) {
-      tp[j] = n - 1 - g.targets[j];
-      f.qmask |= uint64_t(1) << tp[j];
+    f.type = FG_1Q;
+    f.t = t;
+    f.qmask = uint64_t(1) << t;
+    f.cmask = 0;
+    for (int e = 0; e < 4; ++e) f.m[e] = pend[t].W[e];
+    f.orig = pend[t].orig;
+    f.origs.push_back(f.orig);
+    push_fgate(std::move(f), &last, out);
+    pend[t].on = false;
+  };
+  HostMatrix G, D;
+  for (int i = hi - 1; i >= lo; --i) {
+    const sv_gate& g = c->gates[i];
+    if (!gate_matrix(g, theta, c->mat_pool, &G)) {
+      set_error("gate %d: cannot build matrix", i);
+      return false;
     }
-    for (int j = 0; j < g.n_ctrl; ++j) cm |= uint64_t(1) << (n - 1 - g.controls[j]);
-    f.qmask |= cm;
-    const int k = g.n_tar, d = 1 << k;
-    bool diag = true, ones = true;
+    const int d = 1 << G.k;
+    D.k = G.k;
     for (int r = 0; r < d; ++r)
-      for (int q = 0; q < d; ++q)
-        if (r != q && !is_zero(G.at(r, q))) diag = false;
-    for (int r = 0; r + 1 < d; ++r)
-      if (!is_one(G.at(r, r))) ones = false;
-    bool swap = k == 2;
-    if (swap) {
-      static const int perm[4] = {0, 2, 1, 3};
-      for (int r = 0; r < 4; ++r)
-        for (int q = 0; q < 4; ++q)
-          if (q == perm[r] ? !is_one(G.at(r, q)) : !is_zero(G.at(r, q))) swap = false;
-    }
-    if (diag && ones) {
-      f.type = FG_PHASE;
-      f.cmask = f.qmask;
-      f.m[0] = G.at(d - 1, d - 1);
-    } else if (swap) {
-      f.type = FG_SWAP;
-      f.a = tp[0];
-      f.b = tp[1];
-      f.cmask = cm;
-    } else if (k == 1) {
-      f.type = FG_1Q;
-      f.t = tp[0];
-      f.cmask = cm;
-      for (int e = 0; e < 4; ++e) f.m[e] = G.m[e];
-    } else {
-      f.type = FG_ALONE;
-    }
-    if (popc(f.qmask) > kmax) f.type = FG_ALONE;
+      for (int q = 0; q < d; ++q) {
+        const cd z = G.at(q, r);
+        D.m[r * d + q] = {z.re, -z.im};
+      }
+    FGate f = classify(g, i, n, D, kmax);
+    const int pauli = g.param < 0 ? 0 : g.kind == SV_GATE_RX ? 1 : g.kind == SV_GATE_RY ? 2 : 3;
     if (f.type == FG_1Q && f.cmask == 0) {
-      const int p = last[f.t];
-      if (p >= 0 && (*out)[p].type == FG_1Q && (*out)[p].cmask == 0 && (*out)[p].t == f.t) {
-        mul2_left(f.m, (*out)[p].m);
-        (*out)[p].origs.push_back(i);
-        (*out)[p].orig = i;
-        continue;
+      const int t = f.t;
+      if (pauli) {
+        FGate gr;
+        gr.type = FG_GRAD;
+        gr.qmask = uint64_t(1) << t;
+        gr.t = t;
+        gr.cmask = 0;
+        gr.pauli = pauli;
+        gr.slot = slot_of[i];
+        gr.orig = i;
+        if (pend[t].on) {  // generator W^dagger P W, stored as a Hermitian 2x2
+          static const cd PX[4] = {{0, 0}, {1, 0}, {1, 0}, {0, 0}};
+          static const cd PY[4] = {{0, 0}, {0, -1}, {0, 1}, {0, 0}};
+          static const cd PZ[4] = {{1, 0}, {0, 0}, {0, 0}, {-1, 0}};
+          const cd* P = pauli == 1 ? PX : pauli == 2 ? PY : PZ;
+          const cd* W = pend[t].W;
+          const cd Wd[4] = {{W[0].re, -W[0].im}, {W[2].re, -W[2].im},
+                            {W[1].re, -W[1].im}, {W[3].re, -W[3].im}};
+          cd PW[4], M[4];
+          mul2(P, W, PW);
+          mul2(Wd, PW, M);
+          gr.pauli = 0;  // general generator in m
+          for (int e = 0; e < 4; ++e) gr.m[e] = M[e];
+        }
+        push_fgate(std::move(gr), &last, out);
+      }
+      if (pend[t].on) {
+        cd r[4];
+        mul2(f.m, pend[t].W, r);  // this adjoint acts after the pending product
+        for (int e = 0; e < 4; ++e) pend[t].W[e] = r[e];
+      } else {
+        pend[t].on = true;
+        for (int e = 0; e < 4; ++e) pend[t].W[e] = f.m[e];
+      }
+      pend[t].orig = i;
+      continue;
+    }
+    for (int b = 0; b < 64; ++b)
+      if ((f.qmask >> b) & 1) flush(b);
+    if (pauli) {
+      if (f.type == FG_ALONE) {
+        f.pauli = pauli;
+        f.slot = slot_of[i];
+      } else {
+        FGate gr;
+        gr.type = FG_GRAD;
+        gr.qmask = f.qmask;
+        gr.t = n - 1 - g.targets[0];
+        gr.cmask = f.qmask & ~(uint64_t(1) << gr.t);
+        gr.pauli = pauli;
+        gr.slot = slot_of[i];
+        gr.orig = i;
+        push_fgate(std::move(gr), &last, out);
       }
     }
-    out->push_back(f);
-    for (int b = 0; b < 64; ++b)
-      if ((f.qmask >> b) & 1) last[b] = (int)out->size() - 1;
+    push_fgate(std::move(f), &last, out);
   }
+  for (int b = 0; b < 64; ++b) flush(b);
   return true;
 }
 
@@ -138,11 +272,20 @@ FusionConfig fusion_config(int n, sv_dtype dt, int fuse_k) {
   return c;
 }
 
-bool plan_fusion(const sv_circuit* c, const double* theta, const FusionConfig& cfg,
+FusionConfig fusion_config_reverse(int n, sv_dtype dt, int fuse_k) {
+  FusionConfig c = fusion_config(n, dt, std::min(fuse_k, 3));  // two 2^k tiles per thread
+  if (c.m > 10) {
+    c.m -= 1;
+    if (c.m - c.L < c.fuse_k) c.L = std::max(1, c.m - c.fuse_k);
+  }
+  return c;
+}
+
+namespace {
+
+// Passes (steps 2 and 3 of the planning) over the operation list F.
+void form_passes(const std::vector<FGate>& F, int n, const FusionConfig& cfg,
                  std::vector<FusionItem>* out) {
-  const int n = c->n_qubits;
-  std::vector<FGate> F;
-  if (!to_fgates(c, theta, std::min(cfg.fuse_k, cfg.m), &F)) return false;
   std::vector<char> done(F.size(), 0);
   const uint64_t lowL = (cfg.L >= 64) ? ~uint64_t(0) : ((uint64_t(1) << cfg.L) - 1);
   size_t first = 0;
@@ -155,6 +298,8 @@ bool plan_fusion(const sv_circuit* c, const double* theta, const FusionConfig& c
       for (int o : f0.origs) {
         FusionItem it;
         it.gate = o;
+        it.pauli = f0.pauli;
+        it.slot = f0.slot;
         out->push_back(it);
       }
       done[first] = 1;
@@ -234,6 +379,25 @@ bool plan_fusion(const sv_circuit* c, const double* theta, const FusionConfig& c
     for (int j : placed) done[j] = 1;
     out->push_back(std::move(item));
   }
+}
+
+}  // namespace
+
+bool plan_fusion(const sv_circuit* c, const double* theta, const FusionConfig& cfg,
+                 std::vector<FusionItem>* out) {
+  std::vector<FGate> F;
+  if (!to_fgates(c, theta, std::min(cfg.fuse_k, cfg.m), &F)) return false;
+  form_passes(F, c->n_qubits, cfg, out);
+  return true;
+}
+
+bool plan_fusion_reverse(const sv_circuit* c, const double* theta, int lo, int hi,
+                         const std::vector<int>& slot_of, const FusionConfig& cfg,
+                         std::vector<FusionItem>* out) {
+  std::vector<FGate> F;
+  if (!to_fgates_reverse(c, theta, lo, hi, slot_of, std::min(cfg.fuse_k, cfg.m), &F))
+    return false;
+  form_passes(F, c->n_qubits, cfg, out);
   return true;
 }
 

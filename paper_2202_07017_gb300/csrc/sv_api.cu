@@ -704,6 +704,137 @@ sv_status sv_grad(sv_state s, const sv_circuit* c, const double* theta, const sv
   return reverse_sweep(s, c, theta, H, checkpoint_gates, n_checkpoints, energy, grad);
 }
 
+sv_status sv_grad_fused(sv_state s, const sv_circuit* c, const double* theta,
+                        const sv_pauli_sum* H, const int32_t* checkpoint_gates,
+                        int n_checkpoints, int fuse_k, double* energy, double* grad) {
+  if (fuse_k == 0)
+    return sv_grad(s, c, theta, H, checkpoint_gates, n_checkpoints, energy, grad);
+  if (!valid_state(s) || !energy || !grad) return SV_ERR_INVALID;
+  if (!valid_circuit(s, c, theta) || !valid_pauli(s, H) || !valid_grad_circuit(c))
+    return SV_ERR_INVALID;
+  if (fuse_k < 2 || fuse_k > 5) {
+    set_error("sv_grad_fused: fuse_k = %d: expected 0 or 2..5", fuse_k);
+    return SV_ERR_INVALID;
+  }
+  if (n_checkpoints < 0 || (n_checkpoints > 0 && !checkpoint_gates)) {
+    set_error("sv_grad_fused: bad checkpoint list");
+    return SV_ERR_INVALID;
+  }
+  for (int k = 0; k < n_checkpoints; ++k)
+    if (checkpoint_gates[k] < 0 || checkpoint_gates[k] >= c->n_gates ||
+        (k > 0 && checkpoint_gates[k] <= checkpoint_gates[k - 1])) {
+      set_error("sv_grad_fused: checkpoint gates must increase within 0..%d", c->n_gates - 1);
+      return SV_ERR_INVALID;
+    }
+  sv_status st = ensure_work(s, 0);
+  if (st == SV_OK) st = ensure_work(s, 1);
+  if (st) return st;
+  while ((int)s->ckpt.size() < n_checkpoints) {
+    void* p = nullptr;
+    SV_CUDA_TRY(cudaMalloc(&p, s->bytes()));
+    s->ckpt.push_back(p);
+  }
+  // segments between checkpoints, fused separately (fusion reorders gates on
+  // disjoint qubits, never across a checkpoint)
+  std::vector<int> bounds(1, 0);
+  for (int k = 0; k < n_checkpoints; ++k)
+    if (checkpoint_gates[k] > bounds.back()) bounds.push_back(checkpoint_gates[k]);
+  bounds.push_back(c->n_gates);
+  auto ckpt_at = [&](int gate) {
+    for (int k = 0; k < n_checkpoints; ++k)
+      if (checkpoint_gates[k] == gate) return k;
+    return -1;
+  };
+  for (size_t i = 0; i + 1 < bounds.size(); ++i) {
+    const int k = ckpt_at(bounds[i]);
+    if (k >= 0)
+      SV_CUDA_TRY(cudaMemcpyAsync(s->ckpt[k], s->data, s->bytes(), cudaMemcpyDeviceToDevice,
+                                  s->stream));
+    sv_circuit sub = *c;
+    sub.gates = c->gates + bounds[i];
+    sub.n_gates = bounds[i + 1] - bounds[i];
+    st = sv_apply_circuit(s, &sub, theta, fuse_k);
+    if (st) return st;
+  }
+  SV_CUDA_TRY(cudaMemcpyAsync(s->work[0], s->data, s->bytes(), cudaMemcpyDeviceToDevice,
+                              s->stream));
+  // plan every reverse segment; without a bulk-copy geometry use the unfused sweep
+  std::vector<int> slot_of(c->n_gates, -1);
+  int n_pg = 0;
+  for (int i = 0; i < c->n_gates; ++i)
+    if (c->gates[i].param >= 0) slot_of[i] = n_pg++;
+  const FusionConfig cfg = fusion_config_reverse(s->n, s->dt, fuse_k);
+  std::vector<std::vector<FusionItem>> plans(bounds.size() - 1);
+  bool fusable = s->n >= 10;
+  for (size_t i = 0; fusable && i + 1 < bounds.size(); ++i) {
+    if (!plan_fusion_reverse(c, theta, bounds[i], bounds[i + 1], slot_of, cfg, &plans[i]))
+      return SV_ERR_INVALID;
+    for (const FusionItem& it : plans[i])
+      if (it.is_pass && !fused_reverse_ok(s->dt, s->n, it.pass)) fusable = false;
+  }
+  if (!fusable) return reverse_sweep(s, c, theta, H, checkpoint_gates, n_checkpoints, energy, grad);
+  void* psi = s->work[0];
+  void* lam = s->work[1];
+  const int G = kRedMaxBlocks;  // partial slots per gradient (>= any pass's block count)
+  st = ensure_partials(s, (size_t)n_pg * G + n_pg + kRedMaxBlocks);
+  if (st) return st;
+  st = apply_pauli_into(lam, psi, s, H, s->dres);
+  if (st) return st;
+  if (n_pg)
+    SV_CUDA_TRY(cudaMemsetAsync(s->partials, 0, sizeof(double) * (size_t)n_pg * G, s->stream));
+  double* slots = s->partials + (size_t)n_pg * G;
+  HostMatrix Gm, D;
+  for (size_t i = bounds.size() - 1; i-- > 0;) {
+    for (const FusionItem& it : plans[i]) {
+      if (it.is_pass) {
+        st = launch_fused_reverse_pass(psi, lam, s->dt, s->n, s->stream, it.pass, s->partials, G);
+      } else {
+        const sv_gate& g = c->gates[it.gate];
+        gate_matrix(g, theta, c->mat_pool, &Gm);
+        dagger(Gm, &D);
+        int tp[SV_MAX_TARGETS], cp[SV_MAX_CONTROLS];
+        to_bits(s->n, g.targets, g.n_tar, tp);
+        to_bits(s->n, g.controls, g.n_ctrl, cp);
+        if (g.n_tar == 1) {
+          st = launch_adjoint_1q(psi, lam, s->dt, s->n, s->stream, tp[0], g.n_ctrl, cp, D,
+                                 it.slot >= 0 ? it.pauli : 0,
+                                 it.slot >= 0 ? s->partials + (size_t)it.slot * G : nullptr,
+                                 nullptr);
+        } else {
+          st = launch_gate(psi, s->dt, s->n, s->stream, g.n_tar, tp, g.n_ctrl, cp, D);
+          if (st == SV_OK)
+            st = launch_gate(lam, s->dt, s->n, s->stream, g.n_tar, tp, g.n_ctrl, cp, D);
+        }
+      }
+      if (st) return st;
+    }
+    const int k = ckpt_at(bounds[i]);
+    if (k >= 0)
+      SV_CUDA_TRY(cudaMemcpyAsync(psi, s->ckpt[k], s->bytes(), cudaMemcpyDeviceToDevice,
+                                  s->stream));
+  }
+  if (n_pg) {
+    st = launch_finish(s->partials, G, n_pg, slots, s->stream, false);
+    if (st) return st;
+  }
+  std::vector<double> gs(n_pg + 1);
+  if (n_pg)
+    SV_CUDA_TRY(cudaMemcpyAsync(gs.data(), slots, n_pg * sizeof(double), cudaMemcpyDeviceToHost,
+                                s->stream));
+  SV_CUDA_TRY(cudaMemcpyAsync(s->hres, s->dres, sizeof(double), cudaMemcpyDeviceToHost,
+                              s->stream));
+  SV_CUDA_TRY(cudaStreamSynchronize(s->stream));
+  if (take_fused_status()) {
+    set_error("a fused pass gave up waiting for its bulk copies");
+    return SV_ERR_TIMEOUT;
+  }
+  *energy = s->hres[0];
+  for (int p = 0; p < c->n_params; ++p) grad[p] = 0.0;
+  for (int i = 0; i < c->n_gates; ++i)
+    if (slot_of[i] >= 0) grad[c->gates[i].param] += gs[slot_of[i]];
+  return SV_OK;
+}
+
 sv_status sv_sync(sv_state s) {
   if (!valid_state(s)) return SV_ERR_INVALID;
   SV_CUDA_TRY(cudaStreamSynchronize(s->stream));

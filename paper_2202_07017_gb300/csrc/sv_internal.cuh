@@ -124,9 +124,14 @@ sv_status launch_finish(const double* src, int count, int slots, double* dst,
 
 // ---- fusion (planner.cu, fused_kernels.cu) ------------------------------------
 // A gate as the fused kernels see it, in amplitude-index bit positions.
-enum { FG_1Q = 0, FG_PHASE = 1, FG_SWAP = 2, FG_ALONE = 3 };
+// FG_GRAD (reverse sweeps only): accumulate Im<lambda|P|psi> for generator
+// `pauli` (1 X, 2 Y, 3 Z; 0: the Hermitian 2x2 in m) on bit t, restricted to
+// the control bits cmask, into gradient slot `slot`; it precedes the
+// un-applied gate whose derivative it gives.
+enum { FG_1Q = 0, FG_PHASE = 1, FG_SWAP = 2, FG_ALONE = 3, FG_GRAD = 4 };
 struct FGate {
   int type = FG_ALONE;
+  int pauli = 0, slot = -1;  // FG_GRAD; an FG_ALONE gate of a reverse sweep with a gradient
   uint64_t qmask = 0;  // every bit the gate touches (targets and controls)
   uint64_t cmask = 0;  // control bits (FG_1Q, FG_SWAP); all bits for FG_PHASE
   int t = 0, a = 0, b = 0;  // FG_1Q target bit; FG_SWAP bits
@@ -152,6 +157,7 @@ struct FusionItem {
   bool is_pass = false;
   FusedPass pass;            // when is_pass
   int gate = -1;             // circuit gate index to run unfused otherwise
+  int pauli = 0, slot = -1;  // reverse sweeps: the unfused gate's gradient, if any
 };
 
 struct FusionConfig {
@@ -163,12 +169,29 @@ struct FusionConfig {
 };
 
 FusionConfig fusion_config(int n, sv_dtype dt, int fuse_k);
+// Reverse sweeps stage two slices (psi, lambda) and hold two register tiles
+// per thread: one staged bit fewer, register groups of at most 3 qubits.
+FusionConfig fusion_config_reverse(int n, sv_dtype dt, int fuse_k);
 // Plans `c` into passes and unfused gates; returns false (with an error
 // set) if a matrix cannot be built.
 bool plan_fusion(const sv_circuit* c, const double* theta, const FusionConfig& cfg,
                  std::vector<FusionItem>* out);
+// Plan of the reverse sweep over gates [lo, hi): gates hi-1 .. lo as their
+// adjoints, each parameterised gate preceded by its FG_GRAD; slot_of[i] is
+// the gradient slot of circuit gate i (or -1).  Unfused items carry the
+// circuit gate (to be un-applied) and its gradient slot.
+bool plan_fusion_reverse(const sv_circuit* c, const double* theta, int lo, int hi,
+                         const std::vector<int>& slot_of, const FusionConfig& cfg,
+                         std::vector<FusionItem>* out);
 sv_status launch_fused_pass(void* data, sv_dtype dt, int n, cudaStream_t st,
                             const FusedPass& pass);
+// Reverse-sweep pass over psi and lambda (gradient operations write
+// partials[slot * pstride + block], pstride >= the pass's block count; at
+// most pstride blocks are launched).  fused_reverse_ok: the pass has a
+// bulk-copy geometry (else the caller runs the unfused sweep).
+bool fused_reverse_ok(sv_dtype dt, int n, const FusedPass& pass);
+sv_status launch_fused_reverse_pass(void* psi, void* lam, sv_dtype dt, int n, cudaStream_t st,
+                                    const FusedPass& pass, double* partials, int pstride);
 // Reads and clears the fused-pass device status word of the current device
 // (kWaitTimeout = 1: a bounded wait inside a pass gave up).
 unsigned take_fused_status();

@@ -52,7 +52,7 @@ class SvError(RuntimeError):
 EXPORTS = ("sv_alloc", "sv_wrap", "sv_free", "sv_set_stream", "sv_info", "sv_init",
            "sv_upload", "sv_download", "sv_copy", "sv_apply_gate", "sv_apply_circuit",
            "sv_norm", "sv_expval", "sv_expval_async", "sv_apply_pauli_sum", "sv_adjoint",
-           "sv_grad", "sv_sync", "sv_last_error", "sv_launch_count", "sv_version",
+           "sv_grad", "sv_grad_fused", "sv_sync", "sv_last_error", "sv_launch_count", "sv_version",
            "sv_profile_start", "sv_profile_stop", "sv_fusion_plan", "sv_expval_noalloc",
            "sv_probabilities", "sv_sample", "sv_pauli_rotation", "sv_trotter",
            "sv_batch_create", "sv_batch_plan", "sv_batch_info", "sv_batch_kernel", "sv_batch_run", "sv_batch_run_graph", "sv_batch_grad",
@@ -96,6 +96,8 @@ def load(build: bool = True):
         "sv_adjoint": [c_vp, P(SvCircuit), P(c_dbl), P(SvPauliSum), P(c_dbl), P(c_dbl)],
         "sv_grad": [c_vp, P(SvCircuit), P(c_dbl), P(SvPauliSum), P(c_i32), ctypes.c_int,
                     P(c_dbl), P(c_dbl)],
+        "sv_grad_fused": [c_vp, P(SvCircuit), P(c_dbl), P(SvPauliSum), P(c_i32), ctypes.c_int,
+                          ctypes.c_int, P(c_dbl), P(c_dbl)],
         "sv_sync": [c_vp],
         "sv_profile_start": [],
         "sv_pauli_rotation": [c_vp, c_u64, c_u64, c_dbl],
@@ -106,7 +108,7 @@ def load(build: bool = True):
                             ctypes.c_int, P(c_vp)],
         "sv_batch_plan": [P(SvCircuit), P(SvPauliSum), ctypes.c_int, ctypes.c_int, P(c_i32)],
         "sv_batch_info": [c_vp, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int)],
-        "sv_batch_kernel": [c_vp, P(ctypes.c_int)],
+        "sv_batch_kernel": [c_vp, P(ctypes.c_int), P(ctypes.c_int)],
         "sv_batch_run": [c_vp, c_vp, c_vp, c_vp, c_vp],
         "sv_batch_run_graph": [c_vp, c_vp, c_vp, c_vp, c_vp],
         "sv_batch_grad": [P(SvCircuit), P(SvPauliSum), ctypes.c_int, P(c_i32), ctypes.c_int,
@@ -375,6 +377,22 @@ def sv_grad(h: int, circuit, theta, terms, checkpoint_gates: Sequence[int] = ())
     _check(load().sv_grad(c_vp(h), ctypes.byref(pc.c), tp, ctypes.byref(pp.s),
                           ck.ctypes.data_as(ctypes.POINTER(c_i32)), len(checkpoint_gates),
                           ctypes.byref(e), g.ctypes.data_as(ctypes.POINTER(c_dbl))))
+    return e.value, g[:pc.n_params]
+
+
+def sv_grad_fused(h: int, circuit, theta, terms, checkpoint_gates: Sequence[int] = (),
+                  fuse_k: int = 4) -> Tuple[float, np.ndarray]:
+    """sv_grad with the forward circuit and the reverse sweep in fused passes."""
+    pc = pack_circuit(circuit)
+    pp = pack_pauli(terms, pc.n_qubits)
+    keep, tp = _theta_ptr(theta)
+    ck = np.ascontiguousarray(list(checkpoint_gates) or [0], dtype=np.int32)
+    e = c_dbl()
+    g = np.zeros(max(1, pc.n_params), np.float64)
+    _check(load().sv_grad_fused(c_vp(h), ctypes.byref(pc.c), tp, ctypes.byref(pp.s),
+                                ck.ctypes.data_as(ctypes.POINTER(c_i32)), len(checkpoint_gates),
+                                int(fuse_k), ctypes.byref(e),
+                                g.ctypes.data_as(ctypes.POINTER(c_dbl))))
     return e.value, g[:pc.n_params]
 
 
