@@ -147,6 +147,15 @@ sv_status sv_init(sv_state s, uint64_t basis_index);
 sv_status sv_upload(sv_state s, const void* host);
 sv_status sv_download(sv_state s, void* host);
 
+/* Page-locked host buffers for sv_upload / sv_download, allocated through
+ * the same CUDA runtime as the library (so the copies see them as pinned
+ * and run at the host link's bandwidth).  sv_host_alloc writes the buffer
+ * to *out; SV_ERR_OOM if the host cannot pin `bytes`, SV_ERR_INVALID for a
+ * null out or zero bytes.  sv_host_free releases a buffer from
+ * sv_host_alloc (NULL is a no-op). */
+sv_status sv_host_alloc(size_t bytes, void** out);
+sv_status sv_host_free(void* p);
+
 /* Copy the amplitudes of `src` into `dst` (same n and dtype). Asynchronous. */
 sv_status sv_copy(sv_state dst, sv_state src);
 

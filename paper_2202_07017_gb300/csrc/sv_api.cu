@@ -333,6 +333,21 @@ sv_status sv_init(sv_state s, uint64_t basis_index) {
   return launch_init(s->data, s->dt, s->n, s->stream, basis_index);
 }
 
+sv_status sv_host_alloc(size_t bytes, void** out) {
+  if (!out || !bytes) {
+    set_error("sv_host_alloc: null output or zero bytes");
+    return SV_ERR_INVALID;
+  }
+  *out = nullptr;
+  SV_CUDA_TRY(cudaHostAlloc(out, bytes, cudaHostAllocDefault));
+  return SV_OK;
+}
+
+sv_status sv_host_free(void* p) {
+  if (p) SV_CUDA_TRY(cudaFreeHost(p));
+  return SV_OK;
+}
+
 sv_status sv_upload(sv_state s, const void* host) {
   if (!valid_state(s) || !host) return SV_ERR_INVALID;
   SV_CUDA_TRY(cudaMemcpyAsync(s->data, host, s->bytes(), cudaMemcpyHostToDevice, s->stream));

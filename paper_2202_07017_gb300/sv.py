@@ -50,7 +50,7 @@ class SvError(RuntimeError):
 
 
 EXPORTS = ("sv_alloc", "sv_wrap", "sv_free", "sv_set_stream", "sv_info", "sv_init",
-           "sv_upload", "sv_download", "sv_copy", "sv_apply_gate", "sv_apply_circuit",
+           "sv_upload", "sv_download", "sv_host_alloc", "sv_host_free", "sv_copy", "sv_apply_gate", "sv_apply_circuit",
            "sv_norm", "sv_expval", "sv_expval_async", "sv_apply_pauli_sum", "sv_adjoint",
            "sv_grad", "sv_grad_fused", "sv_sync", "sv_last_error", "sv_launch_count", "sv_version",
            "sv_profile_start", "sv_profile_stop", "sv_fusion_plan", "sv_expval_noalloc",
@@ -84,6 +84,8 @@ def load(build: bool = True):
         "sv_info": [c_vp, P(c_vp), P(ctypes.c_int), P(ctypes.c_int)],
         "sv_init": [c_vp, c_u64],
         "sv_upload": [c_vp, c_vp],
+        "sv_host_alloc": [ctypes.c_size_t, P(c_vp)],
+        "sv_host_free": [c_vp],
         "sv_download": [c_vp, c_vp],
         "sv_copy": [c_vp, c_vp],
         "sv_apply_gate": [c_vp, P(ctypes.c_int), ctypes.c_int, P(ctypes.c_int), ctypes.c_int,
@@ -243,6 +245,20 @@ def sv_info(h: int) -> Tuple[int, int, int]:
 
 def sv_init(h: int, basis_index: int = 0) -> None:
     _check(load().sv_init(c_vp(h), c_u64(basis_index)))
+
+
+def sv_host_alloc(n_elems: int, dtype=np.complex64) -> np.ndarray:
+    """A numpy array over a page-locked buffer from the library's CUDA runtime
+    (free it with sv_host_free(array))."""
+    nbytes = int(n_elems) * np.dtype(dtype).itemsize
+    p = c_vp()
+    _check(load().sv_host_alloc(ctypes.c_size_t(nbytes), ctypes.byref(p)))
+    buf = (ctypes.c_char * nbytes).from_address(p.value)
+    return np.frombuffer(buf, dtype=dtype, count=int(n_elems))
+
+
+def sv_host_free(arr: np.ndarray) -> None:
+    _check(load().sv_host_free(c_vp(arr.ctypes.data)))
 
 
 def sv_upload(h: int, host: np.ndarray) -> None:

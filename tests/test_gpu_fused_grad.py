@@ -130,3 +130,31 @@ def test_fused_grad_layered_n28_checkpointed():
     assert "kfused_adj_c64" in prof
     assert abs(e1 - e0) <= 1e-5 * n
     assert np.max(np.abs(g1 - g0)) <= 1e-4 * max(1e-3, np.max(np.abs(g0)))
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_fused_grad_small_states_use_unfused_sweep(dtype):
+    """Below 10 qubits sv_grad_fused takes the unfused reverse sweep: no
+    reverse-pass kernel runs and the result equals sv_grad's."""
+    n = 7
+    c, theta = W.random_layered(n, 6, 31)
+    terms = W.tfim(n)
+    e1, g1, s1, prof = _grad(c, theta, terms, dtype, profile=True)
+    e0, g0, s0, _ = _grad(c, theta, terms, dtype, fuse_k=0)
+    assert not any(k.startswith("kfused_adj") for k in prof), prof
+    assert abs(e1 - e0) <= TOL[dtype] * n
+    assert _rel(g1, g0) <= GRAD_TOL[dtype]
+    assert max_err(s1, s0) <= 4 * TOL[dtype]
+
+
+def test_fused_grad_rejects_bad_group_width():
+    from paper_2202_07017_gb300 import State, SvError
+    c, theta = W.hea(4, 1, 3)
+    st = State(4, "c64").init(0)
+    try:
+        with pytest.raises(SvError):
+            st.grad(c, theta, W.tfim(4), [], fuse_k=1)
+        with pytest.raises(SvError):
+            st.grad(c, theta, W.tfim(4), [], fuse_k=6)
+    finally:
+        st.close()
