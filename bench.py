@@ -313,7 +313,7 @@ def layered_adjoint(torch, n=28, depth=40):
             "fused": fused}
 
 
-def batch_solves(torch, reps=5):
+def batch_solves(torch, reps=5, tune=1):
     """4096 parameter sets of the n = 14, L = 10 hardware-efficient ansatz
     plus 1024 mixed ansatz circuits (n 8..16, depth 5..15), TFIM energies and
     adjoint gradients, complex64: one persistent launch per step, replayed
@@ -328,7 +328,7 @@ def batch_solves(torch, reps=5):
     theta = np.concatenate([W.hea_theta(14, 10, 1003 + i) for i in range(4096)]
                            + [m[1] for m in mixed])
     t0 = time.perf_counter()
-    b = Batch(circuits, hams, items, tune=True)
+    b = Batch(circuits, hams, items, tune=tune)
     t_create = time.perf_counter() - t0
     th = torch.tensor(theta, dtype=torch.float64, device="cuda")
     e = torch.empty(len(items), dtype=torch.float64, device="cuda")
@@ -431,6 +431,9 @@ def main():
     ap.add_argument("--no-fused", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-adj28", action="store_true")
+    ap.add_argument("--batch-tune", type=int, default=1, choices=[0, 1, 2, 3],
+                    help="batch kernel choice: 1 autotune (default), 0 default tile, "
+                         "2 clusters, 3 shared-memory states")
     ap.add_argument("--fused-n", type=int, default=33,
                     help="qubits of the fused layered-circuit measurement")
     ap.add_argument("--gate-table", choices=["c64", "c128"],
@@ -565,7 +568,7 @@ def main():
         meas = sampling(torch, h, n)
         adj = adjoint_ratio(torch)
         fused = None if args.no_fused else fused_layered(torch, n=args.fused_n)
-        batch = None if args.no_batch else batch_solves(torch)
+        batch = None if args.no_batch else batch_solves(torch, tune=args.batch_tune)
         adj28 = None if args.no_adj28 else layered_adjoint(torch)
         cpu = None
         if not args.no_cpu:

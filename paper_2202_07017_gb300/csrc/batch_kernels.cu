@@ -316,6 +316,11 @@ __device__ void group_bwd(float2* psi, float2* lam, int n, const BGroup& g, cons
 // to 13), the rest in its global workspace slot.
 constexpr int kBSmemQubits = 14;
 constexpr size_t kBSmemStateBytes = sizeof(float2) << kBSmemQubits;
+// Every block also caches its item's operation and group descriptors in
+// dynamic shared memory (they are read once per operation per sub-block).
+constexpr size_t kBOpsBytes = sizeof(BOp) * kBMaxGates;
+constexpr size_t kBGroupBytes = sizeof(BGroup) * kBMaxGates;
+constexpr size_t kBCacheBytes = kBOpsBytes + kBGroupBytes + sizeof(BTerm) * kBMaxTerms;
 
 template <int K, int MAXT, int MINB, bool SMS = false>
 __global__ void __launch_bounds__(MAXT, MINB) kbatch(const BatchArgs A) {
@@ -323,7 +328,11 @@ __global__ void __launch_bounds__(MAXT, MINB) kbatch(const BatchArgs A) {
   __shared__ double wpart[(MAXT / 32) * kBMaxParams];
   __shared__ double red[MAXT / 32];
   __shared__ int s_item;
-  extern __shared__ __align__(16) float2 dyn_state[];
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  BOp* sops = reinterpret_cast<BOp*>(dyn_smem);
+  BGroup* sgrp = reinterpret_cast<BGroup*>(dyn_smem + kBOpsBytes);
+  BTerm* sterm = reinterpret_cast<BTerm*>(dyn_smem + kBOpsBytes + kBGroupBytes);
+  float2* dyn_state = reinterpret_cast<float2*>(dyn_smem + kBCacheBytes);
   const int nwarps = blockDim.x >> 5;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float2* const gpsi = A.work + (size_t)blockIdx.x * (size_t(2) << A.nmax);
@@ -369,10 +378,23 @@ __global__ void __launch_bounds__(MAXT, MINB) kbatch(const BatchArgs A) {
     }
     for (int x = threadIdx.x; x < dim; x += blockDim.x) psi[x] = make_float2(x == 0 ? 1.f : 0.f, 0.f);
     for (int i = threadIdx.x; i < nwarps * kBMaxParams; i += blockDim.x) wpart[i] = 0.0;
+    {  // this item's groups and operations, operation indices rebased to the cache
+      const int ng = C.ngroups;
+      const int op_base = ng ? A.groups[C.group0].op0 : 0;
+      const int nops = ng ? A.groups[C.group0 + ng - 1].op1 - op_base : 0;
+      for (int i = threadIdx.x; i < nops; i += blockDim.x) sops[i] = A.ops[op_base + i];
+      for (int i = threadIdx.x; i < ng; i += blockDim.x) {
+        BGroup G = A.groups[C.group0 + i];
+        G.op0 -= op_base;
+        G.op1 -= op_base;
+        sgrp[i] = G;
+      }
+      for (int t = threadIdx.x; t < C.nterms; t += blockDim.x) sterm[t] = A.terms[C.term0 + t];
+    }
     __syncthreads();
     // forward
     for (int gg = 0; gg < C.ngroups; ++gg) {
-      group_fwd<K>(psi, C.n, A.groups[C.group0 + gg], A.ops, mats);
+      group_fwd<K>(psi, C.n, sgrp[gg], sops, mats);
       __syncthreads();
     }
     // lambda = H psi, E = Re <psi|lambda>
@@ -380,7 +402,7 @@ __global__ void __launch_bounds__(MAXT, MINB) kbatch(const BatchArgs A) {
     for (int x = threadIdx.x; x < dim; x += blockDim.x) {
       float orr = 0.f, oi = 0.f;
       for (int t = 0; t < C.nterms; ++t) {
-        const BTerm T = A.terms[C.term0 + t];
+        const BTerm T = sterm[t];
         const float2 b = psi[x ^ (int)T.xm];
         const float cr = (float)T.cre, ci = (float)T.cim;
         const float sr = cr * b.x - ci * b.y, si = cr * b.y + ci * b.x;
@@ -401,7 +423,7 @@ __global__ void __launch_bounds__(MAXT, MINB) kbatch(const BatchArgs A) {
     __syncthreads();
     // reverse sweep
     for (int gg = C.ngroups - 1; gg >= 0; --gg) {
-      group_bwd<K>(psi, lam, C.n, A.groups[C.group0 + gg], A.ops, mats, wpart);
+      group_bwd<K>(psi, lam, C.n, sgrp[gg], sops, mats, wpart);
       __syncthreads();
     }
     const int toff = A.theta_off[item];
@@ -942,16 +964,29 @@ sv_status launch_batch(sv_batch b, const double* theta, double* energy, double* 
     static bool attr[5] = {false, false, false, false, false};
     if (!attr[k]) {
       SV_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)kBSmemStateBytes));
+                                       (int)(kBCacheBytes + kBSmemStateBytes)));
       attr[k] = true;
     }
     ProfScope prof(st, "kbatch_smem");
-    kern<<<blocks, 512, kBSmemStateBytes, st>>>(A);
+    kern<<<blocks, 512, kBCacheBytes + kBSmemStateBytes, st>>>(A);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return check_launch("batch kernel (shared-memory states)");
   }
+  BatchKernel kern = kernel_for(k, threads, std::max(1, blocks / std::max(1, b->sms)));
+  {
+    // static (matrices, partials) + dynamic (descriptor cache) shared memory
+    // can exceed the 48 KiB default: opt in once per kernel variant
+    static std::mutex mu;
+    static std::vector<BatchKernel> done;
+    std::lock_guard<std::mutex> lk(mu);
+    if (std::find(done.begin(), done.end(), kern) == done.end()) {
+      SV_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kBCacheBytes));
+      done.push_back(kern);
+    }
+  }
   ProfScope prof(st, "kbatch");
-  kernel_for(k, threads, std::max(1, blocks / std::max(1, b->sms)))<<<blocks, threads, 0, st>>>(A);
+  kern<<<blocks, threads, kBCacheBytes, st>>>(A);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   return check_launch("batch kernel");
 }
