@@ -11,14 +11,30 @@
 // states once and writes them once.  With controls, the generator acts on
 // the control subspace only, which is exactly the set of units visited.
 //
-// Precision: the per-unit contribution is formed in the state's precision
-// and accumulated in fp64 (thread, block, then the fixed-order finish).
+// Precision: the per-unit contribution is formed in the state's precision;
+// complex64 threads accumulate it in a compensated fp32 sum, complex128
+// threads in fp64; blocks and the fixed-order finish add in fp64.
 #include <vector>
 
 #include "sv_device.cuh"
 
 namespace sv {
 namespace {
+
+// Per-thread compensated (Kahan) fp32 sum of the complex64 kernels' terms:
+// GB300 issues fp64 instructions at a small fraction of the fp32 rate, so the
+// per-unit additions stay in fp32 and the thread's s - c enters the fp64
+// block sum once.
+struct Kahan32 {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
 
 // Im( conj(l0) (P p)_0 + conj(l1) (P p)_1 ) for the pair (p0, p1) of one
 // target qubit; PAULI 1 = X, 2 = Y, 3 = Z.
@@ -38,7 +54,7 @@ template <typename I, int PAULI>
 __global__ void __launch_bounds__(kRedThreads)
     kadj_c64_pair(float4* __restrict__ psi, float4* __restrict__ lam, I n_units, Ins<I> ins,
                   I tmask, I cmask, int amp1_only, M2<float> g, double* __restrict__ partials) {
-  double acc = 0.0;
+  Kahan32 acc;
   for (I u = (I)blockIdx.x * kRedThreads + threadIdx.x; u < n_units;
        u += (I)gridDim.x * kRedThreads) {
     const I lo = insert_zeros(u, ins) | cmask, hi = lo | tmask;
@@ -46,7 +62,7 @@ __global__ void __launch_bounds__(kRedThreads)
     if (PAULI) {
       float c = im_lpp<PAULI>(l0.z, l0.w, l1.z, l1.w, p0.z, p0.w, p1.z, p1.w);
       if (!amp1_only) c += im_lpp<PAULI>(l0.x, l0.y, l1.x, l1.y, p0.x, p0.y, p1.x, p1.y);
-      acc += (double)c;
+      acc.add(c);
     }
     if (!amp1_only) {
       mv2<MK_DENSE>(g, p0.x, p0.y, p1.x, p1.y);
@@ -60,8 +76,8 @@ __global__ void __launch_bounds__(kRedThreads)
     lam[hi] = l1;
   }
   if (PAULI) {
-    acc = block_sum(acc);
-    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+    const double t = block_sum(acc.value());
+    if (threadIdx.x == 0) partials[blockIdx.x] = t;
   }
 }
 
@@ -70,20 +86,20 @@ template <typename I, int PAULI>
 __global__ void __launch_bounds__(kRedThreads)
     kadj_c64_in(float4* __restrict__ psi, float4* __restrict__ lam, I n_units, Ins<I> ins,
                 I cmask, M2<float> g, double* __restrict__ partials) {
-  double acc = 0.0;
+  Kahan32 acc;
   for (I u = (I)blockIdx.x * kRedThreads + threadIdx.x; u < n_units;
        u += (I)gridDim.x * kRedThreads) {
     const I v = insert_zeros(u, ins) | cmask;
     float4 p = psi[v], l = lam[v];
-    if (PAULI) acc += (double)im_lpp<PAULI>(l.x, l.y, l.z, l.w, p.x, p.y, p.z, p.w);
+    if (PAULI) acc.add(im_lpp<PAULI>(l.x, l.y, l.z, l.w, p.x, p.y, p.z, p.w));
     mv2<MK_DENSE>(g, p.x, p.y, p.z, p.w);
     mv2<MK_DENSE>(g, l.x, l.y, l.z, l.w);
     psi[v] = p;
     lam[v] = l;
   }
   if (PAULI) {
-    acc = block_sum(acc);
-    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+    const double t = block_sum(acc.value());
+    if (threadIdx.x == 0) partials[blockIdx.x] = t;
   }
 }
 

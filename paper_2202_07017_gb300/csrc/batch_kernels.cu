@@ -16,8 +16,10 @@
 // the block synchronises once per group instead of once per gate.
 //
 // Precision: states and gate arithmetic in fp32; gate matrices from fp64
-// sincos; the energy and every gradient accumulate in fp64 (per-warp slots
-// summed in a fixed order, so results repeat bit for bit).
+// sincos; the energy and every gradient accumulate per thread / per warp in
+// compensated fp32 sums and across warps in fp64 (fixed order, so results
+// repeat bit for bit; the single-block kernels - the cluster kernel keeps
+// fp64 slots).
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -92,6 +94,17 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 }
 
 __host__ __device__ constexpr int lowbit_b(int r) { return (r & 1) ? 0 : 1 + lowbit_b(r >> 1); }
+
+// Compensated (Kahan) fp32 sum: GB300 issues fp64 instructions at a small
+// fraction of the fp32 rate, so per-operation and per-amplitude additions
+// stay in fp32 and only s - c enters the fp64 totals.
+__device__ __forceinline__ void ksum_add(float2& a, float x) {  // a = (s, c)
+  const float y = x - a.y;
+  const float t = a.x + y;
+  a.y = (t - a.x) - y;
+  a.x = t;
+}
+__device__ __forceinline__ double ksum_value(float2 a) { return (double)a.x - (double)a.y; }
 
 // Arithmetic classes of a gate's 2x2 matrix: the work per pair drops from 16
 // multiply-adds (dense) to 8 (real: H, X, RY; imaginary off-diagonal: Y, RX;
@@ -255,7 +268,7 @@ __device__ void group_fwd(float2* psi, int n, const BGroup& g, const BOp* ops, c
 // backward: for ops in reverse, gradient contribution then un-apply on both
 template <int K>
 __device__ void group_bwd(float2* psi, float2* lam, int n, const BGroup& g, const BOp* ops,
-                          const float* mats, double* wpart) {
+                          const float* mats, float2* wpart) {
   int off[1 << K], lm[K];
   group_offsets<K>(g, off, lm);
   const int kk = g.k;
@@ -290,7 +303,7 @@ __device__ void group_bwd(float2* psi, float2* lam, int n, const BGroup& g, cons
         SV_BIT_SWITCH(op.b0, SV_GRAD)
 #undef SV_GRAD
         c = warp_sum_f(c);
-        if (lane == 0) wpart[warp * kBMaxParams + op.param] += (double)c;
+        if (lane == 0) ksum_add(wpart[warp * kBMaxParams + op.param], c);
       }
 #define SV_BWD(BB)                                  \
   if constexpr (BB < K) {                           \
@@ -325,7 +338,7 @@ constexpr size_t kBCacheBytes = kBOpsBytes + kBGroupBytes + sizeof(BTerm) * kBMa
 template <int K, int MAXT, int MINB, bool SMS = false>
 __global__ void __launch_bounds__(MAXT, MINB) kbatch(const BatchArgs A) {
   __shared__ float mats[8 * kBMaxGates];
-  __shared__ double wpart[(MAXT / 32) * kBMaxParams];
+  __shared__ float2 wpart[(MAXT / 32) * kBMaxParams];  // per warp and parameter: (sum, comp)
   __shared__ double red[MAXT / 32];
   __shared__ int s_item;
   extern __shared__ __align__(16) unsigned char dyn_smem[];
@@ -377,7 +390,8 @@ __global__ void __launch_bounds__(MAXT, MINB) kbatch(const BatchArgs A) {
       for (int e = 0; e < 8; ++e) mats[8 * gi + e] = (float)m[e];
     }
     for (int x = threadIdx.x; x < dim; x += blockDim.x) psi[x] = make_float2(x == 0 ? 1.f : 0.f, 0.f);
-    for (int i = threadIdx.x; i < nwarps * kBMaxParams; i += blockDim.x) wpart[i] = 0.0;
+    for (int i = threadIdx.x; i < nwarps * kBMaxParams; i += blockDim.x)
+      wpart[i] = make_float2(0.f, 0.f);
     {  // this item's groups and operations, operation indices rebased to the cache
       const int ng = C.ngroups;
       const int op_base = ng ? A.groups[C.group0].op0 : 0;
@@ -398,7 +412,7 @@ __global__ void __launch_bounds__(MAXT, MINB) kbatch(const BatchArgs A) {
       __syncthreads();
     }
     // lambda = H psi, E = Re <psi|lambda>
-    double e = 0.0;
+    float2 ek = make_float2(0.f, 0.f);
     for (int x = threadIdx.x; x < dim; x += blockDim.x) {
       float orr = 0.f, oi = 0.f;
       for (int t = 0; t < C.nterms; ++t) {
@@ -416,9 +430,9 @@ __global__ void __launch_bounds__(MAXT, MINB) kbatch(const BatchArgs A) {
       }
       lam[x] = make_float2(orr, oi);
       const float2 a = psi[x];
-      e += (double)(a.x * orr + a.y * oi);
+      ksum_add(ek, a.x * orr + a.y * oi);
     }
-    e = warp_sum_d(e);
+    double e = warp_sum_d(ksum_value(ek));
     if (lane == 0) red[warp] = e;
     __syncthreads();
     // reverse sweep
@@ -429,7 +443,7 @@ __global__ void __launch_bounds__(MAXT, MINB) kbatch(const BatchArgs A) {
     const int toff = A.theta_off[item];
     for (int p = threadIdx.x; p < C.nparams; p += blockDim.x) {
       double g = 0.0;
-      for (int w = 0; w < nwarps; ++w) g += wpart[w * kBMaxParams + p];
+      for (int w = 0; w < nwarps; ++w) g += ksum_value(wpart[w * kBMaxParams + p]);
       A.grad[toff + p] = g;
     }
     if (threadIdx.x == 0) {

@@ -599,14 +599,31 @@ __device__ __forceinline__ R grad_pairs(int pauli, int cm, const R* gm, const R 
   return acc;
 }
 
+// Per-warp gradient accumulator: a compensated (Kahan) sum in the state's
+// precision - GB300 issues fp64 instructions at a small fraction of the fp32
+// rate, so the per-sub-block additions avoid fp64; the block converts s - c
+// to fp64 once at the end.
+template <typename R>
+struct KahanAcc {
+  R s, c;
+};
+
+template <typename R>
+__device__ __forceinline__ void kahan_add(KahanAcc<R>& a, R x) {
+  const R y = x - a.c;
+  const R t = a.s + y;
+  a.c = (t - a.s) - y;
+  a.s = t;
+}
+
 // One register group over both slices: gradient operations accumulate into
-// this warp's fp64 slots gw[0..ngrad), every other operation is applied to
-// psi and lambda.  All lanes of a warp run the same iterations (warp sums).
+// this warp's slots gw[0..ngrad), every other operation is applied to psi
+// and lambda.  All lanes of a warp run the same iterations (warp sums).
 template <int KG, typename R>
 __device__ __forceinline__ void run_group_adj(typename Cplx2<R>::T* smp,
                                               typename Cplx2<R>::T* sml, int m,
                                               const uint8_t* gb, const FOpDev<R>* ops, int o0,
-                                              int o1, double* gw) {
+                                              int o1, KahanAcc<R>* gw) {
   typedef typename Cplx2<R>::T V2;
   constexpr int D = 1 << KG;
   int soff[D];
@@ -650,7 +667,7 @@ __device__ __forceinline__ void run_group_adj(typename Cplx2<R>::T* smp,
         }
 #pragma unroll
         for (int d = 16; d; d >>= 1) c += __shfl_xor_sync(0xffffffffu, c, d);
-        if (lane == 0) gw[op.pad[0] | (op.pad[1] << 8)] += (double)c;
+        if (lane == 0) kahan_add(gw[op.pad[0] | (op.pad[1] << 8)], c);
       } else {
         apply_op<KG, R>(op, pr, pi);
         apply_op<KG, R>(op, lr, li);
@@ -687,8 +704,8 @@ __device__ __forceinline__ void store_pair(uint32_t s1, uint32_t s2, const CUten
 
 // Reverse-sweep pass: as kfused_tma, staging the psi slice (tmap) and the
 // lambda slice (tmap2) on one mbarrier.  Gradient sums: per warp and
-// gradient operation in shared memory, then per block (warps in order) into
-// partials[gslot[j] * pstride + blockIdx.x].
+// gradient operation a compensated sum in shared memory, then per block
+// (warps in order, fp64) into partials[gslot[j] * pstride + blockIdx.x].
 template <typename R, int KGF, int MINB>
 __global__ void __launch_bounds__(kFThreads, MINB)
     kfused_adj(uint64_t n_blocks, const __grid_constant__ FusedParams<R> P,
@@ -701,10 +718,10 @@ __global__ void __launch_bounds__(kFThreads, MINB)
   const uint32_t sbuf2 = sbuf + P.slice_bytes;  // slice bytes are a multiple of 1024
   V2* smp = reinterpret_cast<V2*>(smem_raw + (sbuf - raw));
   V2* sml = reinterpret_cast<V2*>(smem_raw + (sbuf2 - raw));
-  double* gacc = reinterpret_cast<double*>(smem_raw + (sbuf2 - raw) + P.slice_bytes);
+  KahanAcc<R>* gacc = reinterpret_cast<KahanAcc<R>*>(smem_raw + (sbuf2 - raw) + P.slice_bytes);
   constexpr int nw = kFThreads / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i = threadIdx.x; i < nw * P.ngrad; i += kFThreads) gacc[i] = 0.0;
+  for (int i = threadIdx.x; i < nw * P.ngrad; i += kFThreads) gacc[i] = KahanAcc<R>{0, 0};
   const uint32_t barp = smem_addr(&bar);
   if (threadIdx.x == 0) {
     mbar_init(barp, 1);
@@ -763,7 +780,10 @@ __global__ void __launch_bounds__(kFThreads, MINB)
   __syncthreads();
   for (int j = threadIdx.x; j < P.ngrad; j += kFThreads) {
     double t = 0.0;
-    for (int w = 0; w < nw; ++w) t += gacc[w * P.ngrad + j];
+    for (int w = 0; w < nw; ++w) {
+      const KahanAcc<R> a = gacc[w * P.ngrad + j];
+      t += (double)a.s - (double)a.c;
+    }
     partials[(size_t)P.gslot[j] * pstride + blockIdx.x] = t;
   }
 }
@@ -1306,7 +1326,7 @@ sv_status run_adj_pass(void* psi, void* lam, int n, cudaStream_t st, const Fused
     return SV_ERR_INVALID;
   }
   const size_t smem =
-      1024 + 2 * (size_t)P.slice_bytes + sizeof(double) * (kFThreads / 32) * P.ngrad;
+      1024 + 2 * (size_t)P.slice_bytes + sizeof(KahanAcc<R>) * (kFThreads / 32) * P.ngrad;
   static std::map<std::pair<const void*, size_t>, int> resident;
   int& res = resident[{reinterpret_cast<const void*>(kern), smem}];
   if (!res) {
