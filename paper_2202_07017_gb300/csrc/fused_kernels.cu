@@ -1317,7 +1317,7 @@ sv_status run_adj_pass(void* psi, void* lam, int n, cudaStream_t st, const Fused
     return SV_ERR_UNSUPPORTED;
   }
   typedef void (*Kern)(uint64_t, const FusedParams<R>, double*, int);
-  constexpr int MB = sizeof(R) == 4 ? 2 : 1;
+  constexpr int MB = sizeof(R) == 4 ? 3 : 1;
   const Kern kern = kg <= 1   ? kfused_adj<R, 1, MB>
                     : kg == 2 ? kfused_adj<R, 2, MB>
                               : kfused_adj<R, 3, MB>;
