@@ -387,8 +387,19 @@ sv_status sv_batch_free(sv_batch b);
 
 /* ---- status ------------------------------------------------------------ */
 
-/* Synchronise the stream and surface any asynchronous error. */
+/* Synchronise the stream and surface any asynchronous error; SV_ERR_TIMEOUT
+ * if a bulk-copy pass gave up waiting for its copies (each such wait is
+ * bounded by 1 s of GPU time, after which the pass's blocks record the
+ * timeout and return without storing; the status is cleared when read). */
 sv_status sv_sync(sv_state s);
+
+/* Self-test of that bounded wait: queues one bulk-copy pass over the state
+ * that applies no gate and whose barrier expects more bytes than it copies,
+ * so its waits run out (about 1 s); the following sv_sync returns
+ * SV_ERR_TIMEOUT and the state is unchanged.  No GPU fault is involved and
+ * the context stays usable.  States of at least 10 qubits; SV_ERR_INVALID
+ * otherwise.  Asynchronous.  (A test aid: the paper has no counterpart.) */
+sv_status sv_selftest_wait(sv_state s);
 
 /* Message describing the calling thread's last failure ("" if none). */
 const char* sv_last_error(void);

@@ -20,7 +20,8 @@ from .sv import (C64, C128, EXPORTS, PackedBatch, sv_batch_create, sv_batch_free
                  sv_fusion_plan, sv_pauli_rotation, sv_probabilities, sv_sample, sv_trotter,
                  sv_grad, sv_grad_fused, sv_info, sv_init, sv_last_error, sv_launch_count, sv_norm, sv_profile_start,
                  sv_profile_stop, sv_set_stream,
-                 sv_sync, sv_upload, sv_version, sv_wrap, sv_host_alloc, sv_host_free)
+                 sv_sync, sv_upload, sv_version, sv_wrap, sv_host_alloc, sv_host_free,
+                 sv_selftest_wait)
 
 __all__ = ["State", "Batch", "Energy", "energy", "C64", "C128", "SvError", "pack_circuit", "pack_pauli",
            "load"] + list(EXPORTS)

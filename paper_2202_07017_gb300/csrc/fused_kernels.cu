@@ -71,6 +71,7 @@ struct FusedParams {
   int rank, nsw, ncopies;
   uint8_t tlo[5], thi[5], swpos[12];
   uint32_t box_bytes, slice_bytes;
+  uint32_t extra_tx;  // 0; the bounded-wait self-test arms the barrier for more bytes
   int ngroups;
   int ngrad;            // reverse sweeps: gradient operations of the pass
   int gslot[kFMaxOps];  // their gradient slots
@@ -525,7 +526,7 @@ __global__ void __launch_bounds__(kFThreads, MINB)
     if (threadIdx.x < 32) {
       bulk_wait_read_all();
       __syncwarp();
-      if (lane == 0) mbar_arrive_expect_tx(barp, P.slice_bytes);
+      if (lane == 0) mbar_arrive_expect_tx(barp, P.slice_bytes + P.extra_tx);
       __syncwarp();
       for (int k = lane; k < P.ncopies; k += 32) {
         int c[5];
@@ -1104,6 +1105,7 @@ void build_layers(const FusedPass& pass, const int* pos_of, FusedParams<R>* P) {
 template <typename R>
 bool build_params(const FusedPass& pass, const std::vector<int>& order, FusedParams<R>* P) {
   P->ngrad = 0;
+  P->extra_tx = 0;
   const std::vector<int>& S = pass.S;
   P->m = (int)S.size();
   P->L = pass.L;
@@ -1366,6 +1368,39 @@ sv_status launch_fused_reverse_pass(void* psi, void* lam, sv_dtype dt, int n, cu
 sv_status launch_fused_pass(void* data, sv_dtype dt, int n, cudaStream_t st,
                             const FusedPass& pass) {
   return dt == SV_C64 ? run_pass<float>(data, n, st, pass) : run_pass<double>(data, n, st, pass);
+}
+
+// Bounded-wait self-test: one pass over the state with no gates whose
+// mbarrier expects 16 bytes more than its slice, so no phase completes; every
+// block gives up after the wait limit, records the timeout and exits before
+// storing anything.  The state is unchanged.
+template <typename R>
+sv_status selftest_wait(void* data, int n, cudaStream_t st) {
+  static FusedParams<R> P;
+  FusedPass pass;
+  const int m = std::min(n, 10);
+  for (int b = 0; b < m; ++b) pass.S.push_back(b);
+  pass.L = m;
+  const int lw = sizeof(R) == 4 ? 0 : 1;
+  TmaGeom geo;
+  if (n < 10 || !tma_geometry(pass.S, pass.L, n, lw, &geo) || !build_params(pass, geo.order, &P) ||
+      !build_tma(geo, data, &P)) {
+    set_error("bounded-wait self-test: needs a state of at least 10 qubits");
+    return SV_ERR_INVALID;
+  }
+  P.extra_tx = 16;
+  typedef void (*Kern)(uint64_t, const FusedParams<R>);
+  const Kern kern = kfused_tma<R, 1, sizeof(R) == 4 ? 3 : 2, 0>;
+  const size_t smem = ((sizeof(R) * 2) << P.m) + 1024;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  const uint64_t nblk = uint64_t(1) << (n - P.m);
+  kern<<<(unsigned)std::min<uint64_t>(nblk, 152), kFThreads, smem, st>>>(nblk, P);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return check_launch("bounded-wait self-test kernel");
+}
+
+sv_status launch_wait_selftest(void* data, sv_dtype dt, int n, cudaStream_t st) {
+  return dt == SV_C64 ? selftest_wait<float>(data, n, st) : selftest_wait<double>(data, n, st);
 }
 
 unsigned take_fused_status() {

@@ -850,6 +850,11 @@ sv_status sv_grad_fused(sv_state s, const sv_circuit* c, const double* theta,
   return SV_OK;
 }
 
+sv_status sv_selftest_wait(sv_state s) {
+  if (!valid_state(s)) return SV_ERR_INVALID;
+  return launch_wait_selftest(s->data, s->dt, s->n, s->stream);
+}
+
 sv_status sv_sync(sv_state s) {
   if (!valid_state(s)) return SV_ERR_INVALID;
   SV_CUDA_TRY(cudaStreamSynchronize(s->stream));

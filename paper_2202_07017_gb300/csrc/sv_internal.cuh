@@ -192,6 +192,9 @@ sv_status launch_fused_pass(void* data, sv_dtype dt, int n, cudaStream_t st,
 bool fused_reverse_ok(sv_dtype dt, int n, const FusedPass& pass);
 sv_status launch_fused_reverse_pass(void* psi, void* lam, sv_dtype dt, int n, cudaStream_t st,
                                     const FusedPass& pass, double* partials, int pstride);
+// One bulk-copy pass armed for more bytes than it copies (its bounded waits
+// give up; the state is unchanged); see sv_selftest_wait.
+sv_status launch_wait_selftest(void* data, sv_dtype dt, int n, cudaStream_t st);
 // Reads and clears the fused-pass device status word of the current device
 // (kWaitTimeout = 1: a bounded wait inside a pass gave up).
 unsigned take_fused_status();
