@@ -393,6 +393,14 @@ sv_status sv_batch_free(sv_batch b);
  * timeout and return without storing; the status is cleared when read). */
 sv_status sv_sync(sv_state s);
 
+/* States from sv_alloc, and the work states of the adjoint sweeps, are
+ * allocated between two 4 KiB guard regions filled with a fixed byte.
+ * sv_check_guards synchronises the stream and checks every guard of the
+ * handle: SV_ERR_CUDA (with the region and offset in sv_last_error) if a
+ * kernel wrote outside its state; SV_OK otherwise (a state from sv_wrap has
+ * no guards of its own).  A substitute for a memory checker in tests. */
+sv_status sv_check_guards(sv_state s);
+
 /* Self-test of that bounded wait: queues one bulk-copy pass over the state
  * that applies no gate and whose barrier expects more bytes than it copies,
  * so its waits run out (about 1 s); the following sv_sync returns

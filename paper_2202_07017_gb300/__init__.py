@@ -21,7 +21,7 @@ from .sv import (C64, C128, EXPORTS, PackedBatch, sv_batch_create, sv_batch_free
                  sv_grad, sv_grad_fused, sv_info, sv_init, sv_last_error, sv_launch_count, sv_norm, sv_profile_start,
                  sv_profile_stop, sv_set_stream,
                  sv_sync, sv_upload, sv_version, sv_wrap, sv_host_alloc, sv_host_free,
-                 sv_selftest_wait)
+                 sv_selftest_wait, sv_check_guards)
 
 __all__ = ["State", "Batch", "Energy", "energy", "C64", "C128", "SvError", "pack_circuit", "pack_pauli",
            "load"] + list(EXPORTS)
@@ -37,12 +37,19 @@ def _dtype_code(dtype) -> int:
 
 class State:
     """A 2^n-amplitude state in a torch CUDA tensor, wrapped by an sv handle
-    bound to a torch stream (the current stream by default)."""
+    bound to a torch stream (the current stream by default).  guarded=True
+    lets the library allocate the state instead (no torch tensor), between
+    guard regions that check_guards() verifies."""
 
-    def __init__(self, n_qubits: int, dtype="c64", device="cuda", stream=None):
+    def __init__(self, n_qubits: int, dtype="c64", device="cuda", stream=None, guarded=False):
         import torch
         self.n = int(n_qubits)
         self.code = _dtype_code(dtype)
+        if guarded:
+            self.tensor = None
+            self.stream = stream if stream is not None else torch.cuda.current_stream()
+            self.h = sv_alloc(self.n, self.code, self.stream.cuda_stream)
+            return
         tdt = torch.complex64 if self.code == C64 else torch.complex128
         self.tensor = torch.empty(1 << self.n, dtype=tdt, device=device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.tensor.device)
@@ -120,6 +127,10 @@ class State:
 
     def sync(self):
         sv_sync(self.h)
+
+    def check_guards(self):
+        """Raise SvError if a kernel wrote outside the state or its work states."""
+        sv_check_guards(self.h)
 
 
 class Batch:

@@ -115,10 +115,31 @@ sv_status ensure_partials(sv_state s, size_t doubles) {
   return SV_OK;
 }
 
+sv_status alloc_guarded(size_t bytes, void** base, void** data) {
+  *base = *data = nullptr;
+  cudaError_t e = cudaMalloc(base, bytes + 2 * kGuardBytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *base = nullptr;
+    set_error("allocation of %zu bytes: %s", bytes, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? SV_ERR_OOM : SV_ERR_CUDA;
+  }
+  char* b = static_cast<char*>(*base);
+  e = cudaMemset(b, kGuardByte, kGuardBytes);
+  if (e == cudaSuccess) e = cudaMemset(b + kGuardBytes + bytes, kGuardByte, kGuardBytes);
+  if (e != cudaSuccess) {
+    cudaFree(*base);
+    *base = nullptr;
+    set_error("guard fill: %s", cudaGetErrorString(e));
+    return SV_ERR_CUDA;
+  }
+  *data = b + kGuardBytes;
+  return SV_OK;
+}
+
 sv_status ensure_work(sv_state s, int which) {
   if (s->work[which]) return SV_OK;
-  SV_CUDA_TRY(cudaMalloc(&s->work[which], s->bytes()));
-  return SV_OK;
+  return alloc_guarded(s->bytes(), &s->work_base[which], &s->work[which]);
 }
 
 }  // namespace sv
@@ -275,14 +296,16 @@ sv_status sv_alloc(int n_qubits, sv_dtype dtype, void* cuda_stream, sv_state* ou
     return SV_ERR_INVALID;
   }
   const size_t bytes = (size_t(1) << n_qubits) * (dtype == SV_C64 ? 8 : 16);
-  void* p = nullptr;
-  cudaError_t e = cudaMalloc(&p, bytes);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    set_error("sv_alloc: %zu bytes: %s", bytes, cudaGetErrorString(e));
-    return e == cudaErrorMemoryAllocation ? SV_ERR_OOM : SV_ERR_CUDA;
+  void *base = nullptr, *p = nullptr;
+  sv_status st = alloc_guarded(bytes, &base, &p);
+  if (st) return st;
+  st = make_handle(p, true, n_qubits, dtype, cuda_stream, out);
+  if (st) {
+    cudaFree(base);
+    return st;
   }
-  return make_handle(p, true, n_qubits, dtype, cuda_stream, out);
+  (*out)->base = base;
+  return SV_OK;
 }
 
 sv_status sv_wrap(void* dev_ptr, int n_qubits, sv_dtype dtype, void* cuda_stream,
@@ -298,11 +321,11 @@ sv_status sv_wrap(void* dev_ptr, int n_qubits, sv_dtype dtype, void* cuda_stream
 sv_status sv_free(sv_state s) {
   if (!s) return SV_OK;
   cudaStreamSynchronize(s->stream);
-  if (s->owned && s->data) cudaFree(s->data);
+  if (s->owned && s->base) cudaFree(s->base);
   if (s->partials) cudaFree(s->partials);
   if (s->dres) cudaFree(s->dres);
   if (s->hres) cudaFreeHost(s->hres);
-  for (void* w : s->work)
+  for (void* w : s->work_base)
     if (w) cudaFree(w);
   for (void* c : s->ckpt)
     if (c) cudaFree(c);
@@ -847,6 +870,34 @@ sv_status sv_grad_fused(sv_state s, const sv_circuit* c, const double* theta,
   for (int p = 0; p < c->n_params; ++p) grad[p] = 0.0;
   for (int i = 0; i < c->n_gates; ++i)
     if (slot_of[i] >= 0) grad[c->gates[i].param] += gs[slot_of[i]];
+  return SV_OK;
+}
+
+sv_status sv_check_guards(sv_state s) {
+  if (!valid_state(s)) return SV_ERR_INVALID;
+  SV_CUDA_TRY(cudaStreamSynchronize(s->stream));
+  std::vector<unsigned char> h(kGuardBytes);
+  struct Region {
+    const void* base;
+    const char* what;
+  };
+  const Region regions[] = {{s->owned ? s->base : nullptr, "state"},
+                            {s->work_base[0], "adjoint work state psi"},
+                            {s->work_base[1], "adjoint work state lambda"}};
+  for (const Region& r : regions) {
+    if (!r.base) continue;
+    const char* b = static_cast<const char*>(r.base);
+    const size_t offs[2] = {0, kGuardBytes + s->bytes()};
+    for (size_t o : offs) {
+      SV_CUDA_TRY(cudaMemcpy(h.data(), b + o, kGuardBytes, cudaMemcpyDeviceToHost));
+      for (size_t i = 0; i < kGuardBytes; ++i)
+        if (h[i] != kGuardByte) {
+          set_error("sv_check_guards: the %s guard %s the data was overwritten at byte %zu",
+                    r.what, o ? "after" : "before", i);
+          return SV_ERR_CUDA;
+        }
+    }
+  }
   return SV_OK;
 }
 

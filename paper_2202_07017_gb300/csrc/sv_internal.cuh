@@ -67,6 +67,7 @@ int red_blocks(uint64_t units);
 // ---- the state handle --------------------------------------------------------
 struct sv_state_s {
   void* data = nullptr;
+  void* base = nullptr;  // allocation of an owned state: guard, data, guard
   int n = 0;
   sv_dtype dt = SV_C64;
   cudaStream_t stream = nullptr;
@@ -79,11 +80,19 @@ struct sv_state_s {
   double* hres = nullptr;   // pinned host mirror of dres
   // adjoint work states and forward checkpoints
   void* work[2] = {nullptr, nullptr};
+  void* work_base[2] = {nullptr, nullptr};  // their allocations (guarded like data)
   std::vector<void*> ckpt;
   size_t bytes() const { return (size_t(1) << n) * (dt == SV_C64 ? 8 : 16); }
 };
 
 namespace sv {
+
+// Library-owned states (and the adjoint's work states) sit between two
+// kGuardBytes regions filled with kGuardByte; sv_check_guards verifies them.
+constexpr size_t kGuardBytes = 4096;
+constexpr unsigned char kGuardByte = 0xA5;
+// Allocates guard | bytes | guard, fills the guards; *data = base + guard.
+sv_status alloc_guarded(size_t bytes, void** base, void** data);
 
 sv_status ensure_partials(sv_state s, size_t doubles);
 sv_status ensure_work(sv_state s, int which);

@@ -52,7 +52,7 @@ class SvError(RuntimeError):
 EXPORTS = ("sv_alloc", "sv_wrap", "sv_free", "sv_set_stream", "sv_info", "sv_init",
            "sv_upload", "sv_download", "sv_host_alloc", "sv_host_free", "sv_copy", "sv_apply_gate", "sv_apply_circuit",
            "sv_norm", "sv_expval", "sv_expval_async", "sv_apply_pauli_sum", "sv_adjoint",
-           "sv_grad", "sv_grad_fused", "sv_sync", "sv_selftest_wait", "sv_last_error", "sv_launch_count", "sv_version",
+           "sv_grad", "sv_grad_fused", "sv_sync", "sv_selftest_wait", "sv_check_guards", "sv_last_error", "sv_launch_count", "sv_version",
            "sv_profile_start", "sv_profile_stop", "sv_fusion_plan", "sv_expval_noalloc",
            "sv_probabilities", "sv_sample", "sv_pauli_rotation", "sv_trotter",
            "sv_batch_create", "sv_batch_plan", "sv_batch_info", "sv_batch_kernel", "sv_batch_run", "sv_batch_run_graph", "sv_batch_grad",
@@ -102,6 +102,7 @@ def load(build: bool = True):
                           ctypes.c_int, P(c_dbl), P(c_dbl)],
         "sv_sync": [c_vp],
         "sv_selftest_wait": [c_vp],
+        "sv_check_guards": [c_vp],
         "sv_profile_start": [],
         "sv_pauli_rotation": [c_vp, c_u64, c_u64, c_dbl],
         "sv_trotter": [c_vp, P(SvPauliSum), c_dbl, ctypes.c_int, ctypes.c_int],
@@ -419,6 +420,11 @@ def sv_sync(h: int) -> None:
 
 def sv_selftest_wait(h: int) -> None:
     _check(load().sv_selftest_wait(c_vp(h)))
+
+
+def sv_check_guards(h: int) -> None:
+    """Raise SvError if a kernel wrote into a guard region around the state."""
+    _check(load().sv_check_guards(c_vp(h)))
 
 
 def sv_last_error() -> str:

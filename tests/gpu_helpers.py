@@ -17,13 +17,14 @@ def oracle_threads():
 def gpu_run(circuit, theta, psi0, dtype, fuse_k=0, basis=None):
     """Run `circuit` on the GPU from psi0 (or |basis>) and return the state."""
     from paper_2202_07017_gb300 import State
-    st = State(circuit.n_qubits, dtype)
+    st = State(circuit.n_qubits, dtype, guarded=True)
     try:
         if psi0 is None:
             st.init(basis or 0)
         else:
             st.load(np.asarray(psi0, NP_DTYPE[dtype]))
         st.apply_circuit(circuit, theta, fuse_k)
+        st.check_guards()  # nothing written outside the state
         return st.numpy()
     finally:
         st.close()

@@ -2,7 +2,8 @@
 cannot hold returns SV_ERR_OOM and leaves the library usable; a bulk-copy
 pass whose barrier can never complete gives up after its bounded wait, the
 host reads SV_ERR_TIMEOUT from sv_sync, the state is unchanged and the
-context keeps working."""
+context keeps working; the guard regions around a state report a write
+outside it."""
 import numpy as np
 import pytest
 
@@ -66,5 +67,28 @@ def test_bounded_wait_selftest_rejects_small_states():
     try:
         with pytest.raises(SvError):
             sv_selftest_wait(st.h)
+    finally:
+        st.close()
+
+
+def test_guard_regions_report_a_write_outside_the_state():
+    """The 4 KiB guards around an sv_alloc state: clean after a circuit, and a
+    host-issued write of 16 bytes just below the state (inside the guard,
+    within the allocation) is reported by sv_check_guards."""
+    import ctypes
+    from paper_2202_07017_gb300 import SvError, State, sv_info
+    n = 12
+    c, theta = W.random_layered(n, 4, 3)
+    st = State(n, "c64", guarded=True).init(0)
+    try:
+        st.apply_circuit(c, theta, 4)
+        st.check_guards()
+        ptr = sv_info(st.h)[0]
+        rt = ctypes.CDLL("libcudart.so.13")
+        torch.cuda.synchronize()
+        assert rt.cudaMemset(ctypes.c_void_p(ptr - 16), 0, ctypes.c_size_t(16)) == 0
+        torch.cuda.synchronize()
+        with pytest.raises(SvError):
+            st.check_guards()
     finally:
         st.close()

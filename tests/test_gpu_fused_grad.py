@@ -28,7 +28,7 @@ def _rel(g, ref):
 
 def _grad(c, theta, terms, dtype, psi0=None, checkpoints=(), fuse_k=4, profile=False):
     from paper_2202_07017_gb300 import State, sv_profile_start, sv_profile_stop
-    st = State(c.n_qubits, dtype)
+    st = State(c.n_qubits, dtype, guarded=True)
     try:
         if psi0 is None:
             st.init(0)
@@ -38,6 +38,7 @@ def _grad(c, theta, terms, dtype, psi0=None, checkpoints=(), fuse_k=4, profile=F
             sv_profile_start()
         e, g = st.grad(c, theta, terms, list(checkpoints), fuse_k=fuse_k)
         prof = sv_profile_stop() if profile else {}
+        st.check_guards()  # state and both work states
         return e, g, st.numpy(), prof
     finally:
         st.close()
