@@ -333,7 +333,8 @@ constexpr size_t kBSmemStateBytes = sizeof(float2) << kBSmemQubits;
 // dynamic shared memory (they are read once per operation per sub-block).
 constexpr size_t kBOpsBytes = sizeof(BOp) * kBMaxGates;
 constexpr size_t kBGroupBytes = sizeof(BGroup) * kBMaxGates;
-constexpr size_t kBCacheBytes = kBOpsBytes + kBGroupBytes + sizeof(BTerm) * kBMaxTerms;
+constexpr size_t kBTermBytes = sizeof(BTerm) * kBMaxTerms;
+constexpr size_t kBCacheBytes = kBOpsBytes + kBGroupBytes + kBTermBytes + sizeof(float2) * kBMaxTerms;
 
 template <int K, int MAXT, int MINB, bool SMS = false>
 __global__ void __launch_bounds__(MAXT, MINB) kbatch(const BatchArgs A) {
@@ -345,6 +346,9 @@ __global__ void __launch_bounds__(MAXT, MINB) kbatch(const BatchArgs A) {
   BOp* sops = reinterpret_cast<BOp*>(dyn_smem);
   BGroup* sgrp = reinterpret_cast<BGroup*>(dyn_smem + kBOpsBytes);
   BTerm* sterm = reinterpret_cast<BTerm*>(dyn_smem + kBOpsBytes + kBGroupBytes);
+  // the terms' coefficients rounded to fp32 once per item (a conversion from
+  // fp64 per term and amplitude would occupy GB300's slow fp64 pipe)
+  float2* scoef = reinterpret_cast<float2*>(dyn_smem + kBOpsBytes + kBGroupBytes + kBTermBytes);
   float2* dyn_state = reinterpret_cast<float2*>(dyn_smem + kBCacheBytes);
   const int nwarps = blockDim.x >> 5;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -403,7 +407,11 @@ __global__ void __launch_bounds__(MAXT, MINB) kbatch(const BatchArgs A) {
         G.op1 -= op_base;
         sgrp[i] = G;
       }
-      for (int t = threadIdx.x; t < C.nterms; t += blockDim.x) sterm[t] = A.terms[C.term0 + t];
+      for (int t = threadIdx.x; t < C.nterms; t += blockDim.x) {
+        const BTerm T = A.terms[C.term0 + t];
+        sterm[t] = T;
+        scoef[t] = make_float2((float)T.cre, (float)T.cim);
+      }
     }
     __syncthreads();
     // forward
@@ -418,7 +426,7 @@ __global__ void __launch_bounds__(MAXT, MINB) kbatch(const BatchArgs A) {
       for (int t = 0; t < C.nterms; ++t) {
         const BTerm T = sterm[t];
         const float2 b = psi[x ^ (int)T.xm];
-        const float cr = (float)T.cre, ci = (float)T.cim;
+        const float cr = scoef[t].x, ci = scoef[t].y;
         const float sr = cr * b.x - ci * b.y, si = cr * b.y + ci * b.x;
         if (__popcll(((uint64_t)x ^ T.xm) & T.zm) & 1) {
           orr -= sr;
