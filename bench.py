@@ -281,8 +281,9 @@ def fused_layered(torch, n=33, depth=40, k=4):
 
 def layered_adjoint(torch, n=28, depth=40):
     """Adjoint gradient of <sum Z_i> for the random layered circuit at n = 28
-    (complex64, 3900 gates, 3360 parameters) with forward checkpoints every 10
-    layers: forward (circuit + energy) and forward + gradient times."""
+    (complex64, 3900 gates, 3360 parameters; --adj-n changes n) with forward
+    checkpoints every 10 layers: forward (circuit + energy) and forward +
+    gradient times, unfused and fused."""
     import workloads as W
     from paper_2202_07017_gb300 import (C64, pack_circuit, pack_pauli, sv_alloc, sv_apply_circuit,
                                         sv_expval, sv_free, sv_grad, sv_init)
@@ -431,6 +432,8 @@ def main():
     ap.add_argument("--no-fused", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-adj28", action="store_true")
+    ap.add_argument("--adj-n", type=int, default=28,
+                    help="qubits of the layered-circuit adjoint measurement")
     ap.add_argument("--batch-tune", type=int, default=1, choices=[0, 1, 2, 3],
                     help="batch kernel choice: 1 autotune (default), 0 default tile, "
                          "2 clusters, 3 shared-memory states")
@@ -569,7 +572,7 @@ def main():
         adj = adjoint_ratio(torch)
         fused = None if args.no_fused else fused_layered(torch, n=args.fused_n)
         batch = None if args.no_batch else batch_solves(torch, tune=args.batch_tune)
-        adj28 = None if args.no_adj28 else layered_adjoint(torch)
+        adj28 = None if args.no_adj28 else layered_adjoint(torch, n=args.adj_n)
         cpu = None
         if not args.no_cpu:
             threads = os.cpu_count() or 1
