@@ -600,6 +600,53 @@ __device__ __forceinline__ R grad_pairs(int pauli, int cm, const R* gm, const R 
   return acc;
 }
 
+// The four real sums that every generator [[a, b], [conj b, d]] on group
+// bit B needs: with z_rs = conj(l_r) p_s over the pairs inside cm,
+// Im<lambda|M|psi> = a Im z00 + d Im z11 + re b Im(z01 + z10) + im b Re(z01 - z10).
+// Several gradients on one bit then cost these 12 FMAs per pair once.
+template <int KG, int B, typename R>
+__device__ __forceinline__ void grad_quad(int cm, const R (&pr)[1 << KG], const R (&pi)[1 << KG],
+                                          const R (&lr)[1 << KG], const R (&li)[1 << KG],
+                                          R (&q)[4]) {
+#pragma unroll
+  for (int r = 0; r < (1 << KG); ++r) {
+    if (r & (1 << B)) continue;
+    if ((r & cm) != cm) continue;
+    const int r1 = r | (1 << B);
+    const R p0r = pr[r], p0i = pi[r], p1r = pr[r1], p1i = pi[r1];
+    const R l0r = lr[r], l0i = li[r], l1r = lr[r1], l1i = li[r1];
+    q[0] = fma(l0r, p0i, q[0]);
+    q[0] = fma(-l0i, p0r, q[0]);
+    q[1] = fma(l1r, p1i, q[1]);
+    q[1] = fma(-l1i, p1r, q[1]);
+    q[2] = fma(l0r, p1i, q[2]);
+    q[2] = fma(-l0i, p1r, q[2]);
+    q[2] = fma(l1r, p0i, q[2]);
+    q[2] = fma(-l1i, p0r, q[2]);
+    q[3] = fma(l0r, p1r, q[3]);
+    q[3] = fma(l0i, p1i, q[3]);
+    q[3] = fma(-l1r, p0r, q[3]);
+    q[3] = fma(-l1i, p0i, q[3]);
+  }
+}
+
+// Warp sums of v[0..3] in 6 shuffles: afterwards lane 8 i holds the sum of
+// v[i] (lanes split the values by lane bits 4 and 3, then reduce the rest).
+template <typename R>
+__device__ __forceinline__ R warp_sum4(const R (&v)[4], int lane) {
+  const bool h4 = lane & 16, h3 = lane & 8;
+  R a = h4 ? v[2] : v[0], b = h4 ? v[3] : v[1];
+  const R sa = h4 ? v[0] : v[2], sb = h4 ? v[1] : v[3];
+  a += __shfl_xor_sync(0xffffffffu, sa, 16);
+  b += __shfl_xor_sync(0xffffffffu, sb, 16);
+  R w = h3 ? b : a;
+  w += __shfl_xor_sync(0xffffffffu, h3 ? a : b, 8);
+  w += __shfl_xor_sync(0xffffffffu, w, 4);
+  w += __shfl_xor_sync(0xffffffffu, w, 2);
+  w += __shfl_xor_sync(0xffffffffu, w, 1);
+  return w;
+}
+
 // Per-warp gradient accumulator: a compensated (Kahan) sum in the state's
 // precision - GB300 issues fp64 instructions at a small fraction of the fp32
 // rate, so the per-sub-block additions avoid fp64; the block converts s - c
@@ -624,7 +671,7 @@ template <int KG, typename R>
 __device__ __forceinline__ void run_group_adj(typename Cplx2<R>::T* smp,
                                               typename Cplx2<R>::T* sml, int m,
                                               const uint8_t* gb, const FOpDev<R>* ops, int o0,
-                                              int o1, KahanAcc<R>* gw) {
+                                              int o1, const R* gcoef, KahanAcc<R>* gw) {
   typedef typename Cplx2<R>::T V2;
   constexpr int D = 1 << KG;
   int soff[D];
@@ -656,19 +703,48 @@ __device__ __forceinline__ void run_group_adj(typename Cplx2<R>::T* smp,
     for (int o = o0; o < o1; ++o) {
       const FOpDev<R>& op = ops[o];
       if (op.type == FG_GRAD) {
-        R c = 0;
-        if (live) {
-          const int cm = op.cmask, pa = op.cls;
-          switch (op.b0) {
-            case 0: c = grad_pairs<KG, 0, R>(pa, cm, op.m, pr, pi, lr, li); break;
-            case 1: if constexpr (KG > 1) c = grad_pairs<KG, (KG > 1 ? 1 : 0), R>(pa, cm, op.m, pr, pi, lr, li); break;
-            case 2: if constexpr (KG > 2) c = grad_pairs<KG, (KG > 2 ? 2 : 0), R>(pa, cm, op.m, pr, pi, lr, li); break;
-            default: if constexpr (KG > 3) c = grad_pairs<KG, (KG > 3 ? 3 : 0), R>(pa, cm, op.m, pr, pi, lr, li); break;
+        const int j0 = op.pad[0] | (op.pad[1] << 8), ng = op.pad[2];
+        const int cm = op.cmask, pa = op.cls;
+        if (ng == 1 && pa != 0) {  // one Pauli generator: 4 FMAs per pair
+          R c = 0;
+          if (live) {
+            switch (op.b0) {
+              case 0: c = grad_pairs<KG, 0, R>(pa, cm, op.m, pr, pi, lr, li); break;
+              case 1: if constexpr (KG > 1) c = grad_pairs<KG, (KG > 1 ? 1 : 0), R>(pa, cm, op.m, pr, pi, lr, li); break;
+              case 2: if constexpr (KG > 2) c = grad_pairs<KG, (KG > 2 ? 2 : 0), R>(pa, cm, op.m, pr, pi, lr, li); break;
+              default: if constexpr (KG > 3) c = grad_pairs<KG, (KG > 3 ? 3 : 0), R>(pa, cm, op.m, pr, pi, lr, li); break;
+            }
+          }
+#pragma unroll
+          for (int d = 16; d; d >>= 1) c += __shfl_xor_sync(0xffffffffu, c, d);
+          if (lane == 0) kahan_add(gw[j0], c);
+        } else {  // general generator(s): the four sums, then each gradient from them
+          R q[4] = {0, 0, 0, 0};
+          if (live) {
+            switch (op.b0) {
+              case 0: grad_quad<KG, 0, R>(cm, pr, pi, lr, li, q); break;
+              case 1: if constexpr (KG > 1) grad_quad<KG, (KG > 1 ? 1 : 0), R>(cm, pr, pi, lr, li, q); break;
+              case 2: if constexpr (KG > 2) grad_quad<KG, (KG > 2 ? 2 : 0), R>(cm, pr, pi, lr, li, q); break;
+              default: if constexpr (KG > 3) grad_quad<KG, (KG > 3 ? 3 : 0), R>(cm, pr, pi, lr, li, q); break;
+            }
+          }
+          if (ng == 1) {
+            R c = op.m[0] * q[0] + op.m[1] * q[1] + op.m[2] * q[2] + op.m[3] * q[3];
+#pragma unroll
+            for (int d = 16; d; d >>= 1) c += __shfl_xor_sync(0xffffffffu, c, d);
+            if (lane == 0) kahan_add(gw[j0], c);
+          } else {
+            R v[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              const R* gm = gcoef + 4 * (j0 + (i < ng ? i : 0));
+              const R c = gm[0] * q[0] + gm[1] * q[1] + gm[2] * q[2] + gm[3] * q[3];
+              v[i] = i < ng ? c : R(0);
+            }
+            const R w = warp_sum4<R>(v, lane);
+            if ((lane & 7) == 0 && (lane >> 3) < ng) kahan_add(gw[j0 + (lane >> 3)], w);
           }
         }
-#pragma unroll
-        for (int d = 16; d; d >>= 1) c += __shfl_xor_sync(0xffffffffu, c, d);
-        if (lane == 0) kahan_add(gw[op.pad[0] | (op.pad[1] << 8)], c);
       } else {
         apply_op<KG, R>(op, pr, pi);
         apply_op<KG, R>(op, lr, li);
@@ -756,7 +832,7 @@ __global__ void __launch_bounds__(kFThreads, MINB)
       break;
     }
     for (int g = 0; g < P.ngroups; ++g) {
-      run_group_adj<KGF, R>(smp, sml, P.m, P.gbits[g], P.ops, P.gop[g], P.gop[g + 1],
+      run_group_adj<KGF, R>(smp, sml, P.m, P.gbits[g], P.ops, P.gop[g], P.gop[g + 1], P.coef,
                             gacc + warp * P.ngrad);
       if (g + 1 < P.ngroups) __syncthreads();
     }
@@ -1171,19 +1247,30 @@ bool build_params(const FusedPass& pass, const std::vector<int>& order, FusedPar
         o.m[1] = (R)f.m[0].im;
         o.cls = (f.m[0].re == -1.0 && f.m[0].im == 0.0) ? 1 : 0;
       } else if (f.type == FG_GRAD) {
-        // generator on bit t within the control mask; local gradient index in pad
+        // generator(s) on bit t within the control mask; first local gradient
+        // index in pad[0..1], count in pad[2]
         o.b0 = (uint8_t)gl(f.t);
-        o.cls = (uint8_t)f.pauli;
-        if (!f.pauli) {  // Hermitian generator [[a, b], [conj b, d]]
+        o.cls = (uint8_t)(f.ng == 1 ? f.pauli : 0);
+        if (f.ng == 1 && !f.pauli) {  // Hermitian generator [[a, b], [conj b, d]]
           o.m[0] = (R)f.m[0].re;
           o.m[1] = (R)f.m[3].re;
           o.m[2] = (R)f.m[1].re;
           o.m[3] = (R)f.m[1].im;
         }
-        const int j = P->ngrad++;
+        const int j = P->ngrad;
+        if (f.ng < 1 || f.ng > kGradPerOp || j + f.ng > kFMaxOps) return false;
+        P->ngrad += f.ng;
         o.pad[0] = (uint8_t)(j & 0xff);
         o.pad[1] = (uint8_t)(j >> 8);
-        P->gslot[j] = f.slot;
+        o.pad[2] = (uint8_t)f.ng;
+        if (f.ng == 1) {
+          P->gslot[j] = f.slot;
+        } else {  // generators of the shared evaluation in coef[4 j ...]
+          for (int i = 0; i < f.ng; ++i) {
+            P->gslot[j + i] = f.gslots[i];
+            for (int e = 0; e < 4; ++e) P->coef[4 * (j + i) + e] = (R)f.gen[i][e];
+          }
+        }
       } else {
         const int x = gl(f.a), y = gl(f.b);
         o.b0 = (uint8_t)std::min(x, y);
@@ -1192,7 +1279,13 @@ bool build_params(const FusedPass& pass, const std::vector<int>& order, FusedPar
     }
   }
   P->gop[P->ngroups] = (uint16_t)nop;
-  build_layers(pass, pos_of, P);
+  if (P->ngrad == 0) {
+    build_layers(pass, pos_of, P);
+  } else {  // reverse sweeps run gate lists; coef[] holds gradient generators
+    for (int g = 0; g <= P->ngroups; ++g) P->glay[g] = 0;
+    for (int g = 0; g < P->ngroups; ++g) P->gkind[g] = 0;
+    P->ncoef = 4 * P->ngrad;
+  }
   return true;
 }
 
@@ -1351,6 +1444,7 @@ sv_status run_adj_pass(void* psi, void* lam, int n, cudaStream_t st, const Fused
 }
 
 static_assert(sizeof(FusedParams<double>) <= 32000, "kernel parameters above the launch limit");
+static_assert(4 * kFMaxOps * sizeof(double) <= kFCoefBytes, "gradient generators exceed coef[]");
 static_assert(sizeof(FusedParams<float>) <= 32000, "kernel parameters above the launch limit");
 
 }  // namespace

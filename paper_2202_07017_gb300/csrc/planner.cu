@@ -145,13 +145,29 @@ void mul2(const cd* a, const cd* b, cd* out) {  // out = a b
     }
 }
 
+// (a, d, re b, im b) of an FG_GRAD's generator [[a, b], [conj b, d]]
+void generator_of(const FGate& g, double* out) {
+  static const double kPauli[4][4] = {{0, 0, 0, 0}, {0, 0, 1, 0}, {0, 0, 0, -1}, {1, -1, 0, 0}};
+  if (g.pauli) {
+    for (int e = 0; e < 4; ++e) out[e] = kPauli[g.pauli][e];
+  } else {
+    out[0] = g.m[0].re;
+    out[1] = g.m[3].re;
+    out[2] = g.m[1].re;
+    out[3] = g.m[1].im;
+  }
+}
+
 // Reverse sweep over [lo, hi): gate hi-1 first, each as its adjoint, a
 // parameterised gate preceded by its FG_GRAD.  Uncontrolled 1-qubit
 // adjoints are kept pending per qubit (their product W, not yet applied)
 // until another kind of gate touches the qubit; a gradient met while W is
 // pending is evaluated on the untransformed states with the generator
 // W^dagger P W (Im<W lambda|P|W psi> = Im<lambda|W^dagger P W|psi>), so a
-// run RZ, RY, RX on one qubit costs one un-apply.  A parameterised gate
+// run RZ, RY, RX on one qubit costs one un-apply.  Gradients on one qubit with
+// nothing else touching it in between share one FG_GRAD (up to kGradPerOp):
+// the ops between them act on other qubits, commute with the generator and
+// leave the inner product unchanged.  A parameterised gate
 // wider than kmax stays unfused with its gradient.
 bool to_fgates_reverse(const sv_circuit* c, const double* theta, int lo, int hi,
                        const std::vector<int>& slot_of, int kmax, std::vector<FGate>* out) {
@@ -217,7 +233,20 @@ bool to_fgates_reverse(const sv_circuit* c, const double* theta, int lo, int hi,
           gr.pauli = 0;  // general generator in m
           for (int e = 0; e < 4; ++e) gr.m[e] = M[e];
         }
-        push_fgate(std::move(gr), &last, out);
+        // nothing has touched t since a gradient on t: evaluate this one there
+        const int p = last[t];
+        if (p >= 0 && (*out)[p].type == FG_GRAD && (*out)[p].cmask == 0 && (*out)[p].t == t &&
+            (*out)[p].ng < kGradPerOp) {
+          FGate& h = (*out)[p];
+          if (h.ng == 1) {
+            generator_of(h, h.gen[0]);
+            h.gslots[0] = h.slot;
+          }
+          generator_of(gr, h.gen[h.ng]);
+          h.gslots[h.ng++] = gr.slot;
+        } else {
+          push_fgate(std::move(gr), &last, out);
+        }
       }
       if (pend[t].on) {
         cd r[4];
@@ -307,12 +336,13 @@ void form_passes(const std::vector<FGate>& F, int n, const FusionConfig& cfg,
     }
     // 2. grow S from the earliest remaining gate
     uint64_t S = lowL, blocked = 0;
-    int nS = cfg.L;
+    int nS = cfg.L, ngrads = 0;
     std::vector<int> take;
     for (size_t j = first; j < F.size(); ++j) {
       if (done[j]) continue;
       const FGate& f = F[j];
-      bool ok = f.type != FG_ALONE && !(f.qmask & blocked) && (int)take.size() < cfg.max_ops;
+      bool ok = f.type != FG_ALONE && !(f.qmask & blocked) && (int)take.size() < cfg.max_ops &&
+                (f.type != FG_GRAD || ngrads + f.ng <= cfg.max_grads);
       if (ok) {
         const uint64_t need = f.qmask & ~S;
         if (nS + popc(need) > cfg.m) {
@@ -322,9 +352,10 @@ void form_passes(const std::vector<FGate>& F, int n, const FusionConfig& cfg,
           nS += popc(need);
         }
       }
-      if (ok)
+      if (ok) {
         take.push_back((int)j);
-      else
+        if (f.type == FG_GRAD) ngrads += f.ng;
+      } else
         blocked |= f.qmask;
     }
     for (int b = 0; b < n && nS < cfg.m; ++b)

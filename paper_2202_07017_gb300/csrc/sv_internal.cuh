@@ -136,11 +136,17 @@ sv_status launch_finish(const double* src, int count, int slots, double* dst,
 // FG_GRAD (reverse sweeps only): accumulate Im<lambda|P|psi> for generator
 // `pauli` (1 X, 2 Y, 3 Z; 0: the Hermitian 2x2 in m) on bit t, restricted to
 // the control bits cmask, into gradient slot `slot`; it precedes the
-// un-applied gate whose derivative it gives.
+// un-applied gate whose derivative it gives.  ng > 1: ng gradients on the
+// same uncontrolled bit evaluated at one place, generator i in gen[i] =
+// (a, d, re b, im b) of [[a, b], [conj b, d]], slot gslots[i].
 enum { FG_1Q = 0, FG_PHASE = 1, FG_SWAP = 2, FG_ALONE = 3, FG_GRAD = 4 };
+constexpr int kGradPerOp = 4;
 struct FGate {
   int type = FG_ALONE;
   int pauli = 0, slot = -1;  // FG_GRAD; an FG_ALONE gate of a reverse sweep with a gradient
+  int ng = 1;                // FG_GRAD: gradients of this operation
+  int gslots[kGradPerOp] = {};
+  double gen[kGradPerOp][4] = {};
   uint64_t qmask = 0;  // every bit the gate touches (targets and controls)
   uint64_t cmask = 0;  // control bits (FG_1Q, FG_SWAP); all bits for FG_PHASE
   int t = 0, a = 0, b = 0;  // FG_1Q target bit; FG_SWAP bits
@@ -174,6 +180,7 @@ struct FusionConfig {
   int m = 13;                // staged bits per block
   int L = 5;                 // low bits staged as contiguous runs
   int max_ops = 200;         // gate capacity of one pass
+  int max_grads = 200;       // gradient capacity of one pass (reverse sweeps)
   int max_groups = 64;       // group capacity of one pass
 };
 
