@@ -111,10 +111,13 @@ __device__ __forceinline__ int swz<double>(int j) {
 __host__ __device__ constexpr int lowbit(int r) { return (r & 1) ? 0 : 1 + lowbit(r >> 1); }
 
 // ---- register-level gate application -------------------------------------------
+// Every operation acts on NS register tiles at once (1 for forward passes;
+// psi and lambda for reverse sweeps), so one dispatch serves both states.
 // (a, b) <- G (a, b) on every register pair of group bit B; CTRL: only where
 // the group-local control mask is set; MK: arithmetic class of G.
-template <int KG, int B, int MK, bool CTRL, typename R>
-__device__ __forceinline__ void ap1(const FOpDev<R>& op, R (&re)[1 << KG], R (&im)[1 << KG]) {
+template <int KG, int B, int MK, bool CTRL, int NS, typename R>
+__device__ __forceinline__ void ap1(const FOpDev<R>& op, R (&re)[NS][1 << KG],
+                                    R (&im)[NS][1 << KG]) {
   const int cm = op.cmask;
   M2<R> g;
 #pragma unroll
@@ -123,87 +126,112 @@ __device__ __forceinline__ void ap1(const FOpDev<R>& op, R (&re)[1 << KG], R (&i
     g.i[e] = op.m[2 * e + 1];
   }
 #pragma unroll
-  for (int r = 0; r < (1 << KG); ++r) {
-    if (r & (1 << B)) continue;
-    if (CTRL && (r & cm) != cm) continue;
-    const int r1 = r | (1 << B);
-    mv2<MK, R>(g, re[r], im[r], re[r1], im[r1]);
-  }
+  for (int q = 0; q < NS; ++q)
+#pragma unroll
+    for (int r = 0; r < (1 << KG); ++r) {
+      if (r & (1 << B)) continue;
+      if (CTRL && (r & cm) != cm) continue;
+      const int r1 = r | (1 << B);
+      mv2<MK, R>(g, re[q][r], im[q][r], re[q][r1], im[q][r1]);
+    }
 }
 
-template <int KG, int B, typename R>
-__device__ __forceinline__ void ap1_cls(const FOpDev<R>& op, R (&re)[1 << KG], R (&im)[1 << KG]) {
+template <int KG, int B, int NS, typename R>
+__device__ __forceinline__ void ap1_cls(const FOpDev<R>& op, R (&re)[NS][1 << KG],
+                                        R (&im)[NS][1 << KG]) {
   if (op.cmask) {
-    ap1<KG, B, MK_DENSE, true>(op, re, im);
+    ap1<KG, B, MK_DENSE, true, NS>(op, re, im);
     return;
   }
   switch (op.cls) {
-    case MK_REAL: ap1<KG, B, MK_REAL, false>(op, re, im); break;
-    case MK_IMOFF: ap1<KG, B, MK_IMOFF, false>(op, re, im); break;
-    case MK_DIAG: ap1<KG, B, MK_DIAG, false>(op, re, im); break;
-    default: ap1<KG, B, MK_DENSE, false>(op, re, im); break;
+    case MK_REAL: ap1<KG, B, MK_REAL, false, NS>(op, re, im); break;
+    case MK_IMOFF: ap1<KG, B, MK_IMOFF, false, NS>(op, re, im); break;
+    case MK_DIAG: ap1<KG, B, MK_DIAG, false, NS>(op, re, im); break;
+    default: ap1<KG, B, MK_DENSE, false, NS>(op, re, im); break;
   }
 }
 
-template <int KG, int B0, int B1, typename R>
-__device__ __forceinline__ void apswap(int cm, R (&re)[1 << KG], R (&im)[1 << KG]) {
+// phase on the registers whose index has every bit of the compile-time
+// group mask CM set: a sign flip (NEG) or multiplication by (c, s)
+template <int KG, int CM, bool NEG, int NS, typename R>
+__device__ __forceinline__ void phase_cm(R c, R s, R (&re)[NS][1 << KG], R (&im)[NS][1 << KG]) {
 #pragma unroll
-  for (int r = 0; r < (1 << KG); ++r) {
-    if (!((r >> B0) & 1) || ((r >> B1) & 1)) continue;
-    if ((r & cm) != cm) continue;
-    const int r2 = r ^ (1 << B0) ^ (1 << B1);
-    const R tr = re[r], ti = im[r];
-    re[r] = re[r2];
-    im[r] = im[r2];
-    re[r2] = tr;
-    im[r2] = ti;
-  }
+  for (int q = 0; q < NS; ++q)
+#pragma unroll
+    for (int r = 0; r < (1 << KG); ++r) {
+      if ((r & CM) != CM) continue;
+      if (NEG) {
+        re[q][r] = -re[q][r];
+        im[q][r] = -im[q][r];
+      } else {
+        const R xr = re[q][r], xi = im[q][r];
+        re[q][r] = c * xr - s * xi;
+        im[q][r] = s * xr + c * xi;
+      }
+    }
 }
 
-template <int KG, typename R>
-__device__ __forceinline__ void apply_op(const FOpDev<R>& op, R (&re)[1 << KG],
-                                         R (&im)[1 << KG]) {
+// the runtime mask as a compile-time one (no per-register mask tests)
+template <int KG, bool NEG, int NS, typename R>
+__device__ __forceinline__ void phase_op(int cm, R c, R s, R (&re)[NS][1 << KG],
+                                         R (&im)[NS][1 << KG]) {
+#define SV_PHASE_CASE(v) \
+  case v:                \
+    if constexpr (v < (1 << KG)) phase_cm<KG, v, NEG, NS>(c, s, re, im); \
+    break;
+  switch (cm) {
+    SV_PHASE_CASE(0) SV_PHASE_CASE(1) SV_PHASE_CASE(2) SV_PHASE_CASE(3)
+    SV_PHASE_CASE(4) SV_PHASE_CASE(5) SV_PHASE_CASE(6) SV_PHASE_CASE(7)
+    SV_PHASE_CASE(8) SV_PHASE_CASE(9) SV_PHASE_CASE(10) SV_PHASE_CASE(11)
+    SV_PHASE_CASE(12) SV_PHASE_CASE(13) SV_PHASE_CASE(14) SV_PHASE_CASE(15)
+    default: break;
+  }
+#undef SV_PHASE_CASE
+}
+
+template <int KG, int B0, int B1, int NS, typename R>
+__device__ __forceinline__ void apswap(int cm, R (&re)[NS][1 << KG], R (&im)[NS][1 << KG]) {
+#pragma unroll
+  for (int q = 0; q < NS; ++q)
+#pragma unroll
+    for (int r = 0; r < (1 << KG); ++r) {
+      if (!((r >> B0) & 1) || ((r >> B1) & 1)) continue;
+      if ((r & cm) != cm) continue;
+      const int r2 = r ^ (1 << B0) ^ (1 << B1);
+      const R tr = re[q][r], ti = im[q][r];
+      re[q][r] = re[q][r2];
+      im[q][r] = im[q][r2];
+      re[q][r2] = tr;
+      im[q][r2] = ti;
+    }
+}
+
+template <int KG, int NS, typename R>
+__device__ __forceinline__ void apply_op(const FOpDev<R>& op, R (&re)[NS][1 << KG],
+                                         R (&im)[NS][1 << KG]) {
+  static_assert(KG <= 4, "group masks beyond 4 bits");
   if (op.type == FG_1Q) {
     switch (op.b0) {
-      case 0: ap1_cls<KG, 0>(op, re, im); break;
-      case 1: if constexpr (KG > 1) ap1_cls<KG, 1>(op, re, im); break;
-      case 2: if constexpr (KG > 2) ap1_cls<KG, 2>(op, re, im); break;
-      case 3: if constexpr (KG > 3) ap1_cls<KG, 3>(op, re, im); break;
-      default: if constexpr (KG > 4) ap1_cls<KG, 4>(op, re, im); break;
+      case 0: ap1_cls<KG, 0, NS>(op, re, im); break;
+      case 1: if constexpr (KG > 1) ap1_cls<KG, 1, NS>(op, re, im); break;
+      case 2: if constexpr (KG > 2) ap1_cls<KG, 2, NS>(op, re, im); break;
+      default: if constexpr (KG > 3) ap1_cls<KG, 3, NS>(op, re, im); break;
     }
   } else if (op.type == FG_PHASE) {
-    const int cm = op.cmask;
-    if (op.cls) {  // phase -1 (Z, CZ): a sign flip
-#pragma unroll
-      for (int r = 0; r < (1 << KG); ++r) {
-        if ((r & cm) != cm) continue;
-        re[r] = -re[r];
-        im[r] = -im[r];
-      }
-    } else {
-      const R c = op.m[0], s = op.m[1];
-#pragma unroll
-      for (int r = 0; r < (1 << KG); ++r) {
-        if ((r & cm) != cm) continue;
-        const R xr = re[r], xi = im[r];
-        re[r] = c * xr - s * xi;
-        im[r] = s * xr + c * xi;
-      }
-    }
+    if (op.cls)  // phase -1 (Z, CZ): a sign flip
+      phase_op<KG, true, NS>(op.cmask, R(0), R(0), re, im);
+    else
+      phase_op<KG, false, NS>(op.cmask, op.m[0], op.m[1], re, im);
   } else {  // FG_SWAP, b0 < b1
     if constexpr (KG >= 2) {
       const int cm = op.cmask, key = op.b0 * 8 + op.b1;
       switch (key) {
-        case 0 * 8 + 1: apswap<KG, 0, 1>(cm, re, im); break;
-        case 0 * 8 + 2: if constexpr (KG > 2) apswap<KG, 0, 2>(cm, re, im); break;
-        case 1 * 8 + 2: if constexpr (KG > 2) apswap<KG, 1, 2>(cm, re, im); break;
-        case 0 * 8 + 3: if constexpr (KG > 3) apswap<KG, 0, 3>(cm, re, im); break;
-        case 1 * 8 + 3: if constexpr (KG > 3) apswap<KG, 1, 3>(cm, re, im); break;
-        case 2 * 8 + 3: if constexpr (KG > 3) apswap<KG, 2, 3>(cm, re, im); break;
-        case 0 * 8 + 4: if constexpr (KG > 4) apswap<KG, 0, 4>(cm, re, im); break;
-        case 1 * 8 + 4: if constexpr (KG > 4) apswap<KG, 1, 4>(cm, re, im); break;
-        case 2 * 8 + 4: if constexpr (KG > 4) apswap<KG, 2, 4>(cm, re, im); break;
-        case 3 * 8 + 4: if constexpr (KG > 4) apswap<KG, 3, 4>(cm, re, im); break;
+        case 0 * 8 + 1: apswap<KG, 0, 1, NS>(cm, re, im); break;
+        case 0 * 8 + 2: if constexpr (KG > 2) apswap<KG, 0, 2, NS>(cm, re, im); break;
+        case 1 * 8 + 2: if constexpr (KG > 2) apswap<KG, 1, 2, NS>(cm, re, im); break;
+        case 0 * 8 + 3: if constexpr (KG > 3) apswap<KG, 0, 3, NS>(cm, re, im); break;
+        case 1 * 8 + 3: if constexpr (KG > 3) apswap<KG, 1, 3, NS>(cm, re, im); break;
+        case 2 * 8 + 3: if constexpr (KG > 3) apswap<KG, 2, 3, NS>(cm, re, im); break;
         default: break;
       }
     }
@@ -230,19 +258,19 @@ __device__ __forceinline__ void run_group(typename Cplx2<R>::T* sm, int m, const
 #pragma unroll
     for (int i = 0; i < KG; ++i) b = ((b & ~lm[i]) << 1) | (b & lm[i]);
     const int sb = swz<R>(b);
-    R re[D], im[D];
+    R re[1][D], im[1][D];
 #pragma unroll
     for (int r = 0; r < D; ++r) {
       const V2 v = sm[sb ^ soff[r]];
-      re[r] = v.x;
-      im[r] = v.y;
+      re[0][r] = v.x;
+      im[0][r] = v.y;
     }
-    for (int o = o0; o < o1; ++o) apply_op<KG, R>(ops[o], re, im);
+    for (int o = o0; o < o1; ++o) apply_op<KG, 1, R>(ops[o], re, im);
 #pragma unroll
     for (int r = 0; r < D; ++r) {
       V2 v;
-      v.x = re[r];
-      v.y = im[r];
+      v.x = re[0][r];
+      v.y = im[0][r];
       sm[sb ^ soff[r]] = v;
     }
   }
@@ -604,14 +632,14 @@ __device__ __forceinline__ R grad_pairs(int pauli, int cm, const R* gm, const R 
 // bit B needs: with z_rs = conj(l_r) p_s over the pairs inside cm,
 // Im<lambda|M|psi> = a Im z00 + d Im z11 + re b Im(z01 + z10) + im b Re(z01 - z10).
 // Several gradients on one bit then cost these 12 FMAs per pair once.
-template <int KG, int B, typename R>
+template <int KG, int B, bool CTRL, typename R>
 __device__ __forceinline__ void grad_quad(int cm, const R (&pr)[1 << KG], const R (&pi)[1 << KG],
                                           const R (&lr)[1 << KG], const R (&li)[1 << KG],
                                           R (&q)[4]) {
 #pragma unroll
   for (int r = 0; r < (1 << KG); ++r) {
     if (r & (1 << B)) continue;
-    if ((r & cm) != cm) continue;
+    if (CTRL && (r & cm) != cm) continue;
     const int r1 = r | (1 << B);
     const R p0r = pr[r], p0i = pi[r], p1r = pr[r1], p1i = pi[r1];
     const R l0r = lr[r], l0i = li[r], l1r = lr[r1], l1i = li[r1];
@@ -627,6 +655,18 @@ __device__ __forceinline__ void grad_quad(int cm, const R (&pr)[1 << KG], const 
     q[3] = fma(l0i, p1i, q[3]);
     q[3] = fma(-l1r, p0r, q[3]);
     q[3] = fma(-l1i, p0i, q[3]);
+  }
+}
+
+template <int KG, bool CTRL, typename R>
+__device__ __forceinline__ void grad_quad_at(int b, int cm, const R (&pr)[1 << KG],
+                                             const R (&pi)[1 << KG], const R (&lr)[1 << KG],
+                                             const R (&li)[1 << KG], R (&q)[4]) {
+  switch (b) {
+    case 0: grad_quad<KG, 0, CTRL, R>(cm, pr, pi, lr, li, q); break;
+    case 1: if constexpr (KG > 1) grad_quad<KG, (KG > 1 ? 1 : 0), CTRL, R>(cm, pr, pi, lr, li, q); break;
+    case 2: if constexpr (KG > 2) grad_quad<KG, (KG > 2 ? 2 : 0), CTRL, R>(cm, pr, pi, lr, li, q); break;
+    default: if constexpr (KG > 3) grad_quad<KG, (KG > 3 ? 3 : 0), CTRL, R>(cm, pr, pi, lr, li, q); break;
   }
 }
 
@@ -691,15 +731,19 @@ __device__ __forceinline__ void run_group_adj(typename Cplx2<R>::T* smp,
 #pragma unroll
     for (int i = 0; i < KG; ++i) b = ((b & ~lm[i]) << 1) | (b & lm[i]);
     const int sb = swz<R>(b);
-    R pr[D], pi[D], lr[D], li[D];
+    R re[2][D], im[2][D];  // [0] psi, [1] lambda
 #pragma unroll
     for (int r = 0; r < D; ++r) {
       const V2 v = smp[sb ^ soff[r]], w = sml[sb ^ soff[r]];
-      pr[r] = v.x;
-      pi[r] = v.y;
-      lr[r] = w.x;
-      li[r] = w.y;
+      re[0][r] = v.x;
+      im[0][r] = v.y;
+      re[1][r] = w.x;
+      im[1][r] = w.y;
     }
+    R(&pr)[D] = re[0];
+    R(&pi)[D] = im[0];
+    R(&lr)[D] = re[1];
+    R(&li)[D] = im[1];
     for (int o = o0; o < o1; ++o) {
       const FOpDev<R>& op = ops[o];
       if (op.type == FG_GRAD) {
@@ -721,12 +765,10 @@ __device__ __forceinline__ void run_group_adj(typename Cplx2<R>::T* smp,
         } else {  // general generator(s): the four sums, then each gradient from them
           R q[4] = {0, 0, 0, 0};
           if (live) {
-            switch (op.b0) {
-              case 0: grad_quad<KG, 0, R>(cm, pr, pi, lr, li, q); break;
-              case 1: if constexpr (KG > 1) grad_quad<KG, (KG > 1 ? 1 : 0), R>(cm, pr, pi, lr, li, q); break;
-              case 2: if constexpr (KG > 2) grad_quad<KG, (KG > 2 ? 2 : 0), R>(cm, pr, pi, lr, li, q); break;
-              default: if constexpr (KG > 3) grad_quad<KG, (KG > 3 ? 3 : 0), R>(cm, pr, pi, lr, li, q); break;
-            }
+            if (cm)
+              grad_quad_at<KG, true, R>(op.b0, cm, pr, pi, lr, li, q);
+            else
+              grad_quad_at<KG, false, R>(op.b0, cm, pr, pi, lr, li, q);
           }
           if (ng == 1) {
             R c = op.m[0] * q[0] + op.m[1] * q[1] + op.m[2] * q[2] + op.m[3] * q[3];
@@ -746,8 +788,7 @@ __device__ __forceinline__ void run_group_adj(typename Cplx2<R>::T* smp,
           }
         }
       } else {
-        apply_op<KG, R>(op, pr, pi);
-        apply_op<KG, R>(op, lr, li);
+        apply_op<KG, 2, R>(op, re, im);
       }
     }
     if (live) {
