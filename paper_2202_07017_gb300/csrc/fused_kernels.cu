@@ -714,10 +714,20 @@ __device__ __forceinline__ void run_group_adj(typename Cplx2<R>::T* smp,
                                               int o1, const R* gcoef, KahanAcc<R>* gw) {
   typedef typename Cplx2<R>::T V2;
   constexpr int D = 1 << KG;
-  int soff[D];
-  soff[0] = 0;
+  // register offsets: a table for up to 8 registers, else XORs of the
+  // swizzled bit offsets at each access (frees 16 registers for the tiles)
+  constexpr bool kTable = KG <= 3;
+  int sw[KG];
+  int soff[kTable ? D : 1];
+  if constexpr (kTable) {
+    soff[0] = 0;
 #pragma unroll
-  for (int r = 1; r < D; ++r) soff[r] = soff[r & (r - 1)] ^ swz<R>(1 << gb[lowbit(r)]);
+    for (int r = 1; r < D; ++r) soff[r] = soff[r & (r - 1)] ^ swz<R>(1 << gb[lowbit(r)]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < KG; ++i) sw[i] = swz<R>(1 << gb[i]);
+  }
+#define SV_ADJ_OFF(r) (kTable ? soff[kTable ? (r) : 0] : reg_off<KG>((r), sw))
   int lm[KG];
 #pragma unroll
   for (int i = 0; i < KG; ++i) lm[i] = (1 << gb[i]) - 1;
@@ -734,7 +744,7 @@ __device__ __forceinline__ void run_group_adj(typename Cplx2<R>::T* smp,
     R re[2][D], im[2][D];  // [0] psi, [1] lambda
 #pragma unroll
     for (int r = 0; r < D; ++r) {
-      const V2 v = smp[sb ^ soff[r]], w = sml[sb ^ soff[r]];
+      const V2 v = smp[sb ^ SV_ADJ_OFF(r)], w = sml[sb ^ SV_ADJ_OFF(r)];
       re[0][r] = v.x;
       im[0][r] = v.y;
       re[1][r] = w.x;
@@ -799,11 +809,12 @@ __device__ __forceinline__ void run_group_adj(typename Cplx2<R>::T* smp,
         v.y = pi[r];
         w.x = lr[r];
         w.y = li[r];
-        smp[sb ^ soff[r]] = v;
-        sml[sb ^ soff[r]] = w;
+        smp[sb ^ SV_ADJ_OFF(r)] = v;
+        sml[sb ^ SV_ADJ_OFF(r)] = w;
       }
     }
   }
+#undef SV_ADJ_OFF
 }
 
 template <int RANK>
@@ -1454,13 +1465,15 @@ sv_status run_adj_pass(void* psi, void* lam, int n, cudaStream_t st, const Fused
   }
   typedef void (*Kern)(uint64_t, const FusedParams<R>, double*, int);
   constexpr int MB = sizeof(R) == 4 ? 3 : 1;
-  const Kern kern = kg <= 1   ? kfused_adj<R, 1, MB>
-                    : kg == 2 ? kfused_adj<R, 2, MB>
-                              : kfused_adj<R, 3, MB>;
-  if (kg > 3) {
-    set_error("fused reverse pass: register groups wider than 3 qubits");
+  constexpr int KMAX = sizeof(R) == 4 ? 4 : 3;  // two 2^k tiles of complex128 above 3 spill
+  if (kg > KMAX) {
+    set_error("fused reverse pass: register groups wider than %d qubits", KMAX);
     return SV_ERR_INVALID;
   }
+  const Kern kern = kg <= 1   ? kfused_adj<R, 1, MB>
+                    : kg == 2 ? kfused_adj<R, 2, MB>
+                    : kg == 3 ? kfused_adj<R, 3, MB>
+                              : kfused_adj<R, (KMAX > 3 ? 4 : 3), 2>;
   const size_t smem =
       1024 + 2 * (size_t)P.slice_bytes + sizeof(KahanAcc<R>) * (kFThreads / 32) * P.ngrad;
   static std::map<std::pair<const void*, size_t>, int> resident;

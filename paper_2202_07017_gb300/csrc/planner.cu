@@ -302,7 +302,8 @@ FusionConfig fusion_config(int n, sv_dtype dt, int fuse_k) {
 }
 
 FusionConfig fusion_config_reverse(int n, sv_dtype dt, int fuse_k) {
-  FusionConfig c = fusion_config(n, dt, std::min(fuse_k, 3));  // two 2^k tiles per thread
+  // two 2^k tiles per thread: up to 4 qubits for complex64, 3 for complex128
+  FusionConfig c = fusion_config(n, dt, std::min(fuse_k, dt == SV_C64 ? 4 : 3));
   if (c.m > 10) {
     c.m -= 1;
     if (c.m - c.L < c.fuse_k) c.L = std::max(1, c.m - c.fuse_k);

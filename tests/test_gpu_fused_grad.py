@@ -45,17 +45,52 @@ def _grad(c, theta, terms, dtype, psi0=None, checkpoints=(), fuse_k=4, profile=F
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("fuse_k", [3, 4])
 @pytest.mark.parametrize("n,seed", [(11, 1), (13, 2)])
-def test_fused_grad_random_circuits_vs_parameter_shift(dtype, n, seed):
+def test_fused_grad_random_circuits_vs_parameter_shift(dtype, fuse_k, n, seed):
     kinds = ("H", "X", "Y", "Z", "RX", "RY", "RZ", "U1", "SWAP", "MATRIX")
     c, theta = W.random_gates(n, 60, 900 + seed, max_tar=3, max_ctrl=2, kinds=kinds)
     terms = W.random_pauli_sum(n, 8, seed)
     psi0 = rounded(W.random_state(n, seed), dtype)
-    e, g, final, prof = _grad(c, theta, terms, dtype, psi0, profile=True)
+    e, g, final, prof = _grad(c, theta, terms, dtype, psi0, fuse_k=fuse_k, profile=True)
     assert f"kfused_adj_{dtype}" in prof, prof
     assert max_err(final, oracle.run(c, theta, psi0)) <= 4 * TOL[dtype]
     assert abs(e - oracle.energy(c, theta, terms, psi0)) <= TOL[dtype] * sum(abs(t[0]) for t in terms)
     assert c.n_params > 0
+    assert _rel(g, oracle.grad_param_shift(c, theta, terms, psi0=psi0)) <= GRAD_TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("fuse_k", [3, 4])
+def test_fused_grad_rotation_runs(dtype, fuse_k):
+    """Runs of six rotations per qubit (two shared evaluations of up to four
+    gradients each), a controlled rotation and a phase on some qubits between
+    runs (no sharing across them), CZ bricks between layers."""
+    n = 11
+    gates, p = [], 0
+    for layer in range(3):
+        for q in range(n):
+            for kind in ("RX", "RY", "RZ", "RX", "RY", "RZ"):
+                gates.append(W.Gate(kind, (q,), (), p))
+                p += 1
+            if q % 4 == 1:
+                gates.append(W.Gate("RY", (q,), ((q + 3) % n,), p))
+                p += 1
+                gates.append(W.Gate("RZ", (q,), (), p))
+                p += 1
+            if q % 4 == 2:
+                gates.append(W.Gate("U1", (q,), (), -1, 0.3))
+                gates.append(W.Gate("RX", (q,), (), p))
+                p += 1
+        for q in range(layer % 2, n - 1, 2):
+            gates.append(W.Gate("Z", (q + 1,), (q,)))
+    c = W.Circuit(n, gates, p)
+    theta = np.array([W.SplitMix64(77 + i).angle() for i in range(p)])
+    terms = W.tfim(n)
+    psi0 = rounded(W.random_state(n, 5), dtype)
+    e, g, _, prof = _grad(c, theta, terms, dtype, psi0, fuse_k=fuse_k, profile=True)
+    assert f"kfused_adj_{dtype}" in prof, prof
+    assert abs(e - oracle.energy(c, theta, terms, psi0)) <= TOL[dtype] * sum(abs(t[0]) for t in terms)
     assert _rel(g, oracle.grad_param_shift(c, theta, terms, psi0=psi0)) <= GRAD_TOL[dtype]
 
 
