@@ -224,6 +224,23 @@ __device__ void group_offsets(const BGroup& g, int (&off)[1 << K], int (&lm)[K])
   for (int i = 0; i < K; ++i) lm[i] = (1 << g.bits[i]) - 1;
 }
 
+// Storage order of a single-block item's states: amplitude x lives at
+// swzb(x) = x ^ ((x >> 4) & 15).  The map is a bijection of [0, 2^n) for every
+// n and linear over XOR, so swzb(b | off) = swzb(b) ^ swzb(off) for disjoint
+// bits.  It spreads the 16 amplitudes of a 128-byte row over the row by the
+// next four index bits: a warp whose lanes step over a register group's low
+// bits then reaches 16 different 8-byte bank pairs instead of one.
+__device__ __forceinline__ int swzb(int x) { return x ^ ((x >> 4) & 15); }
+
+template <int K>
+__device__ void group_offsets_swzb(const BGroup& g, int (&off)[1 << K], int (&lm)[K]) {
+  off[0] = 0;
+#pragma unroll
+  for (int r = 1; r < (1 << K); ++r) off[r] = off[r & (r - 1)] ^ swzb(1 << g.bits[lowbit_b(r)]);
+#pragma unroll
+  for (int i = 0; i < K; ++i) lm[i] = (1 << g.bits[i]) - 1;
+}
+
 template <int K>
 __device__ __forceinline__ int sub_base(int s, const int (&lm)[K], int kk) {
   int b = s;
@@ -237,17 +254,17 @@ __device__ __forceinline__ int sub_base(int s, const int (&lm)[K], int kk) {
 template <int K>
 __device__ void group_fwd(float2* psi, int n, const BGroup& g, const BOp* ops, const float* mats) {
   int off[1 << K], lm[K];
-  group_offsets<K>(g, off, lm);
+  group_offsets_swzb<K>(g, off, lm);
   const int kk = g.k;
   const int nsub = 1 << (n - kk);
   const int width = 1 << kk;
   for (int s = threadIdx.x; s < nsub; s += blockDim.x) {
-    const int b = sub_base<K>(s, lm, kk);
+    const int b = swzb(sub_base<K>(s, lm, kk));
     float re[1 << K], im[1 << K];
 #pragma unroll
     for (int r = 0; r < (1 << K); ++r)
       if (r < width) {
-        const float2 v = psi[b | off[r]];
+        const float2 v = psi[b ^ off[r]];
         re[r] = v.x;
         im[r] = v.y;
       }
@@ -261,7 +278,7 @@ __device__ void group_fwd(float2* psi, int n, const BGroup& g, const BOp* ops, c
     }
 #pragma unroll
     for (int r = 0; r < (1 << K); ++r)
-      if (r < width) psi[b | off[r]] = make_float2(re[r], im[r]);
+      if (r < width) psi[b ^ off[r]] = make_float2(re[r], im[r]);
   }
 }
 
@@ -270,7 +287,7 @@ template <int K>
 __device__ void group_bwd(float2* psi, float2* lam, int n, const BGroup& g, const BOp* ops,
                           const float* mats, float2* wpart) {
   int off[1 << K], lm[K];
-  group_offsets<K>(g, off, lm);
+  group_offsets_swzb<K>(g, off, lm);
   const int kk = g.k;
   const int nsub = 1 << (n - kk);
   const int width = 1 << kk;
@@ -280,13 +297,13 @@ __device__ void group_bwd(float2* psi, float2* lam, int n, const BGroup& g, cons
   for (int it = 0; it < iters; ++it) {
     const int s = threadIdx.x + it * blockDim.x;
     const bool live = s < nsub;
-    const int b = live ? sub_base<K>(s, lm, kk) : 0;
+    const int b = live ? swzb(sub_base<K>(s, lm, kk)) : 0;
     float pr[1 << K], pi[1 << K], lr[1 << K], li[1 << K];
 #pragma unroll
     for (int r = 0; r < (1 << K); ++r) {
       pr[r] = pi[r] = lr[r] = li[r] = 0.f;
       if (live && r < width) {
-        const float2 v = psi[b | off[r]], w = lam[b | off[r]];
+        const float2 v = psi[b ^ off[r]], w = lam[b ^ off[r]];
         pr[r] = v.x;
         pi[r] = v.y;
         lr[r] = w.x;
@@ -317,8 +334,8 @@ __device__ void group_bwd(float2* psi, float2* lam, int n, const BGroup& g, cons
 #pragma unroll
       for (int r = 0; r < (1 << K); ++r)
         if (r < width) {
-          psi[b | off[r]] = make_float2(pr[r], pi[r]);
-          lam[b | off[r]] = make_float2(lr[r], li[r]);
+          psi[b ^ off[r]] = make_float2(pr[r], pi[r]);
+          lam[b ^ off[r]] = make_float2(lr[r], li[r]);
         }
     }
   }
@@ -393,6 +410,7 @@ __global__ void __launch_bounds__(MAXT, MINB) kbatch(const BatchArgs A) {
       }
       for (int e = 0; e < 8; ++e) mats[8 * gi + e] = (float)m[e];
     }
+    // |0...0>: swzb(0) = 0 and swzb maps every other index to a nonzero one
     for (int x = threadIdx.x; x < dim; x += blockDim.x) psi[x] = make_float2(x == 0 ? 1.f : 0.f, 0.f);
     for (int i = threadIdx.x; i < nwarps * kBMaxParams; i += blockDim.x)
       wpart[i] = make_float2(0.f, 0.f);
@@ -419,13 +437,14 @@ __global__ void __launch_bounds__(MAXT, MINB) kbatch(const BatchArgs A) {
       group_fwd<K>(psi, C.n, sgrp[gg], sops, mats);
       __syncthreads();
     }
-    // lambda = H psi, E = Re <psi|lambda>
+    // lambda = H psi, E = Re <psi|lambda> (logical index x, stored at swzb(x))
     float2 ek = make_float2(0.f, 0.f);
     for (int x = threadIdx.x; x < dim; x += blockDim.x) {
+      const int px = swzb(x);
       float orr = 0.f, oi = 0.f;
       for (int t = 0; t < C.nterms; ++t) {
         const BTerm T = sterm[t];
-        const float2 b = psi[x ^ (int)T.xm];
+        const float2 b = psi[px ^ swzb((int)T.xm)];
         const float cr = scoef[t].x, ci = scoef[t].y;
         const float sr = cr * b.x - ci * b.y, si = cr * b.y + ci * b.x;
         if (__popcll(((uint64_t)x ^ T.xm) & T.zm) & 1) {
@@ -436,8 +455,8 @@ __global__ void __launch_bounds__(MAXT, MINB) kbatch(const BatchArgs A) {
           oi += si;
         }
       }
-      lam[x] = make_float2(orr, oi);
-      const float2 a = psi[x];
+      lam[px] = make_float2(orr, oi);
+      const float2 a = psi[px];
       ksum_add(ek, a.x * orr + a.y * oi);
     }
     double e = warp_sum_d(ksum_value(ek));
