@@ -66,7 +66,9 @@ def hbm_peak():
 def algorithmic_bytes(kernel: str, n: int, amp_bytes: int) -> float:
     """B_alg per launch for the QFT's kernels: 2 * bytes * |A|, A the
     amplitudes the gate changes (H: 2^n, controlled-U1: 2^(n-2),
-    SWAP: 2^(n-1))."""
+    SWAP: 2^(n-1)); the basis-state initialisation writes 2^n once."""
+    if kernel.startswith("kinit"):
+        return 1.0 * amp_bytes * 2 ** n
     if kernel.startswith("kphase"):
         return 2.0 * amp_bytes * 2 ** (n - 2)
     if kernel.startswith("kswap"):
