@@ -154,13 +154,55 @@ __device__ __forceinline__ void pair_apply_c(const float* M, int cm, float (&re)
   }
 }
 
+// controlled phase / sign flip with the control mask CM fixed at compile time
+// (no per-register mask tests)
+template <int K, int B, int CLS, int CM>
+__device__ __forceinline__ void pair_apply_cm(const float* M, float (&re)[1 << K],
+                                              float (&im)[1 << K]) {
+  if constexpr ((CM >> B) & 1) {
+    return;  // a mask holding the target bit selects no pair (as the runtime test)
+  } else {
+    const float g3r = M[6], g3i = M[7];
+#pragma unroll
+    for (int r = 0; r < (1 << K); ++r) {
+      if (r & (1 << B)) continue;
+      if ((r & CM) != CM) continue;
+      const int r1 = r | (1 << B);
+      const float br = re[r1], bi = im[r1];
+      if (CLS == BC_NEG) {
+        re[r1] = -br;
+        im[r1] = -bi;
+      } else {
+        re[r1] = g3r * br - g3i * bi;
+        im[r1] = g3r * bi + g3i * br;
+      }
+    }
+  }
+}
+
+template <int K, int B, int CLS>
+__device__ __forceinline__ void pair_apply_ctrl(const float* M, int cm, float (&re)[1 << K],
+                                                float (&im)[1 << K]) {
+#define SV_CM_CASE(v)                                                       \
+  case v:                                                                   \
+    if constexpr (v < (1 << K)) pair_apply_cm<K, B, CLS, v>(M, re, im);     \
+    break;
+  switch (cm) {
+    SV_CM_CASE(1) SV_CM_CASE(2) SV_CM_CASE(3) SV_CM_CASE(4) SV_CM_CASE(5)
+    SV_CM_CASE(6) SV_CM_CASE(7) SV_CM_CASE(8) SV_CM_CASE(9) SV_CM_CASE(10)
+    SV_CM_CASE(11) SV_CM_CASE(12) SV_CM_CASE(13) SV_CM_CASE(14) SV_CM_CASE(15)
+    default: pair_apply_c<K, B, CLS, true>(M, cm, re, im); break;
+  }
+#undef SV_CM_CASE
+}
+
 template <int K, int B>
 __device__ __forceinline__ void pair_apply(int cls, const float* M, int cm, float (&re)[1 << K],
                                            float (&im)[1 << K]) {
   if (cm) {
     switch (cls) {
-      case BC_PHASE: pair_apply_c<K, B, BC_PHASE, true>(M, cm, re, im); break;
-      case BC_NEG: pair_apply_c<K, B, BC_NEG, true>(M, cm, re, im); break;
+      case BC_PHASE: pair_apply_ctrl<K, B, BC_PHASE>(M, cm, re, im); break;
+      case BC_NEG: pair_apply_ctrl<K, B, BC_NEG>(M, cm, re, im); break;
       default: pair_apply_c<K, B, BC_DENSE, true>(M, cm, re, im); break;
     }
   } else {
@@ -185,26 +227,44 @@ __device__ __forceinline__ void pair_apply_dag(int cls, const float* M, int cm,
 }
 
 // sum over the pairs of Im( conj(l0) (P p)_0 + conj(l1) (P p)_1 )
-template <int K, int B>
-__device__ __forceinline__ float pair_grad(int pauli, int cm, const float (&pr)[1 << K],
-                                           const float (&pi)[1 << K], const float (&lr)[1 << K],
-                                           const float (&li)[1 << K]) {
+template <int K, int B, int PAULI, bool CTRL>
+__device__ __forceinline__ float pair_grad_c(int cm, const float (&pr)[1 << K],
+                                             const float (&pi)[1 << K], const float (&lr)[1 << K],
+                                             const float (&li)[1 << K]) {
   float acc = 0.f;
 #pragma unroll
   for (int r = 0; r < (1 << K); ++r) {
     if (r & (1 << B)) continue;
     const int r1 = r | (1 << B);
-    if ((r & cm) != cm) continue;
+    if (CTRL && (r & cm) != cm) continue;
     const float p0r = pr[r], p0i = pi[r], p1r = pr[r1], p1i = pi[r1];
     const float l0r = lr[r], l0i = li[r], l1r = lr[r1], l1i = li[r1];
-    if (pauli == 1)
+    if (PAULI == 1)
       acc += (l0r * p1i - l0i * p1r) + (l1r * p0i - l1i * p0r);
-    else if (pauli == 2)
+    else if (PAULI == 2)
       acc += -(l0r * p1r + l0i * p1i) + (l1r * p0r + l1i * p0i);
     else
       acc += (l0r * p0i - l0i * p0r) - (l1r * p1i - l1i * p1r);
   }
   return acc;
+}
+
+template <int K, int B>
+__device__ __forceinline__ float pair_grad(int pauli, int cm, const float (&pr)[1 << K],
+                                           const float (&pi)[1 << K], const float (&lr)[1 << K],
+                                           const float (&li)[1 << K]) {
+  if (cm) {
+    switch (pauli) {
+      case 1: return pair_grad_c<K, B, 1, true>(cm, pr, pi, lr, li);
+      case 2: return pair_grad_c<K, B, 2, true>(cm, pr, pi, lr, li);
+      default: return pair_grad_c<K, B, 3, true>(cm, pr, pi, lr, li);
+    }
+  }
+  switch (pauli) {
+    case 1: return pair_grad_c<K, B, 1, false>(0, pr, pi, lr, li);
+    case 2: return pair_grad_c<K, B, 2, false>(0, pr, pi, lr, li);
+    default: return pair_grad_c<K, B, 3, false>(0, pr, pi, lr, li);
+  }
 }
 
 #define SV_BIT_SWITCH(B, CALL) \
