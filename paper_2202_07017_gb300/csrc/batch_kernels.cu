@@ -226,6 +226,63 @@ __device__ __forceinline__ void pair_apply_dag(int cls, const float* M, int cm,
   pair_apply<K, B>(cls, h, cm, re, im);
 }
 
+// M^dagger on the pairs of two tiles (psi and lambda) behind one dispatch
+template <int K, int B, int CLS, bool CTRL>
+__device__ __forceinline__ void pair_apply_c2(const float* h, int cm, float (&pr)[1 << K],
+                                              float (&pi)[1 << K], float (&lr)[1 << K],
+                                              float (&li)[1 << K]) {
+  pair_apply_c<K, B, CLS, CTRL>(h, cm, pr, pi);
+  pair_apply_c<K, B, CLS, CTRL>(h, cm, lr, li);
+}
+
+template <int K, int B, int CLS, int CM>
+__device__ __forceinline__ void pair_apply_cm2(const float* h, float (&pr)[1 << K],
+                                               float (&pi)[1 << K], float (&lr)[1 << K],
+                                               float (&li)[1 << K]) {
+  pair_apply_cm<K, B, CLS, CM>(h, pr, pi);
+  pair_apply_cm<K, B, CLS, CM>(h, lr, li);
+}
+
+template <int K, int B, int CLS>
+__device__ __forceinline__ void pair_apply_ctrl2(const float* h, int cm, float (&pr)[1 << K],
+                                                 float (&pi)[1 << K], float (&lr)[1 << K],
+                                                 float (&li)[1 << K]) {
+#define SV_CM_CASE(v)                                                            \
+  case v:                                                                        \
+    if constexpr (v < (1 << K)) pair_apply_cm2<K, B, CLS, v>(h, pr, pi, lr, li); \
+    break;
+  switch (cm) {
+    SV_CM_CASE(1) SV_CM_CASE(2) SV_CM_CASE(3) SV_CM_CASE(4) SV_CM_CASE(5)
+    SV_CM_CASE(6) SV_CM_CASE(7) SV_CM_CASE(8) SV_CM_CASE(9) SV_CM_CASE(10)
+    SV_CM_CASE(11) SV_CM_CASE(12) SV_CM_CASE(13) SV_CM_CASE(14) SV_CM_CASE(15)
+    default: pair_apply_c2<K, B, CLS, true>(h, cm, pr, pi, lr, li); break;
+  }
+#undef SV_CM_CASE
+}
+
+template <int K, int B>
+__device__ __forceinline__ void pair_apply_dag2(int cls, const float* M, int cm,
+                                                float (&pr)[1 << K], float (&pi)[1 << K],
+                                                float (&lr)[1 << K], float (&li)[1 << K]) {
+  const float h[8] = {M[0], -M[1], M[4], -M[5], M[2], -M[3], M[6], -M[7]};
+  if (cm) {
+    switch (cls) {
+      case BC_PHASE: pair_apply_ctrl2<K, B, BC_PHASE>(h, cm, pr, pi, lr, li); break;
+      case BC_NEG: pair_apply_ctrl2<K, B, BC_NEG>(h, cm, pr, pi, lr, li); break;
+      default: pair_apply_c2<K, B, BC_DENSE, true>(h, cm, pr, pi, lr, li); break;
+    }
+  } else {
+    switch (cls) {
+      case BC_REAL: pair_apply_c2<K, B, BC_REAL, false>(h, 0, pr, pi, lr, li); break;
+      case BC_IMOFF: pair_apply_c2<K, B, BC_IMOFF, false>(h, 0, pr, pi, lr, li); break;
+      case BC_DIAG: pair_apply_c2<K, B, BC_DIAG, false>(h, 0, pr, pi, lr, li); break;
+      case BC_PHASE: pair_apply_c2<K, B, BC_PHASE, false>(h, 0, pr, pi, lr, li); break;
+      case BC_NEG: pair_apply_c2<K, B, BC_NEG, false>(h, 0, pr, pi, lr, li); break;
+      default: pair_apply_c2<K, B, BC_DENSE, false>(h, 0, pr, pi, lr, li); break;
+    }
+  }
+}
+
 // sum over the pairs of Im( conj(l0) (P p)_0 + conj(l1) (P p)_1 )
 template <int K, int B, int PAULI, bool CTRL>
 __device__ __forceinline__ float pair_grad_c(int cm, const float (&pr)[1 << K],
@@ -382,11 +439,8 @@ __device__ void group_bwd(float2* psi, float2* lam, int n, const BGroup& g, cons
         c = warp_sum_f(c);
         if (lane == 0) ksum_add(wpart[warp * kBMaxParams + op.param], c);
       }
-#define SV_BWD(BB)                                  \
-  if constexpr (BB < K) {                           \
-    pair_apply_dag<K, BB>(op.cls, M, op.cm, pr, pi); \
-    pair_apply_dag<K, BB>(op.cls, M, op.cm, lr, li); \
-  }
+#define SV_BWD(BB) \
+  if constexpr (BB < K) pair_apply_dag2<K, BB>(op.cls, M, op.cm, pr, pi, lr, li)
       SV_BIT_SWITCH(op.b0, SV_BWD)
 #undef SV_BWD
     }
