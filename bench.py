@@ -281,6 +281,44 @@ def fused_layered(torch, n=33, depth=40, k=4):
             "unfused_full_estimate_s": t2_u * len(c.gates) / len(layer2.gates)}
 
 
+def qft_c128(torch, n=30, reps=2):
+    """The QFT at n = 30 in complex128 (16 GiB state), unfused: gate-apps/s and
+    each kernel's algorithmic bandwidth from the library's CUDA events."""
+    import workloads as W
+    from paper_2202_07017_gb300 import (C128, pack_circuit, sv_alloc, sv_apply_circuit, sv_free,
+                                        sv_init, sv_profile_start, sv_profile_stop)
+    circ = W.qft(n)
+    pc = pack_circuit(circ)
+    x = W.random_basis_index(n, SEED_QFT)
+    stream = torch.cuda.current_stream()
+    h = sv_alloc(n, C128, stream.cuda_stream)
+    try:
+        sv_init(h, x)
+        sv_apply_circuit(h, pc, None, 0)  # warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        sv_profile_start()
+        e0.record(stream)
+        for _ in range(reps):
+            sv_init(h, x)
+            sv_apply_circuit(h, pc, None, 0)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        prof = sv_profile_stop()
+    finally:
+        sv_free(h)
+    secs = e0.elapsed_time(e1) / 1e3 / reps
+    kernels = {}
+    for name, (cnt, ms) in prof.items():
+        b = algorithmic_bytes(name, n, 16)
+        kernels[name] = {"launches": cnt, "avg_ms": ms / cnt,
+                         "achieved_gbs": b * cnt / (ms / 1e3) / 1e9}
+    return {"workload": f"qft n={n} complex128, unfused, seeded basis input, "
+                        f"{len(circ.gates)} gates", "state_bytes": 16 << n,
+            "ms_per_step": 1e3 * secs, "gate_apps_per_s": len(circ.gates) / secs,
+            "kernels": kernels}
+
+
 def layered_adjoint(torch, n=28, depth=40):
     """Adjoint gradient of <sum Z_i> for the random layered circuit at n = 28
     (complex64, 3900 gates, 3360 parameters; --adj-n changes n) with forward
@@ -434,6 +472,7 @@ def main():
     ap.add_argument("--no-fused", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-adj28", action="store_true")
+    ap.add_argument("--no-c128", action="store_true")
     ap.add_argument("--adj-n", type=int, default=28,
                     help="qubits of the layered-circuit adjoint measurement")
     ap.add_argument("--batch-tune", type=int, default=1, choices=[0, 1, 2, 3],
@@ -575,6 +614,7 @@ def main():
         fused = None if args.no_fused else fused_layered(torch, n=args.fused_n)
         batch = None if args.no_batch else batch_solves(torch, tune=args.batch_tune)
         adj28 = None if args.no_adj28 else layered_adjoint(torch, n=args.adj_n)
+        c128 = None if args.no_c128 else qft_c128(torch, n=n)
         cpu = None
         if not args.no_cpu:
             threads = os.cpu_count() or 1
@@ -594,7 +634,9 @@ def main():
             "config": {"workload": f"qft n={n} complex64, unfused (one kernel per gate), "
                                    f"seeded basis input, {n_gates} gates",
                        "n_qubits": n, "gates": n_gates, "state_bytes": 8 << n,
-                       "l2": "inputs larger than L2 (8 GiB state)",
+                       "l2": (f"inputs larger than L2 ({(8 << n) / 2**30:g} GiB state)"
+                              if (8 << n) > 129e6 else
+                              f"state of {(8 << n) / 2**20:g} MiB resident in L2 (no flush)"),
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline,
             "step_hbm": {"alg_bytes_per_step": step_bytes / args.steps,
@@ -609,6 +651,7 @@ def main():
             "fused": fused,
             "batch": batch,
             "adjoint_n28": adj28,
+            "qft_c128": c128,
             "measure": meas,
         }
     sv_free(h)
