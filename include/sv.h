@@ -191,6 +191,22 @@ sv_status sv_fusion_plan(const sv_circuit* c, const double* theta, sv_dtype dtyp
                          int32_t* order, int32_t* pass_of, int32_t* n_passes,
                          int32_t* staged_bits);
 
+/* Host-only dry run of the reverse-sweep planner used by sv_grad_fused for
+ * the gates [lo, hi) of c (no GPU call).  The sweep un-applies the gates in
+ * reverse and takes each parameterised gate's gradient Im<lambda|P|psi>
+ * before its un-apply (Sec. 3 gradients; the adjoint form); uncontrolled
+ * 1-qubit adjoints on a qubit are multiplied until another gate touches
+ * it, and gradients on one qubit with nothing else touching it in between
+ * share one evaluation.  events receives, in execution order, 4 ints per
+ * event: kind (0 un-apply of a gate, 1 gradient of a gate), the circuit gate
+ * index, the pass (-1: applied alone by the unfused kernels) and, for
+ * gradients, the evaluation id (gradients sharing one evaluation share it;
+ * -1 for un-applies).  Caller-owned, 8 (hi - lo) ints.  *n_events: events
+ * written; *n_passes: passes planned.  Errors: SV_ERR_INVALID. */
+sv_status sv_fusion_plan_reverse(const sv_circuit* c, const double* theta, sv_dtype dtype,
+                                 int fuse_k, int lo, int hi, int32_t* events,
+                                 int32_t* n_events, int32_t* n_passes);
+
 /* ---- reductions (fp64 accumulation, fixed reduction order) ------------ */
 
 /* <psi|psi>.  Synchronises.  Result bit-identical across calls. */

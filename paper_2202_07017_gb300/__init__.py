@@ -17,7 +17,7 @@ from .sv import (C64, C128, EXPORTS, PackedBatch, sv_batch_create, sv_batch_free
                  sv_batch_info, sv_batch_kernel, sv_batch_run, sv_batch_run_graph, PackedCircuit, PackedPauli, SvError, load, pack_circuit,
                  pack_pauli, sv_adjoint, sv_alloc, sv_apply_circuit, sv_apply_gate,
                  sv_apply_pauli_sum, sv_copy, sv_download, sv_expval, sv_expval_async, sv_free,
-                 sv_fusion_plan, sv_pauli_rotation, sv_probabilities, sv_sample, sv_trotter,
+                 sv_fusion_plan, sv_fusion_plan_reverse, sv_pauli_rotation, sv_probabilities, sv_sample, sv_trotter,
                  sv_grad, sv_grad_fused, sv_info, sv_init, sv_last_error, sv_launch_count, sv_norm, sv_profile_start,
                  sv_profile_stop, sv_set_stream,
                  sv_sync, sv_upload, sv_version, sv_wrap, sv_host_alloc, sv_host_free,

@@ -106,7 +106,7 @@ void push_fgate(FGate f, std::vector<int>* last, std::vector<FGate>* out) {
     const int p = (*last)[f.t];
     if (p >= 0 && (*out)[p].type == FG_1Q && (*out)[p].cmask == 0 && (*out)[p].t == f.t) {
       mul2_left(f.m, (*out)[p].m);
-      (*out)[p].origs.push_back(f.orig);
+      for (int o : f.origs) (*out)[p].origs.push_back(o);
       (*out)[p].orig = f.orig;
       return;
     }
@@ -177,6 +177,7 @@ bool to_fgates_reverse(const sv_circuit* c, const double* theta, int lo, int hi,
     bool on = false;
     cd W[4];
     int orig = -1;
+    std::vector<int> origs;  // every circuit gate folded into W
   };
   std::vector<Pend> pend(64);
   auto flush = [&](int t) {
@@ -188,9 +189,10 @@ bool to_fgates_reverse(const sv_circuit* c, const double* theta, int lo, int hi,
     f.cmask = 0;
     for (int e = 0; e < 4; ++e) f.m[e] = pend[t].W[e];
     f.orig = pend[t].orig;
-    f.origs.push_back(f.orig);
+    f.origs = pend[t].origs;
     push_fgate(std::move(f), &last, out);
     pend[t].on = false;
+    pend[t].origs.clear();
   };
   HostMatrix G, D;
   for (int i = hi - 1; i >= lo; --i) {
@@ -207,6 +209,12 @@ bool to_fgates_reverse(const sv_circuit* c, const double* theta, int lo, int hi,
         D.m[r * d + q] = {z.re, -z.im};
       }
     FGate f = classify(g, i, n, D, kmax);
+    if (f.type == FG_PHASE && G.k == 1 && g.n_ctrl == 0) {  // Z, U1: a 1-qubit adjoint too
+      f.type = FG_1Q;
+      f.t = n - 1 - g.targets[0];
+      f.cmask = 0;
+      for (int e = 0; e < 4; ++e) f.m[e] = D.m[e];
+    }
     const int pauli = g.param < 0 ? 0 : g.kind == SV_GATE_RX ? 1 : g.kind == SV_GATE_RY ? 2 : 3;
     if (f.type == FG_1Q && f.cmask == 0) {
       const int t = f.t;
@@ -257,6 +265,7 @@ bool to_fgates_reverse(const sv_circuit* c, const double* theta, int lo, int hi,
         for (int e = 0; e < 4; ++e) pend[t].W[e] = f.m[e];
       }
       pend[t].orig = i;
+      pend[t].origs.push_back(i);
       continue;
     }
     for (int b = 0; b < 64; ++b)

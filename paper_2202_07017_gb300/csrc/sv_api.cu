@@ -502,6 +502,70 @@ sv_status sv_fusion_plan(const sv_circuit* c, const double* theta, sv_dtype dtyp
   return SV_OK;
 }
 
+static bool valid_grad_circuit(const sv_circuit* c);
+
+sv_status sv_fusion_plan_reverse(const sv_circuit* c, const double* theta, sv_dtype dtype,
+                                 int fuse_k, int lo, int hi, int32_t* events,
+                                 int32_t* n_events, int32_t* n_passes) {
+  if (!c || !events || !n_events || !n_passes || c->n_qubits < 1 ||
+      c->n_qubits > SV_MAX_QUBITS || fuse_k < 2 || fuse_k > 5 ||
+      (dtype != SV_C64 && dtype != SV_C128) || lo < 0 || hi < lo || hi > c->n_gates) {
+    set_error("sv_fusion_plan_reverse: bad arguments");
+    return SV_ERR_INVALID;
+  }
+  sv_state_s probe;
+  probe.n = c->n_qubits;
+  probe.dt = dtype;
+  probe.data = (void*)1;
+  if (!valid_circuit(&probe, c, theta) || !valid_grad_circuit(c)) return SV_ERR_INVALID;
+  std::vector<int> slot_of(c->n_gates, -1), gate_of;
+  for (int i = 0; i < c->n_gates; ++i)
+    if (c->gates[i].param >= 0) {
+      slot_of[i] = (int)gate_of.size();
+      gate_of.push_back(i);
+    }
+  const FusionConfig cfg = fusion_config_reverse(c->n_qubits, dtype, fuse_k);
+  std::vector<FusionItem> plan;
+  if (!plan_fusion_reverse(c, theta, lo, hi, slot_of, cfg, &plan)) return SV_ERR_INVALID;
+  const int cap = 2 * (hi - lo);
+  int t = 0, p = 0, e = 0;
+  auto emit = [&](int kind, int gate, int pass, int eval) {
+    if (t < cap) {
+      events[4 * t] = kind;
+      events[4 * t + 1] = gate;
+      events[4 * t + 2] = pass;
+      events[4 * t + 3] = eval;
+    }
+    ++t;
+  };
+  for (const FusionItem& it : plan) {
+    if (it.is_pass) {
+      for (const FusedGroup& g : it.pass.groups)
+        for (int oi : g.ops) {
+          const FGate& f = it.pass.gates[oi];
+          if (f.type == FG_GRAD) {
+            for (int j = 0; j < f.ng; ++j)
+              emit(1, gate_of[f.ng == 1 ? f.slot : f.gslots[j]], p, e);
+            ++e;
+          } else {
+            for (int o : f.origs) emit(0, o, p, -1);
+          }
+        }
+      ++p;
+    } else {
+      if (it.slot >= 0) emit(1, gate_of[it.slot], -1, e++);
+      emit(0, it.gate, -1, -1);
+    }
+  }
+  *n_events = t;
+  *n_passes = p;
+  if (t > cap) {
+    set_error("sv_fusion_plan_reverse: internal error, %d events for %d gates", t, hi - lo);
+    return SV_ERR_INVALID;
+  }
+  return SV_OK;
+}
+
 static sv_status norm_into(sv_state s, double* dst) {
   const int need = kRedMaxBlocks;
   sv_status st = ensure_partials(s, need);

@@ -53,7 +53,8 @@ EXPORTS = ("sv_alloc", "sv_wrap", "sv_free", "sv_set_stream", "sv_info", "sv_ini
            "sv_upload", "sv_download", "sv_host_alloc", "sv_host_free", "sv_copy", "sv_apply_gate", "sv_apply_circuit",
            "sv_norm", "sv_expval", "sv_expval_async", "sv_apply_pauli_sum", "sv_adjoint",
            "sv_grad", "sv_grad_fused", "sv_sync", "sv_selftest_wait", "sv_check_guards", "sv_last_error", "sv_launch_count", "sv_version",
-           "sv_profile_start", "sv_profile_stop", "sv_fusion_plan", "sv_expval_noalloc",
+           "sv_profile_start", "sv_profile_stop", "sv_fusion_plan", "sv_fusion_plan_reverse",
+           "sv_expval_noalloc",
            "sv_probabilities", "sv_sample", "sv_pauli_rotation", "sv_trotter",
            "sv_batch_create", "sv_batch_plan", "sv_batch_info", "sv_batch_kernel", "sv_batch_run", "sv_batch_run_graph", "sv_batch_grad",
            "sv_batch_free")
@@ -121,6 +122,8 @@ def load(build: bool = True):
         "sv_expval_noalloc": [c_vp, ctypes.c_int, ctypes.c_int, P(SvPauliSum), c_vp, c_vp],
         "sv_fusion_plan": [P(SvCircuit), P(c_dbl), ctypes.c_int, ctypes.c_int, P(c_i32), P(c_i32),
                            P(c_i32), P(c_i32)],
+        "sv_fusion_plan_reverse": [P(SvCircuit), P(c_dbl), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                   ctypes.c_int, P(c_i32), P(c_i32), P(c_i32)],
         "sv_profile_stop": [ctypes.c_char_p, ctypes.c_size_t],
     }
     for name, args in sig.items():
@@ -307,6 +310,22 @@ def sv_fusion_plan(circuit, theta=None, dtype: int = C64, fuse_k: int = 4):
     masks = [(int(staged[2 * i]) & 0xffffffff) | ((int(staged[2 * i + 1]) & 0xffffffff) << 32)
              for i in range(p)]
     return order[:pc.n_gates], pass_of[:pc.n_gates], p, masks
+
+
+def sv_fusion_plan_reverse(circuit, theta=None, dtype: int = C64, fuse_k: int = 4, lo: int = 0,
+                           hi=None):
+    """Dry run of the reverse-sweep planner over gates [lo, hi): (events, n_passes),
+    events an (n, 4) array of (kind 0 un-apply / 1 gradient, gate, pass, evaluation)."""
+    pc = pack_circuit(circuit)
+    keep, tp = _theta_ptr(theta)
+    hi = pc.n_gates if hi is None else int(hi)
+    ev = np.zeros(max(1, 8 * (hi - lo)), np.int32)
+    nev, npass = c_i32(), c_i32()
+    P = ctypes.POINTER
+    _check(load().sv_fusion_plan_reverse(ctypes.byref(pc.c), tp, dtype, fuse_k, int(lo), hi,
+                                         ev.ctypes.data_as(P(c_i32)), ctypes.byref(nev),
+                                         ctypes.byref(npass)))
+    return ev[:4 * nev.value].reshape(-1, 4), npass.value
 
 
 def sv_pauli_rotation(h: int, term_ops, theta: float) -> None:
