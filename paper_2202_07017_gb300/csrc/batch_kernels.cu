@@ -38,9 +38,11 @@ constexpr int kBMaxGates = 480;    // gates of one circuit (static smem stays < 
 constexpr int kBMaxParams = 256;   // parameters of one circuit
 constexpr int kBMaxWarps = 16;     // 512 threads
 constexpr int kBMaxTerms = 64;     // Pauli terms of one Hamiltonian
+static_assert(SV_BATCH_MAX_QUBITS < 31, "term masks are packed in 31 bits");
 
 struct BCirc {
   int n, ngates, gate0, ngroups, group0, nparams, nterms, term0;
+  int ndiag;  // terms[term0 .. term0 + ndiag) are diagonal (no X or Y factor)
 };
 struct BGateDesc {
   int kind;   // SV_GATE_* (1-qubit kinds)
@@ -476,7 +478,8 @@ __global__ void __launch_bounds__(MAXT, MINB) kbatch(const BatchArgs A) {
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   BOp* sops = reinterpret_cast<BOp*>(dyn_smem);
   BGroup* sgrp = reinterpret_cast<BGroup*>(dyn_smem + kBOpsBytes);
-  BTerm* sterm = reinterpret_cast<BTerm*>(dyn_smem + kBOpsBytes + kBGroupBytes);
+  // per term: (swzb(x mask), z mask | parity of (x mask & z mask) << 31)
+  int2* sterm = reinterpret_cast<int2*>(dyn_smem + kBOpsBytes + kBGroupBytes);
   // the terms' coefficients rounded to fp32 once per item (a conversion from
   // fp64 per term and amplitude would occupy GB300's slow fp64 pipe)
   float2* scoef = reinterpret_cast<float2*>(dyn_smem + kBOpsBytes + kBGroupBytes + kBTermBytes);
@@ -541,7 +544,8 @@ __global__ void __launch_bounds__(MAXT, MINB) kbatch(const BatchArgs A) {
       }
       for (int t = threadIdx.x; t < C.nterms; t += blockDim.x) {
         const BTerm T = A.terms[C.term0 + t];
-        sterm[t] = T;
+        const int xm = (int)T.xm, zm = (int)T.zm;  // n <= SV_BATCH_MAX_QUBITS < 31
+        sterm[t] = make_int2(swzb(xm), (int)((unsigned)zm | ((unsigned)__popc(xm & zm) << 31)));
         scoef[t] = make_float2((float)T.cre, (float)T.cim);
       }
     }
@@ -555,13 +559,27 @@ __global__ void __launch_bounds__(MAXT, MINB) kbatch(const BatchArgs A) {
     float2 ek = make_float2(0.f, 0.f);
     for (int x = threadIdx.x; x < dim; x += blockDim.x) {
       const int px = swzb(x);
-      float orr = 0.f, oi = 0.f;
-      for (int t = 0; t < C.nterms; ++t) {
-        const BTerm T = sterm[t];
-        const float2 b = psi[px ^ swzb((int)T.xm)];
-        const float cr = scoef[t].x, ci = scoef[t].y;
-        const float sr = cr * b.x - ci * b.y, si = cr * b.y + ci * b.x;
-        if (__popcll(((uint64_t)x ^ T.xm) & T.zm) & 1) {
+      const float2 a = psi[px];
+      // sign of term t at x: parity of ((x ^ xm) & zm) = parity(x & zm) ^ parity(xm & zm)
+      float dr = 0.f, di = 0.f;
+      for (int t = 0; t < C.ndiag; ++t) {
+        const int2 q = sterm[t];
+        const float2 cf = scoef[t];
+        if (__popc(x & q.y) & 1) {  // bit 31 (parity of xm & zm) is 0 here
+          dr -= cf.x;
+          di -= cf.y;
+        } else {
+          dr += cf.x;
+          di += cf.y;
+        }
+      }
+      float orr = dr * a.x - di * a.y, oi = dr * a.y + di * a.x;
+      for (int t = C.ndiag; t < C.nterms; ++t) {
+        const int2 q = sterm[t];
+        const float2 b = psi[px ^ q.x];
+        const float2 cf = scoef[t];
+        const float sr = cf.x * b.x - cf.y * b.y, si = cf.x * b.y + cf.y * b.x;
+        if ((__popc(x & q.y) + ((unsigned)q.y >> 31)) & 1) {
           orr -= sr;
           oi -= si;
         } else {
@@ -570,7 +588,6 @@ __global__ void __launch_bounds__(MAXT, MINB) kbatch(const BatchArgs A) {
         }
       }
       lam[px] = make_float2(orr, oi);
-      const float2 a = psi[px];
       ksum_add(ek, a.x * orr + a.y * oi);
     }
     double e = warp_sum_d(ksum_value(ek));
@@ -1039,13 +1056,19 @@ bool plan_circuit(const sv_circuit* c, const sv_pauli_sum* H, int k, HostPlan* P
     pending.swap(rest);
   }
   C.ngroups = (int)P->groups.size() - C.group0;
-  for (int t = 0; t < H->n_terms; ++t) {
-    const uint64_t xm = H->xmask[t], zm = H->zmask[t];
-    const int ny = popc64(xm & zm) & 3;
-    const double cf = H->coeff[t];
-    P->terms.push_back({xm, zm, ny == 0 ? cf : ny == 2 ? -cf : 0.0,
-                        ny == 1 ? cf : ny == 3 ? -cf : 0.0});
-  }
+  // diagonal terms first: their coefficients combine per amplitude before
+  // the one product with psi_x
+  C.ndiag = 0;
+  for (int pass = 0; pass < 2; ++pass)
+    for (int t = 0; t < H->n_terms; ++t) {
+      const uint64_t xm = H->xmask[t], zm = H->zmask[t];
+      if ((xm == 0) != (pass == 0)) continue;
+      const int ny = popc64(xm & zm) & 3;
+      const double cf = H->coeff[t];
+      P->terms.push_back({xm, zm, ny == 0 ? cf : ny == 2 ? -cf : 0.0,
+                          ny == 1 ? cf : ny == 3 ? -cf : 0.0});
+      if (pass == 0) ++C.ndiag;
+    }
   P->circs.push_back(C);
   return P->ops.size() < (size_t)0x7fffffff;
 }
