@@ -139,6 +139,16 @@ __device__ __forceinline__ void ap1(const FOpDev<R>& op, R (&re)[NS][1 << KG],
 template <int KG, int B, int NS, typename R>
 __device__ __forceinline__ void ap1_cls(const FOpDev<R>& op, R (&re)[NS][1 << KG],
                                         R (&im)[NS][1 << KG]) {
+  if constexpr (NS == 2 && KG >= 4) {
+    // two 16-amplitude tiles: one dense form only (the class-specific
+    // variants raise register pressure past the 2-blocks-per-SM budget; the
+    // un-applied products of a reverse sweep are mostly dense anyway)
+    if (op.cmask)
+      ap1<KG, B, MK_DENSE, true, NS>(op, re, im);
+    else
+      ap1<KG, B, MK_DENSE, false, NS>(op, re, im);
+    return;
+  }
   if (op.cmask) {
     ap1<KG, B, MK_DENSE, true, NS>(op, re, im);
     return;
@@ -218,6 +228,20 @@ __device__ __forceinline__ void apply_op(const FOpDev<R>& op, R (&re)[NS][1 << K
       default: if constexpr (KG > 3) ap1_cls<KG, 3, NS>(op, re, im); break;
     }
   } else if (op.type == FG_PHASE) {
+    if constexpr (NS == 2 && KG >= 4) {
+      const int cm = op.cmask;
+      const R c = op.cls ? R(-1) : op.m[0], sn = op.cls ? R(0) : op.m[1];
+#pragma unroll
+      for (int q = 0; q < NS; ++q)
+#pragma unroll
+        for (int r = 0; r < (1 << KG); ++r) {
+          if ((r & cm) != cm) continue;
+          const R xr = re[q][r], xi = im[q][r];
+          re[q][r] = c * xr - sn * xi;
+          im[q][r] = sn * xr + c * xi;
+        }
+      return;
+    }
     if (op.cls)  // phase -1 (Z, CZ): a sign flip
       phase_op<KG, true, NS>(op.cmask, R(0), R(0), re, im);
     else
@@ -732,7 +756,8 @@ __device__ __forceinline__ void run_group_adj(typename Cplx2<R>::T* smp,
 #pragma unroll
   for (int i = 0; i < KG; ++i) lm[i] = (1 << gb[i]) - 1;
   const int nsub = 1 << (m - KG);
-  const int iters = (nsub + kFThreads - 1) / kFThreads;
+  // reverse slices hold at most 2^12 amplitudes: one sub-block per thread for 4-qubit groups
+  const int iters = KG >= 4 ? 1 : (nsub + kFThreads - 1) / kFThreads;
   const int lane = threadIdx.x & 31;
   for (int it = 0; it < iters; ++it) {
     const int s = threadIdx.x + it * kFThreads;
@@ -1468,6 +1493,10 @@ sv_status run_adj_pass(void* psi, void* lam, int n, cudaStream_t st, const Fused
   constexpr int KMAX = sizeof(R) == 4 ? 4 : 3;  // two 2^k tiles of complex128 above 3 spill
   if (kg > KMAX) {
     set_error("fused reverse pass: register groups wider than %d qubits", KMAX);
+    return SV_ERR_INVALID;
+  }
+  if (kg >= 4 && (1 << (P.m - kg)) > kFThreads) {  // the kernel runs one sub-block per thread
+    set_error("fused reverse pass: slice of 2^%d amplitudes too large for 4-qubit groups", P.m);
     return SV_ERR_INVALID;
   }
   const Kern kern = kg <= 1   ? kfused_adj<R, 1, MB>
