@@ -230,6 +230,17 @@ __device__ __forceinline__ void apply_op(const FOpDev<R>& op, R (&re)[NS][1 << K
   } else if (op.type == FG_PHASE) {
     if constexpr (NS == 2 && KG >= 4) {
       const int cm = op.cmask;
+      if (op.cls) {  // sign flips of the common two-bit masks (CZ) at compile time
+        switch (cm) {
+          case 3: phase_cm<KG, 3, true, NS>(R(0), R(0), re, im); return;
+          case 5: phase_cm<KG, 5, true, NS>(R(0), R(0), re, im); return;
+          case 6: phase_cm<KG, 6, true, NS>(R(0), R(0), re, im); return;
+          case 9: phase_cm<KG, 9, true, NS>(R(0), R(0), re, im); return;
+          case 10: phase_cm<KG, 10, true, NS>(R(0), R(0), re, im); return;
+          case 12: phase_cm<KG, 12, true, NS>(R(0), R(0), re, im); return;
+          default: break;
+        }
+      }
       const R c = op.cls ? R(-1) : op.m[0], sn = op.cls ? R(0) : op.m[1];
 #pragma unroll
       for (int q = 0; q < NS; ++q)
