@@ -845,8 +845,16 @@ __device__ __forceinline__ void run_group_adj(typename Cplx2<R>::T* smp,
         v.y = pi[r];
         w.x = lr[r];
         w.y = li[r];
-        smp[sb ^ SV_ADJ_OFF(r)] = v;
-        sml[sb ^ SV_ADJ_OFF(r)] = w;
+        int o2;
+        if constexpr (kTable) {
+          o2 = sb ^ soff[kTable ? r : 0];
+        } else {
+          int sbr = sb;
+          asm volatile("mov.b32 %0, %1;" : "=r"(sbr) : "r"(sb));  // recompute, do not keep
+          o2 = sbr ^ reg_off<KG>(r, sw);
+        }
+        smp[o2] = v;
+        sml[o2] = w;
       }
     }
   }
