@@ -849,8 +849,11 @@ __device__ __forceinline__ void run_group_adj(typename Cplx2<R>::T* smp,
         if constexpr (kTable) {
           o2 = sb ^ soff[kTable ? r : 0];
         } else {
+          // an opaque copy of sb: the store addresses are recomputed here
+          // instead of being kept live from the loads across every operation
+          // (16 registers that pushed the 4-qubit tiles into spills)
           int sbr = sb;
-          asm volatile("mov.b32 %0, %1;" : "=r"(sbr) : "r"(sb));  // recompute, do not keep
+          asm volatile("mov.b32 %0, %1;" : "=r"(sbr) : "r"(sb));
           o2 = sbr ^ reg_off<KG>(r, sw);
         }
         smp[o2] = v;
