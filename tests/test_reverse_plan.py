@@ -140,3 +140,25 @@ def test_segments_and_bad_arguments():
             sv_fusion_plan_reverse(c, theta, C64, 4, lo, hi)
     with pytest.raises(SvError):
         sv_fusion_plan_reverse(c, theta, C64, 6)
+
+
+def test_gradient_capacity_per_pass():
+    """A pass holds at most 200 gradients (its accumulator slots): 400 rotations
+    on 12 qubits with nothing else between them need at least two passes, and
+    the plan stays valid."""
+    n = 12
+    gates, p = [], 0
+    for rep in range(400 // n + 1):
+        for q in range(n):
+            if p == 400:
+                break
+            gates.append(W.Gate(("RX", "RY", "RZ")[rep % 3], (q,), (), p))
+            p += 1
+    c = W.Circuit(n, gates, p)
+    theta = np.linspace(0.0, 3.0, p)
+    ev, npass, evals = check_reverse_plan(c, theta, C64, 4)
+    per_pass = {}
+    for e in ev:
+        if e[0] == 1:
+            per_pass[int(e[2])] = per_pass.get(int(e[2]), 0) + 1
+    assert npass >= 2 and max(per_pass.values()) <= 200
