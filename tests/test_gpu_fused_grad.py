@@ -194,3 +194,31 @@ def test_fused_grad_rejects_bad_group_width():
             st.grad(c, theta, W.tfim(4), [], fuse_k=6)
     finally:
         st.close()
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_fused_grad_more_gradients_than_one_pass_holds(dtype):
+    """400 rotations on 12 qubits with nothing else between them: the reverse
+    sweep needs several passes of at most 200 gradient slots; sampled
+    entries against the oracle's shift rule."""
+    n = 12
+    gates, p = [], 0
+    for rep in range(400 // n + 1):
+        for q in range(n):
+            if p == 400:
+                break
+            gates.append(W.Gate(("RX", "RY", "RZ")[rep % 3], (q,), (), p))
+            p += 1
+        if rep % 7 == 6:
+            for q in range(0, n - 1, 2):
+                gates.append(W.Gate("Z", (q + 1,), (q,)))
+    c = W.Circuit(n, gates, p)
+    theta = np.array([W.SplitMix64(313 + i).angle() for i in range(p)])
+    terms = W.tfim(n)
+    psi0 = rounded(W.random_state(n, 11), dtype)
+    e, g, _, prof = _grad(c, theta, terms, dtype, psi0, profile=True)
+    assert f"kfused_adj_{dtype}" in prof, prof
+    sample = list(range(0, p, 10)) + [p - 1]
+    ref = oracle.grad_param_shift(c, theta, terms, params=sample, psi0=psi0)
+    assert abs(e - oracle.energy(c, theta, terms, psi0)) <= TOL[dtype] * sum(abs(t[0]) for t in terms)
+    assert _rel(g[sample], ref[sample]) <= GRAD_TOL[dtype]
