@@ -317,8 +317,10 @@ sv_status sv_grad(sv_state s, const sv_circuit* c, const double* theta,
  * 2..5).  Checkpoints split the circuit into segments that are fused
  * separately, so no gate moves across a checkpoint.  A reverse pass stages
  * psi and lambda together (one staged bit fewer than a forward pass,
- * register groups of at most 3 qubits); before un-applying each
- * parameterised gate it accumulates that gate's Im<lambda|P|psi> per block
+ * register groups of at most 4 qubits for complex64 and 3 for complex128);
+ * before un-applying each parameterised gate it accumulates that gate's
+ * Im<lambda|P|psi> (gradients on one qubit with nothing else touching it in
+ * between share one evaluation), per warp in compensated fp32 and per block
  * in fp64, and a fixed-order finish adds the block sums.  States of fewer
  * than 10 qubits, or passes without a bulk-copy geometry, take the unfused
  * sweep.  Outputs, checkpoints and errors as sv_grad. */
