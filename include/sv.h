@@ -336,8 +336,10 @@ sv_status sv_grad_fused(sv_state s, const sv_circuit* c, const double* theta,
  * hamiltonians[item_circuit[i]] and the adjoint gradient dE_i/dtheta.  All
  * items run in one persistent kernel whose thread blocks pull items from an
  * atomic queue (longest first); each block keeps its item's two states in a
- * workspace slot that stays in L1/L2.  Energies and gradients accumulate in
- * fp64 in a fixed order.
+ * workspace slot that stays in L1/L2, or (a variant the autotuner may pick)
+ * psi of up to 14 qubits and lambda of up to 13 in shared memory.  Energies
+ * and gradients accumulate per warp in compensated fp32 and across warps in
+ * fp64, in a fixed order.
  *
  * Limits: <= SV_BATCH_MAX_QUBITS qubits, <= 480 gates and <= 256
  * parameters per circuit, <= 64 Pauli terms per Hamiltonian; gates are the
