@@ -422,6 +422,31 @@ def sampling(torch, h, n, shots=1 << 20):
             "kernels_ms": {k: v[1] for k, v in prof.items()}}
 
 
+def reductions(torch, h, n, reps=3):
+    """Norm, sum-Z energy (diagonal terms only) and TFIM energy of the n = 30
+    state already in `h` (the QFT output): per-kernel times from the
+    library's CUDA events and GB/s on one read of the state (8 * 2^n bytes;
+    an X term also reads each amplitude's partner)."""
+    import workloads as W
+    from paper_2202_07017_gb300 import sv_expval, sv_norm, sv_profile_start, sv_profile_stop
+    out = {"workload": f"reductions over the n={n} complex64 QFT state",
+           "alg_bytes_per_launch": 8 * 2 ** n}
+    cases = (("norm", "knorm", lambda: sv_norm(h)),
+             ("energy_sum_z", "kexpval", lambda: sv_expval(h, W.sum_z(n))),
+             ("energy_tfim", "kexpval", lambda: sv_expval(h, W.tfim(n))))
+    for name, kern, fn in cases:
+        fn()
+        sv_profile_start()
+        for _ in range(reps):
+            v = fn()
+        prof = sv_profile_stop()
+        cnt, ms = prof.get(kern, (0, float("nan")))
+        out[name] = {"value": v, "kernel": kern, "launches": cnt,
+                     "avg_ms": ms / cnt if cnt else None,
+                     "achieved_gbs": 8 * 2 ** n / (ms / cnt / 1e3) / 1e9 if cnt else None}
+    return out
+
+
 def gate_table(n, dtype, reps=5):
     """Per-kernel bandwidth for single gates on every kind of bit position:
     H on bit p, controlled-U1 on bits (a, b), SWAP on (a, b).  Algorithmic
@@ -610,6 +635,7 @@ def main():
                    "download_ms": 1e3 * float(ph[2]),
                    "path": "sv_upload (sv_host_alloc buffer) + sv_apply_circuit + sv_download"}
         meas = sampling(torch, h, n)
+        red = reductions(torch, h, n)
         adj = adjoint_ratio(torch)
         fused = None if args.no_fused else fused_layered(torch, n=args.fused_n)
         batch = None if args.no_batch else batch_solves(torch, tune=args.batch_tune)
@@ -653,6 +679,7 @@ def main():
             "adjoint_n28": adj28,
             "qft_c128": c128,
             "measure": meas,
+            "reductions": red,
         }
     sv_free(h)
     if out is not None:

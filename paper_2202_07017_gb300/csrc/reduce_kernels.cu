@@ -24,16 +24,37 @@ int red_blocks(uint64_t units) {
 
 namespace {
 
+// Per-thread sums.  complex64: a compensated (Kahan) fp32 sum (GB300 issues
+// fp64 at a small fraction of the fp32 rate, so a conversion and an fp64 add
+// per amplitude would bound the pass); the block then meets in fp64.
+// complex128: plain fp64.
+template <typename R>
+struct ThreadSum {
+  R s = 0, c = 0;
+  __device__ __forceinline__ void add(R x) {
+    if constexpr (sizeof(R) == 4) {
+      const R y = x - c;
+      const R t = s + y;
+      c = (t - s) - y;
+      s = t;
+    } else {
+      s += x;
+    }
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
 __global__ void __launch_bounds__(kRedThreads)
     knorm_c64(const float4* __restrict__ psi, uint64_t nvec, double* __restrict__ partials) {
-  double acc = 0.0;
+  ThreadSum<float> acc;
+#pragma unroll 4
   for (uint64_t v = (uint64_t)blockIdx.x * kRedThreads + threadIdx.x; v < nvec;
        v += (uint64_t)gridDim.x * kRedThreads) {
     const float4 a = psi[v];
-    acc += (double)(a.x * a.x + a.y * a.y + a.z * a.z + a.w * a.w);
+    acc.add(a.x * a.x + a.y * a.y + a.z * a.z + a.w * a.w);
   }
-  acc = block_sum(acc);
-  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+  const double t = block_sum(acc.value());
+  if (threadIdx.x == 0) partials[blockIdx.x] = t;
 }
 
 __global__ void __launch_bounds__(kRedThreads)
@@ -48,28 +69,45 @@ __global__ void __launch_bounds__(kRedThreads)
   if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
 
+// coefficient k of the chunk in the kernel's precision
+template <typename R>
+__device__ __forceinline__ R coef_re(const PauliDev& P, int k) {
+  if constexpr (sizeof(R) == 4) return P.cre32[k]; else return P.cre[k];
+}
+template <typename R>
+__device__ __forceinline__ R coef_im(const PauliDev& P, int k) {
+  if constexpr (sizeof(R) == 4) return P.cim32[k]; else return P.cim[k];
+}
+
 // sum_x Re( c'_k s_k(x) conj(psi_x) psi_{x ^ xm_k} ) over this chunk's terms.
+// The chunk's first P.nd terms are diagonal (xm = 0, real coefficients):
+// their signed coefficients add up per index before one product with |psi_x|^2.
 template <typename R, typename T2>
 __global__ void __launch_bounds__(kRedThreads)
     kexpval(const T2* __restrict__ psi, uint64_t dim, const __grid_constant__ PauliDev P,
             double* __restrict__ partials) {
-  double acc = 0.0;
+  ThreadSum<R> acc;
   for (uint64_t x = (uint64_t)blockIdx.x * kRedThreads + threadIdx.x; x < dim;
        x += (uint64_t)gridDim.x * kRedThreads) {
     const T2 a = psi[x];
-    R sum = 0;
-    for (int k = 0; k < P.nt; ++k) {
+    R d = 0;
+    for (int k = 0; k < P.nd; ++k) {
+      const R c = coef_re<R>(P, k);
+      d += (__popcll(x & P.zm[k]) & 1) ? -c : c;
+    }
+    R sum = d * (a.x * a.x + a.y * a.y);
+    for (int k = P.nd; k < P.nt; ++k) {
       const uint64_t xm = P.xm[k];
-      const T2 b = xm ? psi[x ^ xm] : a;
+      const T2 b = psi[x ^ xm];
       const R zr = a.x * b.x + a.y * b.y;  // Re conj(a) b
       const R zi = a.x * b.y - a.y * b.x;  // Im conj(a) b
-      const R t = (R)P.cre[k] * zr - (R)P.cim[k] * zi;
+      const R t = coef_re<R>(P, k) * zr - coef_im<R>(P, k) * zi;
       sum += (__popcll((x ^ xm) & P.zm[k]) & 1) ? -t : t;
     }
-    acc += (double)sum;
+    acc.add(sum);
   }
-  acc = block_sum(acc);
-  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+  const double t = block_sum(acc.value());
+  if (threadIdx.x == 0) partials[blockIdx.x] = t;
 }
 
 // out_x (+)= sum_k c'_k s_k(x) psi_{x ^ xm_k}; optional partials of
@@ -79,7 +117,7 @@ __global__ void __launch_bounds__(kRedThreads)
     kapply_pauli(T2* __restrict__ out, const T2* __restrict__ psi, uint64_t dim,
                  const __grid_constant__ PauliDev P, int accumulate,
                  double* __restrict__ partials) {
-  double acc = 0.0;
+  ThreadSum<R> acc;
   for (uint64_t x = (uint64_t)blockIdx.x * kRedThreads + threadIdx.x; x < dim;
        x += (uint64_t)gridDim.x * kRedThreads) {
     R orr = 0, oi = 0;
@@ -88,10 +126,18 @@ __global__ void __launch_bounds__(kRedThreads)
       orr = o.x;
       oi = o.y;
     }
-    for (int k = 0; k < P.nt; ++k) {
+    const T2 a = psi[x];
+    R d = 0;
+    for (int k = 0; k < P.nd; ++k) {
+      const R c = coef_re<R>(P, k);
+      d += (__popcll(x & P.zm[k]) & 1) ? -c : c;
+    }
+    orr += d * a.x;
+    oi += d * a.y;
+    for (int k = P.nd; k < P.nt; ++k) {
       const uint64_t xm = P.xm[k];
       const T2 b = psi[x ^ xm];
-      const R cr = (R)P.cre[k], ci = (R)P.cim[k];
+      const R cr = coef_re<R>(P, k), ci = coef_im<R>(P, k);
       const R sr = cr * b.x - ci * b.y;
       const R si = cr * b.y + ci * b.x;
       if (__popcll((x ^ xm) & P.zm[k]) & 1) {
@@ -106,14 +152,11 @@ __global__ void __launch_bounds__(kRedThreads)
     o.x = orr;
     o.y = oi;
     out[x] = o;
-    if (partials) {
-      const T2 a = psi[x];
-      acc += (double)(a.x * orr + a.y * oi);
-    }
+    if (partials) acc.add(a.x * orr + a.y * oi);
   }
   if (partials) {
-    acc = block_sum(acc);
-    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+    const double t = block_sum(acc.value());
+    if (threadIdx.x == 0) partials[blockIdx.x] = t;
   }
 }
 
@@ -130,18 +173,29 @@ __global__ void __launch_bounds__(kRedThreads)
 
 void pauli_chunks(const sv_pauli_sum* H, std::vector<PauliDev>* out) {
   out->clear();
+  // diagonal terms (no X or Y factor) first, so that every chunk starts with
+  // its diagonal terms; the sum does not depend on the order
+  std::vector<int> order;
+  for (int pass = 0; pass < 2; ++pass)
+    for (int t = 0; t < H->n_terms; ++t)
+      if ((H->xmask[t] == 0) == (pass == 0)) order.push_back(t);
   for (int k0 = 0; k0 < H->n_terms; k0 += 64) {
     PauliDev P{};
     P.nt = H->n_terms - k0 < 64 ? H->n_terms - k0 : 64;
+    P.nd = 0;
     for (int j = 0; j < P.nt; ++j) {
-      const uint64_t xm = H->xmask[k0 + j], zm = H->zmask[k0 + j];
+      const int t = order[k0 + j];
+      const uint64_t xm = H->xmask[t], zm = H->zmask[t];
       const int ny = __builtin_popcountll(xm & zm) & 3;
-      const double c = H->coeff[k0 + j];
+      const double c = H->coeff[t];
       P.xm[j] = xm;
       P.zm[j] = zm;
       // c * i^{ny}
       P.cre[j] = ny == 0 ? c : ny == 2 ? -c : 0.0;
       P.cim[j] = ny == 1 ? c : ny == 3 ? -c : 0.0;
+      P.cre32[j] = (float)P.cre[j];
+      P.cim32[j] = (float)P.cim[j];
+      if (xm == 0 && P.nd == j) ++P.nd;
     }
     out->push_back(P);
   }
@@ -294,6 +348,9 @@ extern "C" sv_status sv_expval_noalloc(const void* dev_state, int n_qubits, sv_d
       P.zm[j] = zm;
       P.cre[j] = ny == 0 ? c : ny == 2 ? -c : 0.0;
       P.cim[j] = ny == 1 ? c : ny == 3 ? -c : 0.0;
+      P.cre32[j] = (float)P.cre[j];
+      P.cim32[j] = (float)P.cim[j];
+      if (xm == 0 && P.nd == j) ++P.nd;  // leading diagonal terms (no reordering here)
     }
     if (dtype == SV_C64)
       kexpval<float, float2><<<g, kRedThreads, 0, st>>>((const float2*)dev_state, dim, P,

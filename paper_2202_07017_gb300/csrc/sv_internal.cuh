@@ -112,10 +112,13 @@ struct PauliDev {
   // terms after host preprocessing: coefficient times i^{#Y}, folded to
   // (cre, cim); the sign (-1)^popcount((x ^ xm) & zm) is applied per index.
   int nt;
+  int nd;  // the first nd terms are diagonal (xm = 0)
   uint64_t xm[64];
   uint64_t zm[64];
   double cre[64];
   double cim[64];
+  float cre32[64];  // the same, rounded once for complex64 states
+  float cim32[64];
 };
 // Fills PauliDev chunks (64 terms each) from a host Pauli sum.
 void pauli_chunks(const sv_pauli_sum* H, std::vector<PauliDev>* out);
