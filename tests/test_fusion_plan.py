@@ -79,3 +79,22 @@ def test_plan_rejects_bad_arguments():
         sv_fusion_plan(c, theta, C64, 1)
     with pytest.raises(SvError):
         sv_fusion_plan(c, None, C64, 4)   # parameters missing
+
+
+@pytest.mark.parametrize("n", [10, 12, 16, 20, 30])
+def test_staged_bits_per_pass(n):
+    """Every pass stages m bits: 13 (complex64) or 12 (complex128) slices,
+    fewer for mid-size states so that at least 2^8 slices remain, and at
+    least min(n, 10); the lowest L bits (5 for complex64, 4 for complex128,
+    fewer when the slice is small) are always staged."""
+    c, theta = W.random_layered(n, 3, 17)
+    for dt, mmax, lmax in ((C64, 13, 5), (C128, 12, 4)):
+        m = min(n, mmax)
+        if n > 10:
+            m = max(min(m, n - 8), min(n, 10))
+        _, _, npass, masks = sv_fusion_plan(c, theta, dt, 4)
+        assert npass == len(masks) > 0
+        low = (1 << min(lmax, m - 4)) - 1 if m - lmax < 4 else (1 << lmax) - 1
+        for mk in masks:
+            assert bin(mk).count("1") == m, (n, dt, bin(mk))
+            assert mk & low == low
