@@ -1,6 +1,7 @@
 """The batch planner on the host (no GPU): validation of the batch kernel's
 limits and the register-group schedule for every group width, including
 gates as wide as the group (the case that must not stall the schedule)."""
+import numpy as np
 import pytest
 
 import workloads as W
@@ -36,3 +37,20 @@ def test_batch_limits_rejected_on_host():
     mixed = W.mixed_batch(64, 5)
     out = sv_batch_plan([m[0] for m in mixed], [m[2] for m in mixed], 4)
     assert (out > 0).all()
+
+
+def test_mixed_batch_recipe():
+    """The C3 mixed batch: 1024 HEA circuits with n uniform in 8..16 and L in
+    5..15 (every value drawn), each with its own open-chain TFIM and n*L
+    parameters."""
+    items = W.mixed_batch(1024, 1003)
+    ns = [c.n_qubits for c, _, _ in items]
+    Ls = [len(th) // c.n_qubits for c, th, _ in items]
+    assert len(items) == 1024
+    assert set(ns) == set(range(8, 17)) and set(Ls) == set(range(5, 16))
+    for (c, th, H), L in zip(items, Ls):
+        assert c.n_params == len(th) == c.n_qubits * L
+        assert len(H) == 2 * c.n_qubits - 1
+    # roughly uniform: every qubit count within 40 % of 1024 / 9
+    counts = np.bincount(ns, minlength=17)[8:]
+    assert counts.min() > 0.6 * 1024 / 9 and counts.max() < 1.4 * 1024 / 9
