@@ -35,7 +35,7 @@ def test_pauli_rotations(dtype, n):
         got = st.numpy()
     finally:
         st.close()
-    assert max_err(got, ref) <= 4 * TOL[dtype]
+    assert max_err(got, ref) <= TOL[dtype]
 
 
 @pytest.mark.parametrize("dtype", ["c64", "c128"])
@@ -51,7 +51,7 @@ def test_trotter_tfim_and_random(dtype, order):
         finally:
             st.close()
         ref = oracle.trotter(psi, H, 0.8, 6, order)
-        assert max_err(got, ref) <= 8 * TOL[dtype]
+        assert max_err(got, ref) <= TOL[dtype]
 
 
 def test_trotter_commuting_zz_n28_closed_form():
