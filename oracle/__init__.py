@@ -54,7 +54,7 @@ def lib():
         L = ctypes.CDLL(_LIB_PATH)
         P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
         L.orc_apply.argtypes = [I, P, I, P, I, P, P]
-        L.orc_run.argtypes = [I, P, I, P, P, P, P, P, P, P, P, P, P, I, D]
+        L.orc_run.argtypes = [I, P, I, P, P, P, P, P, P, P, P, P, P, P, I, D]
         L.orc_expval.argtypes = [I, P, I, P, P, P, P, P, P, P]
         L.orc_probabilities.argtypes = [I, P, I, P, P]
         L.orc_sample.argtypes = [I, P, I, P, I, P, P]
@@ -106,6 +106,7 @@ class _Packed:
         self.param = np.full(ng, -1, np.int32)
         self.angle = np.zeros(ng, np.float64)
         self.mat_off = np.zeros(ng, np.int64)
+        self.letters = np.zeros(5 * max(ng, 1), np.uint8)
         pool: List[np.ndarray] = []
         off = 0
         for g, gate in enumerate(c.gates):
@@ -116,6 +117,8 @@ class _Packed:
             self.ctl[40 * g:40 * g + len(gate.controls)] = gate.controls
             self.param[g] = gate.param
             self.angle[g] = gate.angle
+            for j, L in enumerate(gate.paulis):
+                self.letters[5 * g + j] = ord(L)
             if gate.kind == "MATRIX":
                 m = np.ascontiguousarray(gate.matrix, dtype=np.complex128).ravel()
                 self.mat_off[g] = off
@@ -142,7 +145,7 @@ def run(c: Circuit, theta: Optional[Sequence[float]] = None,
     p = _Packed(c)
     rc = lib().orc_run(n, _ptr(psi), p.ng, _ptr(p.kind), _ptr(p.ntar), _ptr(p.tar),
                        _ptr(p.nctl), _ptr(p.ctl), _ptr(p.param), _ptr(p.angle),
-                       _ptr(p.mat_off), _ptr(p.pool), _ptr(th), int(shift_gate),
+                       _ptr(p.mat_off), _ptr(p.pool), _ptr(p.letters), _ptr(th), int(shift_gate),
                        float(shift))
     if rc:
         raise ValueError(f"oracle rejected the circuit (code {rc})")
@@ -288,8 +291,8 @@ def grad_param_shift(c: Circuit, theta, terms, params: Optional[Sequence[int]] =
     """Exact gradient by shift rules, summed over every gate that uses a
     parameter.  If `params` is given, only those entries are filled.
 
-    Uncontrolled RX/RY/RZ = exp(-i a P / 2): E(a) = A + B cos a + C sin a,
-    so dE/da = (E(a + pi/2) - E(a - pi/2)) / 2.
+    Uncontrolled RX/RY/RZ and PAULI strings = exp(-i a P / 2) with P^2 = I:
+    E(a) = A + B cos a + C sin a, so dE/da = (E(a + pi/2) - E(a - pi/2)) / 2.
     Controlled rotations = exp(-i a (Pc x P) / 2), Pc the all-ones projector
     of the controls: the generator's eigenvalues are 0 and +-1/2, so E(a)
     has frequencies 1/2 and 1.  For a component of frequency w,
@@ -304,8 +307,8 @@ def grad_param_shift(c: Circuit, theta, terms, params: Optional[Sequence[int]] =
     dm = (math.sqrt(2) - 1) / (4 * math.sqrt(2))
     for idx, gate in enumerate(c.gates):
         if gate.param >= 0 and gate.param in want:
-            if gate.kind not in ("RX", "RY", "RZ"):
-                raise ValueError("shift rules need RX, RY or RZ gates")
+            if gate.kind not in ("RX", "RY", "RZ", "PAULI"):
+                raise ValueError("shift rules need RX, RY, RZ or PAULI gates")
 
             def E(s):
                 return energy(c, theta, terms, psi0, idx, s)

@@ -39,7 +39,7 @@
 
 typedef double complex cplx;
 
-enum { K_H = 0, K_X, K_Y, K_Z, K_RX, K_RY, K_RZ, K_U1, K_SWAP, K_MATRIX };
+enum { K_H = 0, K_X, K_Y, K_Z, K_RX, K_RY, K_RZ, K_U1, K_SWAP, K_MATRIX, K_PAULI };
 
 static int g_threads = 1;
 static int g_mutant = 0;
@@ -137,18 +137,32 @@ int orc_apply(int n, cplx* psi, int k, const int* targets, int nc,
   return 0;
 }
 
+int orc_pauli_rotation(int n, cplx* psi, int nops, const int* qubits, const char* letters,
+                       double a);
+
 /* A circuit applied gate by gate.  Gate g has kind[g], ntar[g] targets in
  * tar[5g..], nctl[g] controls in ctl[40g..], and either a parameter index
  * param[g] >= 0 (angle theta[param[g]]) or a fixed angle angle[g].  MATRIX
- * gates read 4^ntar entries of pool from mat_off[g].  If shift_gate >= 0,
- * that gate's angle is increased by `shift` (parameter-shift evaluations). */
+ * gates read 4^ntar entries of pool from mat_off[g].  PAULI gates are
+ * exp(-i a P / 2) for the string with letter letters[5g + j] ('X', 'Y',
+ * 'Z') on target j, applied by orc_pauli_rotation with angle a / 2; they
+ * take no controls.  If shift_gate >= 0, that gate's angle is increased by
+ * `shift` (parameter-shift evaluations). */
 int orc_run(int n, cplx* psi, int ng, const int* kind, const int* ntar,
             const int* tar, const int* nctl, const int* ctl, const int* param,
             const double* angle, const int64_t* mat_off, const cplx* pool,
-            const double* theta, int shift_gate, double shift) {
+            const char* letters, const double* theta, int shift_gate, double shift) {
   cplx G[1024];
   for (int g = 0; g < ng; ++g) {
     const cplx* M = G;
+    if (kind[g] == K_PAULI) {
+      double a = param[g] >= 0 ? theta[param[g]] : angle[g];
+      if (g == shift_gate) a += shift;
+      if (nctl[g] != 0 || ntar[g] < 1 || ntar[g] > 5) return 1;
+      int rc = orc_pauli_rotation(n, psi, ntar[g], tar + 5 * g, letters + 5 * g, 0.5 * a);
+      if (rc) return rc;
+      continue;
+    }
     if (kind[g] == K_MATRIX) {
       M = pool + mat_off[g];
     } else {

@@ -454,3 +454,76 @@ def test_many_controls_against_bruteforce():
     g = W.Gate("Z", (6,), tuple(range(6)))
     ref = full_operator(n, g.targets, g.controls, PAULI["Z"]) @ psi
     assert np.max(np.abs(oracle.run(W.Circuit(n, [g], 0), None, psi) - ref)) < 1e-15
+
+
+# ---- PAULI gates and QAOA (Sec. 3: QAOA, MaxCut) -----------------------------
+def _pauli_string_matrix(letters) -> np.ndarray:
+    P = np.ones((1, 1), np.complex128)
+    for L in letters:
+        P = np.kron(P, PAULI[L])
+    return P
+
+
+@pytest.mark.parametrize("n,seed", [(2, 21), (4, 22), (6, 23), (8, 24)])
+def test_pauli_gate_against_expm_of_the_string(n, seed):
+    """PAULI(a) on targets t_0.. with letters L_0..: expm(-i a/2 P) of the
+    Kronecker product of the letters (t_0 most significant), placed by the
+    brute-force operator builder."""
+    circ, theta = W.random_gates(n, 30, seed, max_tar=min(5, n), kinds=("PAULI", "H", "RY"))
+    assert any(g.kind == "PAULI" and len(g.targets) > 1 for g in circ.gates)
+    psi = W.random_state(n, 200 + seed)
+    for g in circ.gates:
+        if g.kind == "PAULI":
+            a = theta[g.param]
+            G = scipy.linalg.expm(-0.5j * a * _pauli_string_matrix(g.paulis))
+        else:
+            G = textbook_matrix(g, theta)
+        ref = full_operator(n, g.targets, g.controls, G) @ psi
+        got = oracle.run(_single(circ, g), theta, psi)
+        assert np.max(np.abs(got - ref)) < 1e-13, g
+        psi = got
+
+
+def test_pauli_gate_shift_rule_matches_central_difference():
+    n = 6
+    circ, theta = W.random_gates(n, 24, 31, max_tar=4, kinds=("PAULI", "RX", "H"))
+    terms = W.random_pauli_sum(n, 6, 32)
+    ps = [i for i, g in enumerate(circ.gates) if g.kind == "PAULI"]
+    params = sorted({circ.gates[i].param for i in ps})[:5]
+    g_ps = oracle.grad_param_shift(circ, theta, terms, params=params)
+    g_fd = oracle.grad_fd(circ, theta, terms, h=1e-4, params=params)
+    assert np.max(np.abs(g_ps[params] - g_fd[params])) < 1e-7
+
+
+def _qaoa_p1_edge(gamma, beta, du, dv, lam):
+    """<C_uv> after one QAOA layer, C_uv = (1 - Z_u Z_v) / 2, for vertices of
+    degrees du, dv with lam common neighbours (Wang, Hadfield, Jiang, Rieffel,
+    Phys. Rev. A 97, 022304 (2018), Theorem 1)."""
+    s4b, s2b = math.sin(4 * beta), math.sin(2 * beta)
+    cg = math.cos(gamma)
+    return (0.5 + 0.25 * s4b * math.sin(gamma) * (cg ** (du - 1) + cg ** (dv - 1))
+            - 0.25 * s2b ** 2 * cg ** (du + dv - 2 - 2 * lam) * (1 - math.cos(2 * gamma) ** lam))
+
+
+@pytest.mark.parametrize("graph", ["ring7", "reg3_n8", "reg3_n10", "reg4_n9"])
+def test_qaoa_p1_energy_closed_form(graph):
+    """One QAOA layer on MaxCut: the oracle's <C> equals the published closed
+    form, summed over edges (degrees and common neighbours per edge), for
+    graphs with and without triangles.  The circuit's angles are
+    (-gamma, 2 beta) for Farhi et al.'s exp(-i gamma C), exp(-i beta B)."""
+    if graph == "ring7":
+        n, edges = 7, W.ring_graph(7)
+    else:
+        d, n = (int(graph[3]), int(graph.split("_n")[1]))
+        edges = W.random_regular_graph(n, d, 40 + n)
+    adj = {v: set() for v in range(n)}
+    for i, j in edges:
+        adj[i].add(j)
+        adj[j].add(i)
+    c, _ = W.qaoa(n, edges, 1, 1)
+    for gamma, beta in ((0.37, 0.91), (1.3, -0.25), (2.9, 2.2)):
+        psi = oracle.run(c, np.array([-gamma, 2 * beta]))
+        F = oracle.expval(psi, W.maxcut(edges))
+        ref = sum(_qaoa_p1_edge(gamma, beta, len(adj[i]), len(adj[j]), len(adj[i] & adj[j]))
+                  for i, j in edges)
+        assert abs(F - ref) < 1e-12, (graph, gamma, beta, F, ref)

@@ -31,8 +31,11 @@ MASK64 = (1 << 64) - 1
 
 # Gate kinds.  Controlled forms are the same kinds with controls:
 # CZ = Z + 1 control, CNOT = X + 1 control, CU1(l) = U1(l) + 1 control.
-KINDS = ("H", "X", "Y", "Z", "RX", "RY", "RZ", "U1", "SWAP", "MATRIX")
-PARAM_KINDS = ("RX", "RY", "RZ")
+# PAULI(a) = exp(-i a P / 2) for the Pauli string P whose letters (one per
+# target, in `paulis`) act on the targets; no controls.
+BASE_KINDS = ("H", "X", "Y", "Z", "RX", "RY", "RZ", "U1", "SWAP", "MATRIX")
+KINDS = BASE_KINDS + ("PAULI",)
+PARAM_KINDS = ("RX", "RY", "RZ", "PAULI")
 MAX_TARGETS = 5
 MAX_CONTROLS = 8
 
@@ -94,9 +97,13 @@ class Gate:
     param: int = -1          # index into theta, -1 for a fixed angle
     angle: float = 0.0       # used when param == -1 (U1, or fixed rotations)
     matrix: Optional[np.ndarray] = field(default=None, compare=False)  # MATRIX only
+    paulis: str = ""         # PAULI only: one letter X, Y or Z per target
 
     def __post_init__(self):
         assert self.kind in KINDS, self.kind
+        if self.kind == "PAULI":
+            assert len(self.paulis) == len(self.targets) and set(self.paulis) <= set("XYZ")
+            assert not self.controls
 
 
 @dataclass
@@ -114,7 +121,8 @@ class Circuit:
         for g in reversed(self.gates):
             if g.kind in PARAM_KINDS or g.kind == "U1":
                 a = theta[g.param] if g.param >= 0 else g.angle
-                inv.append(Gate(g.kind, g.targets, g.controls, -1, -float(a)))
+                inv.append(Gate(g.kind, g.targets, g.controls, -1, -float(a),
+                                paulis=g.paulis))
             elif g.kind == "MATRIX":
                 inv.append(Gate("MATRIX", g.targets, g.controls,
                                 matrix=np.conj(g.matrix.T).copy()))
@@ -261,7 +269,7 @@ def random_unitary(k: int, rng: SplitMix64) -> np.ndarray:
 
 
 def random_gates(n: int, n_gates: int, seed: int, max_tar: int = 5,
-                 max_ctrl: int = 3, kinds: Sequence[str] = KINDS) -> Tuple[Circuit, np.ndarray]:
+                 max_ctrl: int = 3, kinds: Sequence[str] = BASE_KINDS) -> Tuple[Circuit, np.ndarray]:
     """Random gate list over every kind: random distinct targets and
     controls, rotation angles as parameters, MATRIX gates with seeded
     unitaries on 1..max_tar targets."""
@@ -272,19 +280,23 @@ def random_gates(n: int, n_gates: int, seed: int, max_tar: int = 5,
         kind = kinds[rng.next() % len(kinds)]
         if kind == "SWAP":
             k = 2
-        elif kind == "MATRIX":
+        elif kind in ("MATRIX", "PAULI"):
             k = 1 + rng.next() % min(max_tar, n)
         else:
             k = 1
         if kind == "SWAP" and n < 2:
             kind, k = "H", 1
-        nc = rng.next() % (min(max_ctrl, n - k) + 1)
+        nc = rng.next() % (min(max_ctrl, n - k) + 1) if kind != "PAULI" else 0
         perm = list(range(n))
         for i in range(n - 1, 0, -1):          # Fisher-Yates
             j = rng.next() % (i + 1)
             perm[i], perm[j] = perm[j], perm[i]
         tg, ct = tuple(perm[:k]), tuple(perm[k:k + nc])
-        if kind in PARAM_KINDS:
+        if kind == "PAULI":
+            letters = "".join("XYZ"[rng.next() % 3] for _ in range(k))
+            theta.append(rng.angle())
+            gates.append(Gate(kind, tg, (), len(theta) - 1, paulis=letters))
+        elif kind in PARAM_KINDS:
             theta.append(rng.angle())
             gates.append(Gate(kind, tg, ct, len(theta) - 1))
         elif kind == "U1":
@@ -309,3 +321,63 @@ def mixed_batch(count: int, seed: int, n_lo: int = 8, n_hi: int = 16,
         c, th = hea(n, L, seed + 1 + i)
         items.append((c, th, tfim(n)))
     return items
+
+
+# --------------------------------------------------------------------------
+# QAOA for MaxCut (Sec. 3: pre-coded MaxCut Hamiltonian and QAOA models;
+# QAOA as defined by Farhi, Goldstone, Gutmann, arXiv:1411.4028)
+# --------------------------------------------------------------------------
+def ring_graph(n: int) -> List[Tuple[int, int]]:
+    """Edges (i, i+1 mod n) of the n-cycle."""
+    return [(i, (i + 1) % n) for i in range(n)]
+
+
+def random_regular_graph(n: int, d: int, seed: int) -> List[Tuple[int, int]]:
+    """A seeded simple d-regular graph on n vertices (n d even): pair the
+    n d half-edges by a Fisher-Yates shuffle and retry until no loop or
+    repeated edge remains.  Edges as (i, j) with i < j, sorted."""
+    assert (n * d) % 2 == 0 and d < n
+    rng = SplitMix64(seed)
+    while True:
+        stubs = [v for v in range(n) for _ in range(d)]
+        for i in range(len(stubs) - 1, 0, -1):
+            j = rng.next() % (i + 1)
+            stubs[i], stubs[j] = stubs[j], stubs[i]
+        edges = set()
+        ok = True
+        for a, b in zip(stubs[0::2], stubs[1::2]):
+            e = (min(a, b), max(a, b))
+            if a == b or e in edges:
+                ok = False
+                break
+            edges.add(e)
+        if ok:
+            return sorted(edges)
+
+
+def maxcut(edges: Sequence[Tuple[int, int]]) -> List[PauliTerm]:
+    """The MaxCut cost C = sum over edges (i, j) of (1 - Z_i Z_j) / 2 as a
+    Pauli sum: the identity with coefficient |E| / 2 (empty string) and
+    -1/2 Z_i Z_j per edge."""
+    terms: List[PauliTerm] = [(0.5 * len(edges), ())]
+    terms += [(-0.5, ((i, "Z"), (j, "Z"))) for i, j in edges]
+    return terms
+
+
+def qaoa(n: int, edges: Sequence[Tuple[int, int]], p: int, seed: int) -> Tuple[Circuit, np.ndarray]:
+    """QAOA circuit with p layers on the MaxCut graph `edges`: H on every
+    qubit (|+>^n), then per layer l the cost rotations PAULI "ZZ" on every
+    edge with parameter 2l and the mixer rotations PAULI "X" on every qubit
+    with parameter 2l + 1.  A gate PAULI(a) is exp(-i a P / 2), so Farhi et
+    al.'s U(C, gamma) = exp(-i gamma C) is (up to a global phase) the cost
+    rotations at a = -gamma and U(B, beta) = exp(-i beta sum_j X_j) the
+    mixer at a = 2 beta.  Angles uniform in [0, 2pi) from the seed."""
+    rng = SplitMix64(seed)
+    gates: List[Gate] = [Gate("H", (q,)) for q in range(n)]
+    for layer in range(p):
+        for i, j in edges:
+            gates.append(Gate("PAULI", (i, j), (), 2 * layer, paulis="ZZ"))
+        for q in range(n):
+            gates.append(Gate("PAULI", (q,), (), 2 * layer + 1, paulis="X"))
+    theta = np.array([rng.angle() for _ in range(2 * p)])
+    return Circuit(n, gates, 2 * p, f"qaoa_n{n}_p{p}"), theta
