@@ -67,11 +67,18 @@ typedef enum {
  *   RX(a) = [[c,-is],[-is,c]], RY(a) = [[c,-s],[s,c]],
  *   RZ(a) = diag(e^{-ia/2}, e^{ia/2}), U1(a) = diag(1, e^{ia}),
  *   SWAP exchanges |01> and |10> of its two targets,
- *   MATRIX reads 4^n_tar complex128 entries from the circuit's pool. */
+ *   MATRIX reads 4^n_tar complex128 entries from the circuit's pool,
+ *   PAULI(a) = exp(-i a P / 2) = c I - i s P for the Pauli string
+ *     P = sigma_{L_0} (x) ... (x) sigma_{L_{k-1}} on targets t_0..t_{k-1}
+ *     (letter L_j in bits 2j..2j+1 of `paulis`: 1 X, 2 Y, 3 Z), 1..5
+ *     targets and no controls: the rotations exp(-i gamma Z_i Z_j / 2) and
+ *     exp(-i beta X_j / 2) of QAOA (Sec. 3: QAOA, MaxCut) and the
+ *     exponentials of Pauli terms of Trotter products.  Differentiable:
+ *     dE/da = Im<lambda|P|psi> as for RX, RY, RZ. */
 enum {
   SV_GATE_H = 0, SV_GATE_X = 1, SV_GATE_Y = 2, SV_GATE_Z = 3,
   SV_GATE_RX = 4, SV_GATE_RY = 5, SV_GATE_RZ = 6, SV_GATE_U1 = 7,
-  SV_GATE_SWAP = 8, SV_GATE_MATRIX = 9
+  SV_GATE_SWAP = 8, SV_GATE_MATRIX = 9, SV_GATE_PAULI = 10
 };
 
 #define SV_MAX_QUBITS 34
@@ -92,6 +99,8 @@ typedef struct {
   int32_t controls[SV_MAX_CONTROLS];   /* qubit numbers */
   double angle;                        /* angle when param == -1 */
   int64_t mat_off;                     /* MATRIX: offset (in complex entries) into mat_pool */
+  int32_t paulis;                      /* PAULI: letter of targets[j] in bits 2j..2j+1 */
+  int32_t reserved;                    /* 0 */
 } sv_gate;
 
 typedef struct {
@@ -133,6 +142,25 @@ sv_status sv_free(sv_state s);
 /* Rebind the handle to another stream (e.g. a stream being captured into a
  * CUDA graph).  Later calls launch there. */
 sv_status sv_set_stream(sv_state s, void* cuda_stream);
+
+/* Rounding of complex64 gate arithmetic (Sec. 2, Eq. 1 evaluated in fp32).
+ * Every mode rounds inexact matrices to fp32 with error feedback: the state
+ * keeps the squared-norm factor that its rounded matrices have applied and
+ * scales the next one against it, so the fp32 rounding of 1/sqrt2 in H
+ * (2 h^2 = 1 - 3.4e-8) does not accumulate over many gates.
+ *   SV_ROUNDING_DEFAULT: the one-kernel-per-gate 1-qubit kernels round each
+ *     output with dither (a pseudo-random term below one fp32 step added
+ *     before the final rounding, keyed by amplitude and launch), so equal
+ *     amplitudes do not repeat one rounding error gate after gate; the
+ *     fused qubit-block passes round to nearest.
+ *   SV_ROUNDING_DITHERED: the fused passes' dense 2x2 products dither too
+ *     (about twice their arithmetic); for circuits whose states keep many
+ *     equal amplitudes, such as Grover's search, whose norm otherwise drifts
+ *     linearly with the iteration count.
+ * Results are reproducible: the dither restarts with sv_init / sv_upload.
+ * complex128 states ignore the mode.  SV_ERR_INVALID for another value. */
+typedef enum { SV_ROUNDING_DEFAULT = 0, SV_ROUNDING_DITHERED = 1 } sv_rounding;
+sv_status sv_set_rounding(sv_state s, int mode);
 
 /* Device pointer, qubit count and dtype of the state. */
 sv_status sv_info(sv_state s, void** dev_ptr, int* n_qubits, sv_dtype* dtype);
@@ -221,16 +249,17 @@ sv_status sv_expval(sv_state s, const sv_pauli_sum* H, double* out);
 sv_status sv_expval_async(sv_state s, const sv_pauli_sum* H, double* dev_out);
 
 /* <psi|H|psi> like sv_expval_async, for callers that cannot allocate device
- * memory at the time of the call: code recording into a CUDA graph (stream
- * capture forbids cudaMalloc), a process whose device memory is all handed
- * to a caching allocator or a fixed arena, or code that has no way to
- * recover from a failed allocation.  The paper has no counterpart; this
+ * memory at the time of the call: a process whose device memory is all
+ * handed to a caching allocator or a fixed arena, or code that has no way
+ * to recover from a failed allocation.  The paper has no counterpart; this
  * is a deployment variant of sv_expval_async.
  *
  * It allocates nothing and needs no handle: dev_state is the caller's
  * device state (2^n_qubits amplitudes of `dtype`, 16-byte aligned),
  * dev_out the caller's device double that receives the result, and the
- * kernels run on `cuda_stream` without synchronising.  The reduction's
+ * kernels run on `cuda_stream` (NULL: the legacy default stream; otherwise a
+ * stream of the current device, else SV_ERR_INVALID) without
+ * synchronising.  The reduction's
  * block partials live in one fixed array of SV_NOALLOC_MAX_TERMS / 64 *
  * 1216 doubles (152 KiB) compiled into the library, which every GPU that
  * loads the library keeps until the process exits.
@@ -294,7 +323,8 @@ sv_status sv_sample(sv_state s, const int* qubits, int n_meas, int64_t n_shots,
  * method).  On entry `s` holds psi_N as left by sv_apply_circuit(s, c,
  * theta, *) on psi_0; it is not modified.  The reverse sweep keeps two work
  * states (lambda = H psi and the un-applied psi) owned by the handle.
- * Parameterised gates must be RX/RY/RZ; energy (host) and grad (host,
+ * Parameterised gates must be RX/RY/RZ (with or without controls) or PAULI
+ * (without controls); energy (host) and grad (host,
  * c->n_params doubles, gradients of gates sharing a parameter are summed)
  * are written and the stream is synchronised.  Gradients accumulate in
  * fp64. */

@@ -19,7 +19,7 @@ from .sv import (C64, C128, EXPORTS, PackedBatch, sv_batch_create, sv_batch_free
                  sv_apply_pauli_sum, sv_copy, sv_download, sv_expval, sv_expval_async, sv_free,
                  sv_fusion_plan, sv_fusion_plan_reverse, sv_pauli_rotation, sv_probabilities, sv_sample, sv_trotter,
                  sv_grad, sv_grad_fused, sv_info, sv_init, sv_last_error, sv_launch_count, sv_norm, sv_profile_start,
-                 sv_profile_stop, sv_set_stream,
+                 sv_profile_stop, sv_set_stream, sv_set_rounding,
                  sv_sync, sv_upload, sv_version, sv_wrap, sv_host_alloc, sv_host_free,
                  sv_selftest_wait, sv_check_guards)
 
@@ -69,6 +69,11 @@ class State:
     def set_stream(self, stream):
         self.stream = stream
         sv_set_stream(self.h, stream.cuda_stream)
+
+    def set_rounding(self, mode):
+        """Complex64 rounding: "default" or "dithered" (see sv_set_rounding)."""
+        sv_set_rounding(self.h, mode)
+        return self
 
     def init(self, basis_index: int = 0):
         sv_init(self.h, basis_index)
@@ -174,26 +179,36 @@ def _energy_fn():
     class Energy(torch.autograd.Function):
         """E(theta) = <psi(theta)|H|psi(theta)>, psi(theta) = U(theta)|basis>.
 
-        forward: sv_init + sv_apply_circuit + sv_expval on `state`;
-        backward: sv_adjoint on the forward state (the state must not be
-        changed between the two), times the incoming gradient."""
+        forward: when theta requires a gradient, sv_grad (fuse_k = 0) or
+        sv_grad_fused runs the circuit from |basis> and the adjoint sweep at
+        once (checkpoints: gate indices whose forward states the sweep
+        restores) and keeps dE/dtheta for backward; otherwise sv_init +
+        sv_apply_circuit + sv_expval.  backward: the kept gradient times the
+        incoming one.  The gate matrices are built on the host from theta in
+        fp64, so theta is copied to the host once per forward."""
 
         @staticmethod
-        def forward(ctx, theta, state, circuit, terms, basis=0):
+        def forward(ctx, theta, state, circuit, terms, basis=0, fuse_k=0, checkpoints=()):
             th = theta.detach().to("cpu", torch.float64).numpy().copy()
             pc = pack_circuit(circuit)
             pp = pack_pauli(terms, state.n)
             state.init(basis)
-            sv_apply_circuit(state.h, pc, th, 0)
-            e = sv_expval(state.h, pp)
-            ctx.state, ctx.pc, ctx.pp, ctx.th = state, pc, pp, th
+            if ctx.needs_input_grad[0]:
+                if fuse_k:
+                    e, g = sv_grad_fused(state.h, pc, th, pp, list(checkpoints), fuse_k)
+                else:
+                    e, g = sv_grad(state.h, pc, th, pp, list(checkpoints))
+                ctx.grad = torch.from_numpy(np.asarray(g, np.float64)).to(theta.device)
+            else:
+                sv_apply_circuit(state.h, pc, th, fuse_k)
+                e = sv_expval(state.h, pp)
+                ctx.grad = None
             return torch.tensor(e, dtype=torch.float64, device=theta.device)
 
         @staticmethod
         def backward(ctx, grad_out):
-            _, g = sv_adjoint(ctx.state.h, ctx.pc, ctx.th, ctx.pp)
-            gt = torch.from_numpy(g).to(grad_out.device) * grad_out
-            return gt, None, None, None, None
+            gt = None if ctx.grad is None else ctx.grad * grad_out
+            return gt, None, None, None, None, None, None
 
     return Energy
 
@@ -210,6 +225,8 @@ class _Lazy:
 Energy = _Lazy()
 
 
-def energy(theta, state: State, circuit, terms, basis: int = 0):
-    """Differentiable energy (torch scalar) via the adjoint kernels."""
-    return Energy.apply(theta, state, circuit, terms, basis)
+def energy(theta, state: State, circuit, terms, basis: int = 0, fuse_k: int = 0,
+           checkpoints=()):
+    """Differentiable energy (torch scalar) via the adjoint kernels; fuse_k >= 2
+    runs the circuit and the reverse sweep as fused qubit-block passes."""
+    return Energy.apply(theta, state, circuit, terms, basis, fuse_k, tuple(checkpoints))

@@ -72,6 +72,7 @@ struct FusedParams {
   uint8_t tlo[5], thi[5], swpos[12];
   uint32_t box_bytes, slice_bytes;
   uint32_t extra_tx;  // 0; the bounded-wait self-test arms the barrier for more bytes
+  uint32_t dseed;     // complex64 forward passes: seed of the dithered rounding (0: none)
   int ngroups;
   int ngrad;            // reverse sweeps: gradient operations of the pass
   int gslot[kFMaxOps];  // their gradient slots
@@ -337,6 +338,24 @@ __device__ __forceinline__ void dense_bit(const R* c, R (&re)[1 << KG], R (&im)[
   }
 }
 
+// dense_bit with the final rounding of every output dithered (mv2_dither),
+// pair r keyed by mix32(h + r): complex64 only
+template <int KG, int B>
+__device__ __forceinline__ void dense_bit_dither(const float* c, float (&re)[1 << KG],
+                                                 float (&im)[1 << KG], uint32_t h) {
+  M2<float> g;
+  const float4 x = reinterpret_cast<const float4*>(c)[0];
+  const float4 y = reinterpret_cast<const float4*>(c)[1];
+  g.r[0] = x.x; g.i[0] = x.y; g.r[1] = x.z; g.i[1] = x.w;
+  g.r[2] = y.x; g.i[2] = y.y; g.r[3] = y.z; g.i[3] = y.w;
+#pragma unroll
+  for (int r = 0; r < (1 << KG); ++r) {
+    if (r & (1 << B)) continue;
+    const int r1 = r | (1 << B);
+    mv2_dither<MK_DENSE>(g, re[r], im[r], re[r1], im[r1], mix32(h + (uint32_t)r));
+  }
+}
+
 // The group as a layer program (see FLayerDev): no per-gate dispatch, every
 // register index fixed at compile time.
 // slot offset of register r: XOR of the swizzled group-bit offsets sw[i]
@@ -350,9 +369,12 @@ __device__ __forceinline__ int reg_off(int r, const int (&sw)[KG]) {
   return o;
 }
 
-template <int KG, typename R, bool TABLE>
+// DITHER (complex64): every dense 2x2 rounds its outputs with dither (see
+// mv2_dither), keyed by dseed and the sub-block.
+template <int KG, typename R, bool TABLE, bool DITHER = false>
 __device__ __forceinline__ void run_layers(typename Cplx2<R>::T* sm, int m, const uint8_t* gb,
-                                           const FLayerDev* lay, int l0, int l1, const R* coef) {
+                                           const FLayerDev* lay, int l0, int l1, const R* coef,
+                                           uint32_t dseed = 0) {
   typedef typename Cplx2<R>::T V2;
   constexpr int D = 1 << KG;
   int sw[KG];
@@ -386,12 +408,23 @@ __device__ __forceinline__ void run_layers(typename Cplx2<R>::T* sm, int m, cons
       re[r] = v.x;
       im[r] = v.y;
     }
+    uint32_t h = 0;
+    if constexpr (DITHER) h = mix32(dseed + (uint32_t)s * 0x9E3779B1u);
     for (int l = l0; l < l1; ++l) {
       const FLayerDev L = lay[l];
       const R* c = coef + L.off;
 #pragma unroll
       for (int i = 0; i < KG; ++i) {
         if (L.u1 & (1 << i)) {
+          if constexpr (DITHER && sizeof(R) == 4) {
+            h = mix32(h + (uint32_t)(l * KG + i));
+            if (i == 0) dense_bit_dither<KG, 0>(c, re, im, h);
+            if constexpr (KG > 1) if (i == 1) dense_bit_dither<KG, (KG > 1 ? 1 : 0)>(c, re, im, h);
+            if constexpr (KG > 2) if (i == 2) dense_bit_dither<KG, (KG > 2 ? 2 : 0)>(c, re, im, h);
+            if constexpr (KG > 3) if (i == 3) dense_bit_dither<KG, (KG > 3 ? 3 : 0)>(c, re, im, h);
+            c += 8;
+            continue;
+          }
           if (i == 0) dense_bit<KG, 0, R>(c, re, im);
           if constexpr (KG > 1) if (i == 1) dense_bit<KG, (KG > 1 ? 1 : 0), R>(c, re, im);
           if constexpr (KG > 2) if (i == 2) dense_bit<KG, (KG > 2 ? 2 : 0), R>(c, re, im);
@@ -564,7 +597,9 @@ __device__ __forceinline__ void issue_store(const FusedParams<R>& P, uint32_t sr
 // thread waits for the phase (bounded), runs the groups, makes its writes
 // visible to the async proxy, and warp 0 issues the box stores.
 // MODE: 0 every group a gate list, 1 mixed, 3 every group a layer program
-// (shared-memory addresses recomputed per access instead of tabulated)
+// (shared-memory addresses recomputed per access instead of tabulated), 4 as
+// 3 with every dense 2x2 rounded with dither (complex64, dithered rounding
+// selected for the state)
 template <typename R, int KGF, int MINB, int MODE>
 __global__ void __launch_bounds__(kFThreads, MINB)
     kfused_tma(uint64_t n_blocks, const __grid_constant__ FusedParams<R> P) {
@@ -604,7 +639,11 @@ __global__ void __launch_bounds__(kFThreads, MINB)
       break;
     }
     for (int g = 0; g < P.ngroups; ++g) {
-      if (MODE == 3)
+      if (MODE == 4)
+        run_layers<KGF, R, false, true>(
+            sm, P.m, P.gbits[g], P.layers, P.glay[g], P.glay[g + 1], csm,
+            mix32(P.dseed ^ (uint32_t)blk ^ ((uint32_t)(blk >> 32) + (uint32_t)g * 0x85ebca6bu)));
+      else if (MODE == 3)
         run_layers<KGF, R, false>(sm, P.m, P.gbits[g], P.layers, P.glay[g], P.glay[g + 1], csm);
       else if (MODE == 1 && P.gkind[g])
         run_layers<KGF, R, true>(sm, P.m, P.gbits[g], P.layers, P.glay[g], P.glay[g + 1], csm);
@@ -1137,15 +1176,18 @@ bool build_tma(const TmaGeom& g, void* data, FusedParams<R>* P, CUtensorMap* map
   return true;
 }
 
-// Rewrites every group whose gates are uncontrolled 1-qubit gates and
-// diagonal gates (phases on subspaces, controlled diagonal 1-qubit gates) as
-// a layer program: a 1-qubit gate joins the open layer unless the layer's
-// diagonal already touches its bit (then a new layer starts); consecutive
-// 1-qubit gates on one bit multiply; diagonal gates multiply into the
-// layer's diagonal.  All products in fp64.  Other groups keep their gate
-// list.
+// Rewrites group g, if its gates are uncontrolled 1-qubit gates and diagonal
+// gates (phases on subspaces, controlled diagonal 1-qubit gates), as a layer
+// program: a 1-qubit gate joins the open layer unless the layer's diagonal
+// already touches its bit (then a new layer starts); consecutive 1-qubit
+// gates on one bit multiply; diagonal gates multiply into the layer's
+// diagonal.  All products in fp64; the coefficients are rounded with the
+// state's error feedback (drift; the layers' 2x2s and diagonals act on the
+// whole state).  Returns false (and leaves nl, nc) if the group keeps its
+// gate list.
 template <typename R>
-void build_layers(const FusedPass& pass, const int* pos_of, FusedParams<R>* P) {
+bool layer_group(const FusedPass& pass, int g, const int* pos_of, FusedParams<R>* P, int* nlp,
+                 int* ncp, double* drift) {
   struct LayerH {
     int u1 = 0, dtouch = 0;
     cd U[5][4];
@@ -1156,11 +1198,10 @@ void build_layers(const FusedPass& pass, const int* pos_of, FusedParams<R>* P) {
     bool empty() const { return !u1 && !dtouch; }
   };
   auto cmul = [](cd a, cd b) { return cd{a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; };
-  int nl = 0, nc = 0;
+  int& nl = *nlp;
+  int& nc = *ncp;
   const int cap = (int)(sizeof(P->coef) / sizeof(R));
-  for (int g = 0; g < P->ngroups; ++g) {
-    P->gkind[g] = 0;
-    P->glay[g] = (uint16_t)nl;
+  {
     const FusedGroup& grp = pass.groups[g];
     const int k = grp.k, D = 1 << k;
     // convertible: uncontrolled or diagonal 1-qubit gates and phases only
@@ -1171,7 +1212,7 @@ void build_layers(const FusedPass& pass, const int* pos_of, FusedParams<R>* P) {
                          f.m[2].im == 0;
       if (!(f.type == FG_PHASE || (f.type == FG_1Q && (f.cmask == 0 || diag1)))) conv = false;
     }
-    if (!conv) continue;
+    if (!conv) return false;
     int lb[5];
     for (int i = 0; i < k; ++i) lb[i] = pos_of[pass.S[grp.bits[i]]];
     std::sort(lb, lb + k);
@@ -1228,7 +1269,7 @@ void build_layers(const FusedPass& pass, const int* pos_of, FusedParams<R>* P) {
       }
       if (!ok) break;
     }
-    if (!ok) continue;
+    if (!ok) return false;
     if (L.back().empty()) L.pop_back();
     // coefficient count and capacity
     int need = 0;
@@ -1245,42 +1286,47 @@ void build_layers(const FusedPass& pass, const int* pos_of, FusedParams<R>* P) {
       need += dk == 0 ? 0 : dk == 1 ? D : 2 * D;
       need = (need + 3) & ~3;  // 16-byte alignment of the next layer (float)
     }
-    if (nl + (int)L.size() > kFMaxLayers || nc + need > cap) continue;
+    if (nl + (int)L.size() > kFMaxLayers || nc + need > cap) return false;
+    double* fb = sizeof(R) == 4 ? drift : nullptr;
     for (size_t li = 0; li < L.size(); ++li) {
-      const LayerH& h = L[li];
+      LayerH& h = L[li];
       FLayerDev& d = P->layers[nl++];
       d.u1 = (uint8_t)h.u1;
       d.dk = (uint8_t)dks[li];
       d.off = (uint16_t)nc;
       for (int i = 0; i < k; ++i)
-        if ((h.u1 >> i) & 1)
+        if ((h.u1 >> i) & 1) {
+          feedback_round(h.U[i], 2, fb);
           for (int e = 0; e < 4; ++e) {
             P->coef[nc++] = (R)h.U[i][e].re;
             P->coef[nc++] = (R)h.U[i][e].im;
           }
-      if (dks[li] == 1)
+        }
+      if (dks[li] == 1) {  // entries +-1: exact
         for (int r = 0; r < D; ++r) P->coef[nc++] = (R)h.Dg[r].re;
-      else if (dks[li] == 2)
+      } else if (dks[li] == 2) {
+        feedback_round_diag(h.Dg, D, fb);
         for (int r = 0; r < D; ++r) {
           P->coef[nc++] = (R)h.Dg[r].re;
           P->coef[nc++] = (R)h.Dg[r].im;
         }
+      }
       while (nc & 3) P->coef[nc++] = 0;
     }
-    P->gkind[g] = 1;
-    P->glay[g + 1] = (uint16_t)nl;
+    return true;
   }
-  for (int g = 0; g < P->ngroups; ++g)
-    if (!P->gkind[g]) P->glay[g + 1] = P->glay[g];
-  P->glay[P->ngroups] = (uint16_t)nl;
-  P->ncoef = nc;
 }
 
-// order: the staged bits in local order (order[0..L) = 0..L-1)
+// order: the staged bits in local order (order[0..L) = 0..L-1).  forward:
+// a forward pass (groups may become layer programs; complex64 coefficients of
+// operations on the whole state are rounded with the error feedback drift);
+// otherwise a reverse-sweep pass (gate lists, plain rounding).
 template <typename R>
-bool build_params(const FusedPass& pass, const std::vector<int>& order, FusedParams<R>* P) {
+bool build_params(const FusedPass& pass, const std::vector<int>& order, FusedParams<R>* P,
+                  bool forward = true, double* drift = nullptr) {
   P->ngrad = 0;
   P->extra_tx = 0;
+  P->dseed = 0;
   const std::vector<int>& S = pass.S;
   P->m = (int)S.size();
   P->L = pass.L;
@@ -1378,8 +1424,30 @@ bool build_params(const FusedPass& pass, const std::vector<int>& order, FusedPar
     }
   }
   P->gop[P->ngroups] = (uint16_t)nop;
-  if (P->ngrad == 0) {
-    build_layers(pass, pos_of, P);
+  if (forward && P->ngrad == 0) {
+    // groups in application order, so the feedback sees the roundings in the
+    // order they act on the state
+    int nl = 0, nc = 0;
+    double* fb = sizeof(R) == 4 ? drift : nullptr;
+    for (int g = 0; g < P->ngroups; ++g) {
+      P->glay[g] = (uint16_t)nl;
+      P->gkind[g] = layer_group(pass, g, pos_of, P, &nl, &nc, fb) ? 1 : 0;
+      if (P->gkind[g] || !fb) continue;
+      const FusedGroup& grp = pass.groups[g];
+      for (size_t j = 0; j < grp.ops.size(); ++j) {
+        const FGate& f = pass.gates[grp.ops[j]];
+        if (f.type != FG_1Q || f.cmask) continue;
+        cd gm[4] = {f.m[0], f.m[1], f.m[2], f.m[3]};
+        feedback_round(gm, 2, fb);
+        FOpDev<R>& o = P->ops[P->gop[g] + j];
+        for (int e = 0; e < 4; ++e) {
+          o.m[2 * e] = (R)gm[e].re;
+          o.m[2 * e + 1] = (R)gm[e].im;
+        }
+      }
+    }
+    P->glay[P->ngroups] = (uint16_t)nl;
+    P->ncoef = nc;
   } else {  // reverse sweeps run gate lists; coef[] holds gradient generators
     for (int g = 0; g <= P->ngroups; ++g) P->glay[g] = 0;
     for (int g = 0; g < P->ngroups; ++g) P->gkind[g] = 0;
@@ -1397,6 +1465,8 @@ struct PassKernels {
   }
   template <int KG, int MINB>
   static Tma pick(int mode) {
+    if constexpr (sizeof(R) == 4)
+      if (mode == 4) return kfused_tma<R, KG, MINB, 4>;
     return mode == 3   ? kfused_tma<R, KG, MINB, 3>
            : mode == 1 ? kfused_tma<R, KG, MINB, 1>
                        : kfused_tma<R, KG, MINB, 0>;
@@ -1406,13 +1476,14 @@ struct PassKernels {
   // register budget of 2 blocks per SM, gate lists with 3.
   static Tma tma(int kg, int mode) {
     constexpr int MB = sizeof(R) == 4 ? 3 : 2;
-    if (kg == 4) return mode == 3 ? pick<4, 2>(mode) : pick<4, MB>(mode);
+    if (kg == 4) return mode >= 3 ? pick<4, 2>(mode) : pick<4, MB>(mode);
     return kg <= 1 ? pick<1, MB>(mode) : kg == 2 ? pick<2, MB>(mode) : pick<3, MB>(mode);
   }
 };
 
 template <typename R>
-sv_status run_pass(void* data, int n, cudaStream_t st, const FusedPass& pass) {
+sv_status run_pass(void* data, int n, cudaStream_t st, const FusedPass& pass, RoundCtx* rc) {
+  double* drift = rc ? &rc->drift : nullptr;
   static FusedParams<R> P;  // ~8-15 KB: kept off the stack; launches are serialised per call
   static std::mutex mu;
   std::lock_guard<std::mutex> lk(mu);
@@ -1426,7 +1497,8 @@ sv_status run_pass(void* data, int n, cudaStream_t st, const FusedPass& pass) {
   TmaGeom geo;
   bool tma = tma_geometry(pass.S, pass.L, n, lw, &geo);
   std::vector<int> order = tma ? geo.order : pass.S;
-  if (!build_params(pass, order, &P)) {
+  const double drift0 = drift ? *drift : 0.0;
+  if (!build_params(pass, order, &P, true, drift)) {
     set_error("fused pass exceeds kernel capacity");
     return SV_ERR_INVALID;
   }
@@ -1436,10 +1508,13 @@ sv_status run_pass(void* data, int n, cudaStream_t st, const FusedPass& pass) {
     return SV_ERR_INVALID;
   }
   if (tma) tma = build_tma(geo, data, &P);
-  if (!tma && order != pass.S && !build_params(pass, pass.S, &P)) {
+  if (!tma && order != pass.S && drift) *drift = drift0;  // rebuilt below
+  if (!tma && order != pass.S && !build_params(pass, pass.S, &P, true, drift)) {
     set_error("fused pass exceeds kernel capacity");
     return SV_ERR_INVALID;
   }
+  const bool dither_all = sizeof(R) == 4 && rc && rc->mode == SV_ROUNDING_DITHERED;
+  if (dither_all) P.dseed = rc->next_seed();
   const uint64_t nblk = uint64_t(1) << (n - P.m);
   const size_t amp = sizeof(R) * 2;
   ProfScope prof(st, sizeof(R) == 4 ? (tma ? "kfused_tma_c64" : "kfused_c64")
@@ -1447,7 +1522,7 @@ sv_status run_pass(void* data, int n, cudaStream_t st, const FusedPass& pass) {
   if (tma) {
     int nlay = 0;
     for (int g = 0; g < P.ngroups; ++g) nlay += P.gkind[g];
-    const int mode = nlay == 0 ? 0 : nlay == P.ngroups ? 3 : 1;
+    const int mode = nlay == 0 ? 0 : nlay == P.ngroups ? (dither_all ? 4 : 3) : 1;
     typename PassKernels<R>::Tma kern = PassKernels<R>::tma(kg, mode);
     const size_t smem = (amp << P.m) + 1024 + sizeof(R) * (size_t)P.ncoef;
     // resident blocks per SM for this kernel and shared-memory size
@@ -1503,7 +1578,7 @@ sv_status run_adj_pass(void* psi, void* lam, int n, cudaStream_t st, const Fused
     }
   const int lw = sizeof(R) == 4 ? 0 : 1;
   TmaGeom geo;
-  if (!tma_geometry(pass.S, pass.L, n, lw, &geo) || !build_params(pass, geo.order, &P) ||
+  if (!tma_geometry(pass.S, pass.L, n, lw, &geo) || !build_params(pass, geo.order, &P, false) ||
       !verify_tma(geo, pass.S, n, lw, 0) ||
       !verify_tma(geo, pass.S, n, lw, (uint64_t(1) << (n - (int)pass.S.size())) - 1) ||
       !build_tma(geo, psi, &P) || !build_tma(geo, lam, &P, &P.tmap2)) {
@@ -1565,8 +1640,9 @@ sv_status launch_fused_reverse_pass(void* psi, void* lam, sv_dtype dt, int n, cu
 }
 
 sv_status launch_fused_pass(void* data, sv_dtype dt, int n, cudaStream_t st,
-                            const FusedPass& pass) {
-  return dt == SV_C64 ? run_pass<float>(data, n, st, pass) : run_pass<double>(data, n, st, pass);
+                            const FusedPass& pass, RoundCtx* rc) {
+  return dt == SV_C64 ? run_pass<float>(data, n, st, pass, rc)
+                      : run_pass<double>(data, n, st, pass, nullptr);
 }
 
 // Bounded-wait self-test: one pass over the state with no gates whose

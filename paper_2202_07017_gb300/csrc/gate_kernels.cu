@@ -52,10 +52,17 @@ __device__ __forceinline__ void rot(R c, R s, R& re, R& im) {
 }
 
 // ---- complex64 1-qubit, target bit >= 1: two coalesced streams --------------------
-template <typename I, int MK, int ITEMS>
+// DITHER: the outputs' final roundings are dithered (mv2_dither), keyed by
+// the vector index and the launch's seed.
+template <typename I>
+__device__ __forceinline__ uint32_t unit_key(I v, uint32_t seed) {
+  return mix32((uint32_t)v * 0x9E3779B1u ^ (uint32_t)((uint64_t)v >> 32) ^ seed);
+}
+
+template <typename I, int MK, int ITEMS, bool DITHER>
 __global__ void __launch_bounds__(kThreads)
     k1q_c64_pair(float4* __restrict__ psi, I n_units, Ins<I> ins, I tmask, I cmask,
-                 int amp1_only, M2<float> g) {
+                 int amp1_only, M2<float> g, uint32_t seed) {
   const I base = (I)blockIdx.x * (I)(kThreads * ITEMS) + (I)threadIdx.x;
   I lo[ITEMS];
   float4 a[ITEMS], b[ITEMS];
@@ -73,8 +80,14 @@ __global__ void __launch_bounds__(kThreads)
     const I u = base + (I)(it * kThreads);
     if (u < n_units) {
       float4 x = a[it], y = b[it];
-      if (!amp1_only) mv2<MK>(g, x.x, x.y, y.x, y.y);
-      mv2<MK>(g, x.z, x.w, y.z, y.w);
+      if constexpr (DITHER) {
+        const uint32_t h = unit_key(lo[it], seed);
+        if (!amp1_only) mv2_dither<MK>(g, x.x, x.y, y.x, y.y, h);
+        mv2_dither<MK>(g, x.z, x.w, y.z, y.w, mix32(h));
+      } else {
+        if (!amp1_only) mv2<MK>(g, x.x, x.y, y.x, y.y);
+        mv2<MK>(g, x.z, x.w, y.z, y.w);
+      }
       psi[lo[it]] = x;
       psi[lo[it] | tmask] = y;
     }
@@ -82,9 +95,10 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // ---- complex64 1-qubit, target bit 0: the pair shares one 16-byte vector ----------
-template <typename I, int MK, int ITEMS>
+template <typename I, int MK, int ITEMS, bool DITHER>
 __global__ void __launch_bounds__(kThreads)
-    k1q_c64_in(float4* __restrict__ psi, I n_units, Ins<I> ins, I cmask, M2<float> g) {
+    k1q_c64_in(float4* __restrict__ psi, I n_units, Ins<I> ins, I cmask, M2<float> g,
+               uint32_t seed) {
   const I base = (I)blockIdx.x * (I)(kThreads * ITEMS) + (I)threadIdx.x;
   I v[ITEMS];
   float4 a[ITEMS];
@@ -101,7 +115,10 @@ __global__ void __launch_bounds__(kThreads)
     const I u = base + (I)(it * kThreads);
     if (u < n_units) {
       float4 x = a[it];
-      mv2<MK>(g, x.x, x.y, x.z, x.w);
+      if constexpr (DITHER)
+        mv2_dither<MK>(g, x.x, x.y, x.z, x.w, unit_key(v[it], seed));
+      else
+        mv2<MK>(g, x.x, x.y, x.z, x.w);
       psi[v[it]] = x;
     }
   }
@@ -427,7 +444,7 @@ void split_c64(const int* bits, int nb, std::vector<int>* vpos, I* vmask, int* a
 
 template <typename I, int MK>
 void run_1q_c64(float4* psi, int n, cudaStream_t st, int t, int nc, const int* cp,
-                const M2<float>& g) {
+                const M2<float>& g, uint32_t seed) {
   std::vector<int> vpos;
   I cmask = 0;
   int amp1_only = 0;
@@ -437,7 +454,12 @@ void run_1q_c64(float4* psi, int n, cudaStream_t st, int t, int nc, const int* c
     const I nu = I(1) << (n - 1 - (int)vpos.size());
     with_items(items_single(), [&](auto it) {
       constexpr int IT = decltype(it)::value;
-      launch_k(k1q_c64_in<I, MK, IT>, "k1q_c64_in", grid_for(nu, IT), st, psi, nu, ins, cmask, g);
+      if (seed)
+        launch_k(k1q_c64_in<I, MK, IT, true>, "k1q_c64_in", grid_for(nu, IT), st, psi, nu, ins,
+                 cmask, g, seed);
+      else
+        launch_k(k1q_c64_in<I, MK, IT, false>, "k1q_c64_in", grid_for(nu, IT), st, psi, nu, ins,
+                 cmask, g, seed);
     });
   } else {
     vpos.push_back(t - 1);
@@ -446,8 +468,12 @@ void run_1q_c64(float4* psi, int n, cudaStream_t st, int t, int nc, const int* c
     const I nu = I(1) << (n - 1 - (int)vpos.size());
     with_items(items_pair(), [&](auto it) {
       constexpr int IT = decltype(it)::value;
-      launch_k(k1q_c64_pair<I, MK, IT>, "k1q_c64_pair", grid_for(nu, IT), st, psi, nu, ins,
-               tmask, cmask, amp1_only, g);
+      if (seed)
+        launch_k(k1q_c64_pair<I, MK, IT, true>, "k1q_c64_pair", grid_for(nu, IT), st, psi, nu,
+                 ins, tmask, cmask, amp1_only, g, seed);
+      else
+        launch_k(k1q_c64_pair<I, MK, IT, false>, "k1q_c64_pair", grid_for(nu, IT), st, psi, nu,
+                 ins, tmask, cmask, amp1_only, g, seed);
     });
   }
 }
@@ -473,16 +499,16 @@ void run_1q_c128(double2* psi, int n, cudaStream_t st, int t, int nc, const int*
 
 template <typename I>
 void run_1q(void* data, sv_dtype dt, int n, cudaStream_t st, int t, int nc, const int* cp,
-            const HostMatrix& G) {
+            const HostMatrix& G, uint32_t seed) {
   const int mk = classify2(G);
   if (dt == SV_C64) {
     float4* psi = (float4*)data;
     M2<float> g = to_m2<float>(G);
     switch (mk) {
-      case MK_DIAG: run_1q_c64<I, MK_DIAG>(psi, n, st, t, nc, cp, g); break;
-      case MK_REAL: run_1q_c64<I, MK_REAL>(psi, n, st, t, nc, cp, g); break;
-      case MK_IMOFF: run_1q_c64<I, MK_IMOFF>(psi, n, st, t, nc, cp, g); break;
-      default: run_1q_c64<I, MK_DENSE>(psi, n, st, t, nc, cp, g); break;
+      case MK_DIAG: run_1q_c64<I, MK_DIAG>(psi, n, st, t, nc, cp, g, seed); break;
+      case MK_REAL: run_1q_c64<I, MK_REAL>(psi, n, st, t, nc, cp, g, seed); break;
+      case MK_IMOFF: run_1q_c64<I, MK_IMOFF>(psi, n, st, t, nc, cp, g, seed); break;
+      default: run_1q_c64<I, MK_DENSE>(psi, n, st, t, nc, cp, g, seed); break;
     }
   } else {
     double2* psi = (double2*)data;
@@ -651,7 +677,7 @@ bool is_swap(const HostMatrix& G) {
 
 template <typename I>
 void dispatch(void* data, sv_dtype dt, int n, cudaStream_t st, int k, const int* tp, int nc,
-              const int* cp, const HostMatrix& G) {
+              const int* cp, const HostMatrix& G, uint32_t seed) {
   const int d = 1 << k;
   bool diag = true, ones = true;
   for (int r = 0; r < d && diag; ++r)
@@ -677,7 +703,7 @@ void dispatch(void* data, sv_dtype dt, int n, cudaStream_t st, int k, const int*
     return;
   }
   if (k == 1) {
-    run_1q<I>(data, dt, n, st, tp[0], nc, cp, G);
+    run_1q<I>(data, dt, n, st, tp[0], nc, cp, G, seed);
     return;
   }
   run_gen<I>(data, dt, n, st, k, tp, nc, cp, G);
@@ -692,11 +718,40 @@ bool use_32bit_index(int n, sv_dtype dt) {
 }
 
 sv_status launch_gate(void* data, sv_dtype dt, int n, cudaStream_t st, int k, const int* tp,
-                      int nc, const int* cp, const HostMatrix& G) {
+                      int nc, const int* cp, const HostMatrix& G, RoundCtx* rc) {
+  // complex64 without controls: round with the state's error feedback.
+  // Phases on a subspace (diag(1, .., 1, ph)) act on part of the state only
+  // and keep plain rounding; the structure tests below see the unscaled G.
+  // Complex64 matrices with entries that are not fp32 numbers get a
+  // dithered final rounding in the 1-qubit kernels (seed != 0).
+  const HostMatrix* Gp = &G;
+  static thread_local HostMatrix Gs;
+  uint32_t seed = 0;
+  const int d = 1 << k;
+  if (rc && dt == SV_C64) {
+    for (int e = 0; e < d * d && !seed; ++e)
+      if ((double)(float)G.m[e].re != G.m[e].re || (double)(float)G.m[e].im != G.m[e].im)
+        seed = rc->next_seed();
+  }
+  if (rc && dt == SV_C64 && nc == 0) {
+    bool phase_only = true;
+    for (int r = 0; r < d && phase_only; ++r)
+      for (int c = 0; c < d; ++c)
+        if ((r != c && !is_zero(G.at(r, c))) || (r == c && r + 1 < d && !is_one(G.at(r, c)))) {
+          phase_only = false;
+          break;
+        }
+    if (!phase_only) {
+      Gs.k = k;
+      for (int e = 0; e < d * d; ++e) Gs.m[e] = G.m[e];
+      feedback_round(Gs.m, d, &rc->drift);
+      Gp = &Gs;
+    }
+  }
   if (use_32bit_index(n, dt))
-    dispatch<uint32_t>(data, dt, n, st, k, tp, nc, cp, G);
+    dispatch<uint32_t>(data, dt, n, st, k, tp, nc, cp, *Gp, seed);
   else
-    dispatch<uint64_t>(data, dt, n, st, k, tp, nc, cp, G);
+    dispatch<uint64_t>(data, dt, n, st, k, tp, nc, cp, *Gp, seed);
   return check_launch("gate kernel");
 }
 

@@ -96,6 +96,8 @@ FGate classify(const sv_gate& g, int i, int n, const HostMatrix& G, int kmax) {
     f.type = FG_ALONE;
   }
   if (popc(f.qmask) > kmax) f.type = FG_ALONE;
+  // a multi-qubit Pauli string runs as one rotation pass of its own
+  if (g.kind == SV_GATE_PAULI && k > 1) f.type = FG_ALONE;
   return f;
 }
 
@@ -215,7 +217,16 @@ bool to_fgates_reverse(const sv_circuit* c, const double* theta, int lo, int hi,
       f.cmask = 0;
       for (int e = 0; e < 4; ++e) f.m[e] = D.m[e];
     }
-    const int pauli = g.param < 0 ? 0 : g.kind == SV_GATE_RX ? 1 : g.kind == SV_GATE_RY ? 2 : 3;
+    // generator of a parameterised gate: 1 X, 2 Y, 3 Z on its target; a
+    // multi-qubit PAULI string (4) stays unfused with its own adjoint kernel
+    int pauli = 0;
+    if (g.param >= 0) {
+      if (g.kind == SV_GATE_PAULI)
+        pauli = g.n_tar == 1 ? (g.paulis & 3) : 4;
+      else
+        pauli = g.kind == SV_GATE_RX ? 1 : g.kind == SV_GATE_RY ? 2 : 3;
+    }
+    if (g.kind == SV_GATE_PAULI && g.n_tar > 1) f.type = FG_ALONE;
     if (f.type == FG_1Q && f.cmask == 0) {
       const int t = f.t;
       if (pauli) {

@@ -261,19 +261,20 @@ sv_status launch_finish(const double* src, int count, int slots, double* dst, cu
 
 // ---- expectation value without any allocation ------------------------------------
 // Some callers cannot allocate device memory when they need an energy: a
-// program recording work into a CUDA graph (stream capture forbids
-// cudaMalloc), a serving process that hands the whole device to a
-// caching allocator or a fixed arena up front (a cudaMalloc behind its back
-// can fail or fragment), or code running where a failed allocation cannot be
-// handled.  sv_expval_noalloc serves them: the block partials of the
-// reduction live in this fixed array, which every GPU that loads the library
-// holds until the process exits.  It holds kNoAllocPartials doubles
-// (152 KiB): red_blocks(2^n) <= 1216 partials per chunk of 64 terms, up to
-// SV_NOALLOC_MAX_TERMS / 64 = 16 chunks.  Every block writes its own slot
-// before the finishing kernel reads it, so nothing has to start at zero;
-// calls share the array, so calls that overlap on the GPU (different
-// streams, or devices sharing a context) race.
-constexpr int kNoAllocPartials = kRedMaxBlocks * (SV_NOALLOC_MAX_TERMS / 64);
+// serving process that hands the whole device to a caching allocator or a
+// fixed arena up front (a cudaMalloc behind its back can fail or fragment),
+// or code running where a failed allocation cannot be handled.
+// sv_expval_noalloc serves them: the block partials of the reduction live in
+// this fixed array, which every GPU that loads the library holds until the
+// process exits.  It holds kNoAllocPartials doubles (152 KiB): red_blocks(2^n)
+// <= 1216 partials per chunk of 64 terms, up to SV_NOALLOC_MAX_TERMS / 64 = 16
+// chunks.  Every block writes its own slot before the finishing kernel reads
+// it, so nothing has to start at zero; calls share the array, so calls that
+// overlap on the GPU (different streams, or devices sharing a context) race.
+constexpr int kNoAllocChunks = (SV_NOALLOC_MAX_TERMS + 63) / 64;
+constexpr int kNoAllocPartials = kRedMaxBlocks * kNoAllocChunks;
+static_assert(kNoAllocPartials >= kRedMaxBlocks * ((SV_NOALLOC_MAX_TERMS + 63) / 64),
+              "scratch below one partial per block and chunk");
 static __device__ __align__(256) double g_noalloc_partials[kNoAllocPartials];
 
 namespace {
@@ -313,6 +314,16 @@ extern "C" sv_status sv_expval_noalloc(const void* dev_state, int n_qubits, sv_d
     set_error("sv_expval_noalloc: device ordinal %d out of range", dev);
     return SV_ERR_INVALID;
   }
+  if (cuda_stream) {
+    // the array's address is per device: the stream must run on the current one
+    int sdev = -1;
+    SV_CUDA_TRY(cudaStreamGetDevice((cudaStream_t)cuda_stream, &sdev));
+    if (sdev != dev) {
+      set_error("sv_expval_noalloc: the stream belongs to device %d, the current device is %d",
+                sdev, dev);
+      return SV_ERR_INVALID;
+    }
+  }
   double* scratch = nullptr;
   {
     // first call on a device: look up the array's device address (the host
@@ -337,21 +348,10 @@ extern "C" sv_status sv_expval_noalloc(const void* dev_state, int n_qubits, sv_d
   const uint64_t dim = uint64_t(1) << n_qubits;
   const int g = red_blocks(dim);
   int total = 0;
-  for (int k0 = 0; k0 < H->n_terms; k0 += 64) {
-    PauliDev P{};  // one chunk of up to 64 terms, on the stack
-    P.nt = H->n_terms - k0 < 64 ? H->n_terms - k0 : 64;
-    for (int j = 0; j < P.nt; ++j) {
-      const uint64_t xm = H->xmask[k0 + j], zm = H->zmask[k0 + j];
-      const int ny = __builtin_popcountll(xm & zm) & 3;
-      const double c = H->coeff[k0 + j];
-      P.xm[j] = xm;
-      P.zm[j] = zm;
-      P.cre[j] = ny == 0 ? c : ny == 2 ? -c : 0.0;
-      P.cim[j] = ny == 1 ? c : ny == 3 ? -c : 0.0;
-      P.cre32[j] = (float)P.cre[j];
-      P.cim32[j] = (float)P.cim[j];
-      if (xm == 0 && P.nd == j) ++P.nd;  // leading diagonal terms (no reordering here)
-    }
+  // the same term chunks as sv_expval (a host vector: no device memory)
+  std::vector<PauliDev> chunks;
+  pauli_chunks(H, &chunks);
+  for (const PauliDev& P : chunks) {
     if (dtype == SV_C64)
       kexpval<float, float2><<<g, kRedThreads, 0, st>>>((const float2*)dev_state, dim, P,
                                                         scratch + total);

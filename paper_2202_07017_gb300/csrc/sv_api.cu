@@ -93,9 +93,93 @@ bool gate_matrix(const sv_gate& g, const double* theta, const double* pool, Host
       for (int e = 0; e < d * d; ++e) m[e] = {p[2 * e], p[2 * e + 1]};
       break;
     }
+    case SV_GATE_PAULI: {
+      // c I - i s P, P[tau][tau'] = prod_j sigma_{L_j}[b_j(tau)][b_j(tau')]
+      // with b_j the bit of target j (t_0 the most significant)
+      if (g.n_tar < 1 || g.n_tar > SV_MAX_TARGETS) return false;
+      out->k = g.n_tar;
+      const int k = g.n_tar, d = 1 << k;
+      static const cd sig[4][4] = {{{1, 0}, {0, 0}, {0, 0}, {1, 0}},
+                                   {{0, 0}, {1, 0}, {1, 0}, {0, 0}},
+                                   {{0, 0}, {0, -1}, {0, 1}, {0, 0}},
+                                   {{1, 0}, {0, 0}, {0, 0}, {-1, 0}}};
+      for (int r = 0; r < d; ++r)
+        for (int q = 0; q < d; ++q) {
+          cd p{1, 0};
+          for (int j = 0; j < k; ++j) {
+            const int L = (g.paulis >> (2 * j)) & 3;
+            const int br = (r >> (k - 1 - j)) & 1, bq = (q >> (k - 1 - j)) & 1;
+            const cd f = sig[L][br * 2 + bq];
+            p = {p.re * f.re - p.im * f.im, p.re * f.im + p.im * f.re};
+          }
+          // c delta - i s p
+          m[r * d + q] = {(r == q ? c : 0.0) + s * p.im, -s * p.re};
+        }
+      break;
+    }
     default: return false;
   }
   return out->k == g.n_tar;
+}
+
+// Masks of a PAULI gate's string in amplitude-index bits (qubit q <-> bit
+// n-1-q): X sets x, Z sets z, Y sets both.
+void pauli_masks(int n, const sv_gate& g, uint64_t* xm, uint64_t* zm) {
+  *xm = *zm = 0;
+  for (int j = 0; j < g.n_tar; ++j) {
+    const int L = (g.paulis >> (2 * j)) & 3;
+    const uint64_t b = uint64_t(1) << (n - 1 - g.targets[j]);
+    if (L == 1 || L == 2) *xm |= b;
+    if (L == 2 || L == 3) *zm |= b;
+  }
+}
+
+namespace {
+bool fp32_number(double x) { return (double)(float)x == x; }
+double sq32(cd z) {
+  const double r = (float)z.re, i = (float)z.im;
+  return r * r + i * i;
+}
+}  // namespace
+
+void feedback_round(cd* m, int d, double* drift) {
+  if (!drift) return;
+  bool exact = true;
+  for (int e = 0; e < d * d && exact; ++e) exact = fp32_number(m[e].re) && fp32_number(m[e].im);
+  if (exact) return;
+  const double f = std::exp(-0.5 * *drift);
+  double t = 0.0;
+  for (int e = 0; e < d * d; ++e) {
+    m[e].re *= f;
+    m[e].im *= f;
+    t += sq32(m[e]);
+  }
+  *drift += std::log(t / d);
+}
+
+void feedback_round_diag(cd* dg, int d, double* drift) {
+  if (!drift) return;
+  bool exact = true;
+  for (int e = 0; e < d && exact; ++e) exact = fp32_number(dg[e].re) && fp32_number(dg[e].im);
+  if (exact) return;
+  const double f = std::exp(-0.5 * *drift);
+  double t = 0.0;
+  for (int e = 0; e < d; ++e) {
+    dg[e].re *= f;
+    dg[e].im *= f;
+    t += sq32(dg[e]);
+  }
+  *drift += std::log(t / d);
+}
+
+void feedback_round_pair(double* c, cd* k, double* drift) {
+  if (!drift || (fp32_number(*c) && fp32_number(k->re) && fp32_number(k->im))) return;
+  const double f = std::exp(-0.5 * *drift);
+  *c *= f;
+  k->re *= f;
+  k->im *= f;
+  const double cr = (float)*c;
+  *drift += std::log(cr * cr + sq32(*k));
 }
 
 static void dagger(const HostMatrix& G, HostMatrix* D) {
@@ -103,6 +187,65 @@ static void dagger(const HostMatrix& G, HostMatrix* D) {
   D->k = G.k;
   for (int r = 0; r < d; ++r)
     for (int c = 0; c < d; ++c) D->m[r * d + c] = {G.m[c * d + r].re, -G.m[c * d + r].im};
+}
+
+// Gate i of c applied to the state in the forward direction: PAULI gates by
+// the Pauli-rotation kernels (one pass, whatever the string), every other
+// kind by its matrix (Eq. 1).  Rounding feedback from the state.
+static sv_status apply_circuit_gate(sv_state s, const sv_circuit* c, int i,
+                                    const double* theta) {
+  const sv_gate& g = c->gates[i];
+  if (g.kind == SV_GATE_PAULI) {
+    uint64_t xm, zm;
+    pauli_masks(s->n, g, &xm, &zm);
+    const double a = g.param >= 0 ? theta[g.param] : g.angle;
+    return launch_pauli_rotation(s->data, s->dt, s->n, s->stream, xm, zm, 0.5 * a, &s->rc);
+  }
+  static thread_local HostMatrix G;
+  if (!gate_matrix(g, theta, c->mat_pool, &G)) {
+    set_error("gate %d: cannot build matrix", i);
+    return SV_ERR_INVALID;
+  }
+  int tp[SV_MAX_TARGETS], cp[SV_MAX_CONTROLS];
+  for (int j = 0; j < g.n_tar; ++j) tp[j] = s->n - 1 - g.targets[j];
+  for (int j = 0; j < g.n_ctrl; ++j) cp[j] = s->n - 1 - g.controls[j];
+  return launch_gate(s->data, s->dt, s->n, s->stream, g.n_tar, tp, g.n_ctrl, cp, G, &s->rc);
+}
+
+// Reverse-sweep step for gate i of c on (psi, lam): un-apply it on both
+// states; a parameterised gate first adds Im<lam|P|psi> into `part`
+// (nullptr: no gradient).  PAULI strings by their own kernel, 1-qubit gates
+// by the 1-qubit adjoint kernel, wider gates by their adjoint matrix.
+static sv_status unapply_circuit_gate(sv_state s, void* psi, void* lam, const sv_circuit* c,
+                                      int i, const double* theta, double* part) {
+  const sv_gate& g = c->gates[i];
+  if (g.kind == SV_GATE_PAULI) {
+    uint64_t xm, zm;
+    pauli_masks(s->n, g, &xm, &zm);
+    const double a = g.param >= 0 ? theta[g.param] : g.angle;
+    return launch_adjoint_pauli(psi, lam, s->dt, s->n, s->stream, xm, zm, a,
+                                g.param >= 0 ? part : nullptr, nullptr);
+  }
+  static thread_local HostMatrix G, D;
+  if (!gate_matrix(g, theta, c->mat_pool, &G)) {
+    set_error("gate %d: cannot build matrix", i);
+    return SV_ERR_INVALID;
+  }
+  dagger(G, &D);
+  int tp[SV_MAX_TARGETS], cp[SV_MAX_CONTROLS];
+  for (int j = 0; j < g.n_tar; ++j) tp[j] = s->n - 1 - g.targets[j];
+  for (int j = 0; j < g.n_ctrl; ++j) cp[j] = s->n - 1 - g.controls[j];
+  if (g.n_tar == 1) {
+    const int pauli = (g.param < 0 || !part) ? 0
+                      : g.kind == SV_GATE_RX ? 1
+                      : g.kind == SV_GATE_RY ? 2
+                                             : 3;
+    return launch_adjoint_1q(psi, lam, s->dt, s->n, s->stream, tp[0], g.n_ctrl, cp, D, pauli,
+                             pauli ? part : nullptr, nullptr);
+  }
+  sv_status st = launch_gate(psi, s->dt, s->n, s->stream, g.n_tar, tp, g.n_ctrl, cp, D);
+  if (st == SV_OK) st = launch_gate(lam, s->dt, s->n, s->stream, g.n_tar, tp, g.n_ctrl, cp, D);
+  return st;
 }
 
 sv_status ensure_partials(sv_state s, size_t doubles) {
@@ -203,11 +346,23 @@ static bool valid_circuit(sv_state s, const sv_circuit* c, const double* theta) 
   }
   for (int i = 0; i < c->n_gates; ++i) {
     const sv_gate& g = c->gates[i];
-    if (g.kind < SV_GATE_H || g.kind > SV_GATE_MATRIX) {
+    if (g.kind < SV_GATE_H || g.kind > SV_GATE_PAULI) {
       set_error("gate %d: unknown kind %d", i, g.kind);
       return false;
     }
-    const int want = g.kind == SV_GATE_SWAP ? 2 : g.kind == SV_GATE_MATRIX ? -1 : 1;
+    if (g.kind == SV_GATE_PAULI) {
+      bool ok = g.n_tar >= 1 && g.n_tar <= SV_MAX_TARGETS && g.n_ctrl == 0 &&
+                (g.paulis >> (2 * g.n_tar)) == 0;
+      for (int j = 0; ok && j < g.n_tar; ++j) ok = ((g.paulis >> (2 * j)) & 3) != 0;
+      if (!ok) {
+        set_error("gate %d: PAULI takes 1..%d targets, a letter (X, Y, Z) for each and no "
+                  "controls", i, SV_MAX_TARGETS);
+        return false;
+      }
+    }
+    const int want = g.kind == SV_GATE_SWAP                                ? 2
+                     : (g.kind == SV_GATE_MATRIX || g.kind == SV_GATE_PAULI) ? -1
+                                                                            : 1;
     if (want > 0 && g.n_tar != want) {
       set_error("gate %d: kind %d takes %d targets, got %d", i, g.kind, want, g.n_tar);
       return false;
@@ -339,6 +494,16 @@ sv_status sv_set_stream(sv_state s, void* cuda_stream) {
   return SV_OK;
 }
 
+sv_status sv_set_rounding(sv_state s, int mode) {
+  if (!valid_state(s)) return SV_ERR_INVALID;
+  if (mode != SV_ROUNDING_DEFAULT && mode != SV_ROUNDING_DITHERED) {
+    set_error("sv_set_rounding: mode %d is not SV_ROUNDING_DEFAULT or SV_ROUNDING_DITHERED", mode);
+    return SV_ERR_INVALID;
+  }
+  s->rc.mode = mode;
+  return SV_OK;
+}
+
 sv_status sv_info(sv_state s, void** dev_ptr, int* n_qubits, sv_dtype* dtype) {
   if (!valid_state(s)) return SV_ERR_INVALID;
   if (dev_ptr) *dev_ptr = s->data;
@@ -353,6 +518,7 @@ sv_status sv_init(sv_state s, uint64_t basis_index) {
     set_error("sv_init: basis index beyond 2^%d", s->n);
     return SV_ERR_INVALID;
   }
+  s->rc.reset();
   return launch_init(s->data, s->dt, s->n, s->stream, basis_index);
 }
 
@@ -374,6 +540,7 @@ sv_status sv_host_free(void* p) {
 sv_status sv_upload(sv_state s, const void* host) {
   if (!valid_state(s) || !host) return SV_ERR_INVALID;
   SV_CUDA_TRY(cudaMemcpyAsync(s->data, host, s->bytes(), cudaMemcpyHostToDevice, s->stream));
+  s->rc.reset();
   return SV_OK;
 }
 
@@ -393,6 +560,9 @@ sv_status sv_copy(sv_state dst, sv_state src) {
   if (dst->data == src->data) return SV_OK;
   SV_CUDA_TRY(cudaMemcpyAsync(dst->data, src->data, src->bytes(), cudaMemcpyDeviceToDevice,
                               dst->stream));
+  const int mode = dst->rc.mode;
+  dst->rc = src->rc;
+  dst->rc.mode = mode;
   return SV_OK;
 }
 
@@ -411,7 +581,7 @@ sv_status sv_apply_gate(sv_state s, const int* targets, int n_tar, const int* co
   int tp[SV_MAX_TARGETS], cp[SV_MAX_CONTROLS];
   to_bits(s->n, targets, n_tar, tp);
   to_bits(s->n, controls, n_ctrl, cp);
-  return launch_gate(s->data, s->dt, s->n, s->stream, n_tar, tp, n_ctrl, cp, G);
+  return launch_gate(s->data, s->dt, s->n, s->stream, n_tar, tp, n_ctrl, cp, G, &s->rc);
 }
 
 sv_status sv_apply_circuit(sv_state s, const sv_circuit* c, const double* theta, int fuse_k) {
@@ -421,36 +591,22 @@ sv_status sv_apply_circuit(sv_state s, const sv_circuit* c, const double* theta,
     set_error("fuse_k = %d: expected 0 (unfused) or 2..5", fuse_k);
     return SV_ERR_INVALID;
   }
-  HostMatrix G;
   if (fuse_k > 0) {
     std::vector<FusionItem> plan;
     if (!plan_fusion(c, theta, fusion_config(s->n, s->dt, fuse_k), &plan)) return SV_ERR_INVALID;
     for (const FusionItem& it : plan) {
       sv_status st;
       if (it.is_pass) {
-        st = launch_fused_pass(s->data, s->dt, s->n, s->stream, it.pass);
+        st = launch_fused_pass(s->data, s->dt, s->n, s->stream, it.pass, &s->rc);
       } else {
-        const sv_gate& g = c->gates[it.gate];
-        gate_matrix(g, theta, c->mat_pool, &G);
-        int tp[SV_MAX_TARGETS], cp[SV_MAX_CONTROLS];
-        to_bits(s->n, g.targets, g.n_tar, tp);
-        to_bits(s->n, g.controls, g.n_ctrl, cp);
-        st = launch_gate(s->data, s->dt, s->n, s->stream, g.n_tar, tp, g.n_ctrl, cp, G);
+        st = apply_circuit_gate(s, c, it.gate, theta);
       }
       if (st != SV_OK) return st;
     }
     return SV_OK;
   }
   for (int i = 0; i < c->n_gates; ++i) {
-    const sv_gate& g = c->gates[i];
-    if (!gate_matrix(g, theta, c->mat_pool, &G)) {
-      set_error("gate %d: cannot build matrix", i);
-      return SV_ERR_INVALID;
-    }
-    int tp[SV_MAX_TARGETS], cp[SV_MAX_CONTROLS];
-    to_bits(s->n, g.targets, g.n_tar, tp);
-    to_bits(s->n, g.controls, g.n_ctrl, cp);
-    sv_status st = launch_gate(s->data, s->dt, s->n, s->stream, g.n_tar, tp, g.n_ctrl, cp, G);
+    sv_status st = apply_circuit_gate(s, c, i, theta);
     if (st != SV_OK) return st;
   }
   return SV_OK;
@@ -674,8 +830,10 @@ sv_status sv_apply_pauli_sum(sv_state out, sv_state in, const sv_pauli_sum* H) {
 static bool valid_grad_circuit(const sv_circuit* c) {
   for (int i = 0; i < c->n_gates; ++i) {
     const sv_gate& g = c->gates[i];
-    if (g.param >= 0 && g.kind != SV_GATE_RX && g.kind != SV_GATE_RY && g.kind != SV_GATE_RZ) {
-      set_error("gate %d: only RX, RY, RZ gates may carry a parameter for gradients", i);
+    if (g.param >= 0 && g.kind != SV_GATE_RX && g.kind != SV_GATE_RY && g.kind != SV_GATE_RZ &&
+        g.kind != SV_GATE_PAULI) {
+      set_error("gate %d: only RX, RY, RZ and PAULI gates may carry a parameter for gradients",
+                i);
       return false;
     }
   }
@@ -700,30 +858,15 @@ static sv_status reverse_sweep(sv_state s, const sv_circuit* c, const double* th
   st = apply_pauli_into(lam, psi, s, H, s->dres);
   if (st) return st;
   double* slots = s->partials + (size_t)n_pg * grid;
-  HostMatrix G, D;
   int slot = n_pg;
   int ck = n_ckpt - 1;
   for (int i = c->n_gates - 1; i >= 0; --i) {
-    const sv_gate& g = c->gates[i];
-    gate_matrix(g, theta, c->mat_pool, &G);
-    dagger(G, &D);
-    int tp[SV_MAX_TARGETS], cp[SV_MAX_CONTROLS];
-    to_bits(s->n, g.targets, g.n_tar, tp);
-    to_bits(s->n, g.controls, g.n_ctrl, cp);
-    if (g.n_tar == 1) {
-      int pauli = 0;
-      double* part = nullptr;
-      if (g.param >= 0) {
-        --slot;
-        pauli = g.kind == SV_GATE_RX ? 1 : g.kind == SV_GATE_RY ? 2 : 3;
-        part = s->partials + (size_t)slot * grid;
-      }
-      st = launch_adjoint_1q(psi, lam, s->dt, s->n, s->stream, tp[0], g.n_ctrl, cp, D, pauli,
-                             part, nullptr);
-    } else {
-      st = launch_gate(psi, s->dt, s->n, s->stream, g.n_tar, tp, g.n_ctrl, cp, D);
-      if (st == SV_OK) st = launch_gate(lam, s->dt, s->n, s->stream, g.n_tar, tp, g.n_ctrl, cp, D);
+    double* part = nullptr;
+    if (c->gates[i].param >= 0) {
+      --slot;
+      part = s->partials + (size_t)slot * grid;
     }
+    st = unapply_circuit_gate(s, psi, lam, c, i, theta, part);
     if (st) return st;
     if (ck >= 0 && ckpt_gates[ck] == i) {
       SV_CUDA_TRY(cudaMemcpyAsync(psi, s->ckpt[ck], s->bytes(), cudaMemcpyDeviceToDevice,
@@ -785,7 +928,6 @@ sv_status sv_grad(sv_state s, const sv_circuit* c, const double* theta, const sv
     s->ckpt.push_back(p);
   }
   // forward, storing the state before each checkpoint gate
-  HostMatrix G;
   int ck = 0;
   for (int i = 0; i < c->n_gates; ++i) {
     if (ck < n_checkpoints && checkpoint_gates[ck] == i) {
@@ -793,12 +935,7 @@ sv_status sv_grad(sv_state s, const sv_circuit* c, const double* theta, const sv
                                   s->stream));
       ++ck;
     }
-    const sv_gate& g = c->gates[i];
-    gate_matrix(g, theta, c->mat_pool, &G);
-    int tp[SV_MAX_TARGETS], cp[SV_MAX_CONTROLS];
-    to_bits(s->n, g.targets, g.n_tar, tp);
-    to_bits(s->n, g.controls, g.n_ctrl, cp);
-    st = launch_gate(s->data, s->dt, s->n, s->stream, g.n_tar, tp, g.n_ctrl, cp, G);
+    st = apply_circuit_gate(s, c, i, theta);
     if (st) return st;
   }
   SV_CUDA_TRY(cudaMemcpyAsync(s->work[0], s->data, s->bytes(), cudaMemcpyDeviceToDevice,
@@ -885,28 +1022,13 @@ sv_status sv_grad_fused(sv_state s, const sv_circuit* c, const double* theta,
   if (n_pg)
     SV_CUDA_TRY(cudaMemsetAsync(s->partials, 0, sizeof(double) * (size_t)n_pg * G, s->stream));
   double* slots = s->partials + (size_t)n_pg * G;
-  HostMatrix Gm, D;
   for (size_t i = bounds.size() - 1; i-- > 0;) {
     for (const FusionItem& it : plans[i]) {
       if (it.is_pass) {
         st = launch_fused_reverse_pass(psi, lam, s->dt, s->n, s->stream, it.pass, s->partials, G);
       } else {
-        const sv_gate& g = c->gates[it.gate];
-        gate_matrix(g, theta, c->mat_pool, &Gm);
-        dagger(Gm, &D);
-        int tp[SV_MAX_TARGETS], cp[SV_MAX_CONTROLS];
-        to_bits(s->n, g.targets, g.n_tar, tp);
-        to_bits(s->n, g.controls, g.n_ctrl, cp);
-        if (g.n_tar == 1) {
-          st = launch_adjoint_1q(psi, lam, s->dt, s->n, s->stream, tp[0], g.n_ctrl, cp, D,
-                                 it.slot >= 0 ? it.pauli : 0,
-                                 it.slot >= 0 ? s->partials + (size_t)it.slot * G : nullptr,
-                                 nullptr);
-        } else {
-          st = launch_gate(psi, s->dt, s->n, s->stream, g.n_tar, tp, g.n_ctrl, cp, D);
-          if (st == SV_OK)
-            st = launch_gate(lam, s->dt, s->n, s->stream, g.n_tar, tp, g.n_ctrl, cp, D);
-        }
+        st = unapply_circuit_gate(s, psi, lam, c, it.gate, theta,
+                                  it.slot >= 0 ? s->partials + (size_t)it.slot * G : nullptr);
       }
       if (st) return st;
     }
@@ -1024,6 +1146,6 @@ sv_status sv_profile_stop(char* buf, size_t len) {
 
 uint64_t sv_launch_count(void) { return g_launches.load(); }
 
-int sv_version(void) { return 100; }
+int sv_version(void) { return 101; }
 
 }  // extern "C"

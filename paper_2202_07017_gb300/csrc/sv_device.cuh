@@ -86,6 +86,94 @@ __device__ __forceinline__ void mv2(const M2<R>& g, R& ar, R& ai, R& br, R& bi) 
   bi = nbi;
 }
 
+// ---- complex64: dithered rounding ---------------------------------------------
+// Round-to-nearest errors of identical inputs are identical.  In states with
+// many equal amplitudes (uniform superpositions, the iterates of Grover's
+// search) every amplitude of such a class makes the same rounding error at
+// every gate, and ||psi||^2 moves by the same relative amount each time: a
+// drift linear in the gate count (measured 3e-8 per Grover iteration at
+// n = 20).  Complex64 gate kernels therefore add, inside each output's
+// fused multiply-add chain before its final rounding, a pseudo-random term
+// rho (|a| + |b|) with |rho| <= 2^-24 and zero mean, keyed by the amplitude
+// index and a per-launch seed: the final rounding becomes dithered (its
+// error random, with zero mean, from amplitude to amplitude) and equal
+// amplitudes leave the gate distinct in their last bit, so later roundings
+// are uncorrelated as well.  The added error is of the size of one rounding.
+//
+// mix32: the "lowbias32" integer hash (C. Wellons, hash-prospector, 2018).
+__device__ __forceinline__ uint32_t mix32(uint32_t x) {
+  x ^= x >> 16;
+  x *= 0x7feb352du;
+  x ^= x >> 15;
+  x *= 0x846ca68bu;
+  x ^= x >> 16;
+  return x;
+}
+
+// byte i of h as an odd integer in -255..255 times 2^-32 (|rho| < 2^-24,
+// mean 0 over uniform bytes)
+__device__ __forceinline__ float dither_rho(uint32_t h, int i) {
+  const int b = (int)(int8_t)(h >> (8 * i));
+  return (float)(2 * b + 1) * 2.3283064365386963e-10f;
+}
+
+// (a, b) <- G (a, b) in fp32 with the final rounding of each of the four
+// outputs dithered by rho_i (|a| + |b|) of its own component.
+template <int MK>
+__device__ __forceinline__ void mv2_dither(const M2<float>& g, float& ar, float& ai, float& br,
+                                           float& bi, uint32_t h) {
+  const float dr0 = dither_rho(h, 0) * (fabsf(ar) + fabsf(br));
+  const float di0 = dither_rho(h, 1) * (fabsf(ai) + fabsf(bi));
+  const float dr1 = dither_rho(h, 2) * (fabsf(ar) + fabsf(br));
+  const float di1 = dither_rho(h, 3) * (fabsf(ai) + fabsf(bi));
+  float nar, nai, nbr, nbi;
+  if (MK == MK_DENSE) {
+    nar = fmaf(g.r[0], ar, fmaf(-g.i[0], ai, fmaf(g.r[1], br, fmaf(-g.i[1], bi, dr0))));
+    nai = fmaf(g.r[0], ai, fmaf(g.i[0], ar, fmaf(g.r[1], bi, fmaf(g.i[1], br, di0))));
+    nbr = fmaf(g.r[2], ar, fmaf(-g.i[2], ai, fmaf(g.r[3], br, fmaf(-g.i[3], bi, dr1))));
+    nbi = fmaf(g.r[2], ai, fmaf(g.i[2], ar, fmaf(g.r[3], bi, fmaf(g.i[3], br, di1))));
+  } else if (MK == MK_DIAG) {
+    nar = fmaf(g.r[0], ar, fmaf(-g.i[0], ai, dr0));
+    nai = fmaf(g.r[0], ai, fmaf(g.i[0], ar, di0));
+    nbr = fmaf(g.r[3], br, fmaf(-g.i[3], bi, dr1));
+    nbi = fmaf(g.r[3], bi, fmaf(g.i[3], br, di1));
+  } else if (MK == MK_REAL) {
+    nar = fmaf(g.r[0], ar, fmaf(g.r[1], br, dr0));
+    nai = fmaf(g.r[0], ai, fmaf(g.r[1], bi, di0));
+    nbr = fmaf(g.r[2], ar, fmaf(g.r[3], br, dr1));
+    nbi = fmaf(g.r[2], ai, fmaf(g.r[3], bi, di1));
+  } else {  // [[r0, i*i1], [i*i2, r3]]
+    nar = fmaf(g.r[0], ar, fmaf(-g.i[1], bi, dr0));
+    nai = fmaf(g.r[0], ai, fmaf(g.i[1], br, di0));
+    nbr = fmaf(g.r[3], br, fmaf(-g.i[2], ai, dr1));
+    nbi = fmaf(g.r[3], bi, fmaf(g.i[2], ar, di1));
+  }
+  ar = nar;
+  ai = nai;
+  br = nbr;
+  bi = nbi;
+}
+
+// A thread's running sum: compensated (Kahan) in fp32 for complex64 kernels
+// (GB300 issues fp64 at a small fraction of the fp32 rate, so the per-unit
+// additions stay in fp32 and s - c meets the fp64 block sum once), plain fp64
+// for complex128.
+template <typename R>
+struct CompSum {
+  R s = 0, c = 0;
+  __device__ __forceinline__ void add(R x) {
+    if constexpr (sizeof(R) == 4) {
+      const R y = x - c;
+      const R t = s + y;
+      c = (t - s) - y;
+      s = t;
+    } else {
+      s += x;
+    }
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
 // Sum over the block (fixed order); the result is valid in thread 0.
 __device__ __forceinline__ double block_sum(double v) {
   __shared__ double ws[32];

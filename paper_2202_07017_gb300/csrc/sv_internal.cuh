@@ -57,6 +57,44 @@ struct HostMatrix {
 // for an unknown kind or a wrong target count.
 bool gate_matrix(const sv_gate& g, const double* theta, const double* pool, HostMatrix* out);
 
+// ---- complex64 coefficients: rounding with error feedback --------------------
+// Rounding a unitary to fp32 leaves it slightly non-unitary.  Applied without
+// controls, the rounded matrix fl(G) scales the squared norm of the state by
+// ||fl(G)||_F^2 / 2^k averaged over states - exactly, on every state, for
+// H and for Pauli rotations, whose rounded forms are multiples of unitaries.
+// For H that factor is 2 fl(1/sqrt2)^2 = 1 - 3.4e-8, so N Hadamards lose
+// N * 3.4e-8 of ||psi||^2: a bias that grows with the gate count.  A state
+// therefore carries `drift`, the log of the factor its roundings have applied
+// so far, and each inexact matrix is scaled by exp(-drift / 2) before it is
+// rounded: once the accumulated factor is off by more than half an fp32 step,
+// the entries round the other way, and the factor stays within about 1e-7 of
+// 1 however many gates run.  Matrices whose entries are fp32 numbers (X, Z,
+// CZ, SWAP, ...) are left untouched.
+//
+// feedback_round scales the d x d row-major matrix m in place (when drift is
+// not null and some entry is not an fp32 number) and adds the log of the
+// rounded matrix's mean squared column norm to *drift.  feedback_round_diag
+// does the same for a diagonal of d entries.  feedback_round_pair treats a
+// Pauli rotation c I + k P (P^2 = I, Hermitian) with factor |c|^2 + |k|^2.
+void feedback_round(cd* m, int d, double* drift);
+void feedback_round_diag(cd* dg, int d, double* drift);
+void feedback_round_pair(double* c, cd* k, double* drift);
+
+// A state's complex64 rounding context: the feedback factor above and the
+// launch sequence that seeds the kernels' dithered rounding (mix32 of it;
+// restarting with the state keeps results reproducible).  Null: plain
+// rounding, no dither.
+struct RoundCtx {
+  double drift = 0.0;
+  uint32_t seq = 0;
+  int mode = SV_ROUNDING_DEFAULT;  // sv_set_rounding; kept across resets
+  void reset() {
+    drift = 0.0;
+    seq = 0;
+  }
+  uint32_t next_seed() { return ((++seq) * 0x9E3779B9u) | 1u; }
+};
+
 // ---- reduction geometry -----------------------------------------------------
 constexpr int kRedThreads = 256;
 constexpr int kRedMaxBlocks = 1216;  // 152 SMs x 8
@@ -73,6 +111,8 @@ struct sv_state_s {
   cudaStream_t stream = nullptr;
   bool owned = false;
   int device = 0;
+  // complex64 rounding context since the state was last set (see RoundCtx)
+  sv::RoundCtx rc;
   // fp64 reduction scratch: partials and device results
   double* partials = nullptr;
   size_t partials_cap = 0;  // doubles
@@ -101,9 +141,11 @@ sv_status ensure_work(sv_state s, int which);
 // Applies matrix G on target bit positions tp[0..k-1] (tp[0] = MSB of tau)
 // where all bit positions cp[0..nc-1] are 1.  Picks the specialised kernel
 // from the matrix structure (phase-on-subspace, diagonal, real, swap,
-// dense 1-qubit, generic k-qubit).
+// dense 1-qubit, generic k-qubit).  rc: the state's complex64 rounding
+// context (feedback for gates without controls, dithered rounding of the
+// 1-qubit kernels); null for plain rounding.
 sv_status launch_gate(void* data, sv_dtype dt, int n, cudaStream_t st, int k, const int* tp,
-                      int nc, const int* cp, const HostMatrix& G);
+                      int nc, const int* cp, const HostMatrix& G, RoundCtx* rc = nullptr);
 
 sv_status launch_init(void* data, sv_dtype dt, int n, cudaStream_t st, uint64_t basis);
 
@@ -202,8 +244,9 @@ bool plan_fusion(const sv_circuit* c, const double* theta, const FusionConfig& c
 bool plan_fusion_reverse(const sv_circuit* c, const double* theta, int lo, int hi,
                          const std::vector<int>& slot_of, const FusionConfig& cfg,
                          std::vector<FusionItem>* out);
+// rc: the state's complex64 rounding context (null: plain rounding)
 sv_status launch_fused_pass(void* data, sv_dtype dt, int n, cudaStream_t st,
-                            const FusedPass& pass);
+                            const FusedPass& pass, RoundCtx* rc = nullptr);
 // Reverse-sweep pass over psi and lambda (gradient operations write
 // partials[slot * pstride + block], pstride >= the pass's block count; at
 // most pstride blocks are launched).  fused_reverse_ok: the pass has a
@@ -217,6 +260,18 @@ sv_status launch_wait_selftest(void* data, sv_dtype dt, int n, cudaStream_t st);
 // Reads and clears the fused-pass device status word of the current device
 // (kWaitTimeout = 1: a bounded wait inside a pass gave up).
 unsigned take_fused_status();
+
+// ---- Pauli-string rotations (evolve_kernels.cu) --------------------------------
+// psi <- exp(-i a P) psi for the Pauli string P = (xm, zm) (mask convention
+// of sv_pauli_sum); rc as in launch_gate.
+sv_status launch_pauli_rotation(void* data, sv_dtype dt, int n, cudaStream_t st, uint64_t xm,
+                                uint64_t zm, double a, RoundCtx* rc = nullptr);
+// Reverse-sweep step of U = exp(-i theta P / 2): Im<lam|P|psi> into
+// partials[0..nparts) (nparts = the 1-qubit adjoint's fixed grid), then
+// psi, lam <- U^dagger psi, U^dagger lam.
+sv_status launch_adjoint_pauli(void* psi, void* lam, sv_dtype dt, int n, cudaStream_t st,
+                               uint64_t xm, uint64_t zm, double theta, double* partials,
+                               int* nparts);
 
 // ---- adjoint (adjoint_kernels.cu) ----------------------------------------------
 // Un-applies U^dagger (given as matrix Gdag on bit tp, controls cp) on both

@@ -19,7 +19,8 @@ from . import _build
 
 C64, C128 = 0, 1
 KIND_CODE = {"H": 0, "X": 1, "Y": 2, "Z": 3, "RX": 4, "RY": 5, "RZ": 6, "U1": 7,
-             "SWAP": 8, "MATRIX": 9}
+             "SWAP": 8, "MATRIX": 9, "PAULI": 10}
+LETTER_CODE = {"X": 1, "Y": 2, "Z": 3}
 STATUS = {0: "SV_OK", 1: "SV_ERR_INVALID", 2: "SV_ERR_OOM", 3: "SV_ERR_CUDA",
           4: "SV_ERR_TIMEOUT", 5: "SV_ERR_UNSUPPORTED"}
 
@@ -30,7 +31,7 @@ c_i32, c_i64, c_u64, c_dbl, c_vp = (ctypes.c_int32, ctypes.c_int64, ctypes.c_uin
 class SvGate(ctypes.Structure):
     _fields_ = [("kind", c_i32), ("n_tar", c_i32), ("n_ctrl", c_i32), ("param", c_i32),
                 ("targets", c_i32 * 5), ("controls", c_i32 * 33), ("angle", c_dbl),
-                ("mat_off", c_i64)]
+                ("mat_off", c_i64), ("paulis", c_i32), ("reserved", c_i32)]
 
 
 class SvCircuit(ctypes.Structure):
@@ -49,7 +50,7 @@ class SvError(RuntimeError):
         self.status = status
 
 
-EXPORTS = ("sv_alloc", "sv_wrap", "sv_free", "sv_set_stream", "sv_info", "sv_init",
+EXPORTS = ("sv_alloc", "sv_wrap", "sv_free", "sv_set_stream", "sv_set_rounding", "sv_info", "sv_init",
            "sv_upload", "sv_download", "sv_host_alloc", "sv_host_free", "sv_copy", "sv_apply_gate", "sv_apply_circuit",
            "sv_norm", "sv_expval", "sv_expval_async", "sv_apply_pauli_sum", "sv_adjoint",
            "sv_grad", "sv_grad_fused", "sv_sync", "sv_selftest_wait", "sv_check_guards", "sv_last_error", "sv_launch_count", "sv_version",
@@ -82,6 +83,7 @@ def load(build: bool = True):
         "sv_wrap": [c_vp, ctypes.c_int, ctypes.c_int, c_vp, P(c_vp)],
         "sv_free": [c_vp],
         "sv_set_stream": [c_vp, c_vp],
+        "sv_set_rounding": [c_vp, ctypes.c_int],
         "sv_info": [c_vp, P(c_vp), P(ctypes.c_int), P(ctypes.c_int)],
         "sv_init": [c_vp, c_u64],
         "sv_upload": [c_vp, c_vp],
@@ -171,6 +173,10 @@ class PackedCircuit:
                 r.controls[j] = int(c)
             r.param = int(g.param)
             r.angle = float(g.angle)
+            letters = getattr(g, "paulis", "")
+            if len(letters) > 5:
+                raise SvError(1, f"gate {i}: too many Pauli letters")
+            r.paulis = sum(LETTER_CODE[L] << (2 * j) for j, L in enumerate(letters))
             if g.kind == "MATRIX":
                 m = np.ascontiguousarray(g.matrix, dtype=np.complex128).ravel()
                 r.mat_off = off
@@ -240,6 +246,14 @@ def sv_free(h: int) -> None:
 
 def sv_set_stream(h: int, stream: int) -> None:
     _check(load().sv_set_stream(c_vp(h), c_vp(stream)))
+
+
+ROUNDING = {"default": 0, "dithered": 1}
+
+
+def sv_set_rounding(h: int, mode) -> None:
+    """Complex64 rounding mode: "default" (0) or "dithered" (1)."""
+    _check(load().sv_set_rounding(c_vp(h), int(ROUNDING.get(mode, mode))))
 
 
 def sv_info(h: int) -> Tuple[int, int, int]:

@@ -4,6 +4,7 @@ GPU (these calls make no CUDA call, so they run without a GPU)."""
 import ctypes
 import os
 import re
+import subprocess
 
 import pytest
 
@@ -46,15 +47,32 @@ def test_host_validation_without_gpu():
     assert lib.sv_init(None, 0) == 1
     assert lib.sv_apply_gate(None, None, 1, None, 0, None) == 1
     assert lib.sv_norm(None, None) == 1
+    assert lib.sv_set_rounding(None, 0) == 1
     assert lib.sv_free(None) == 0
     with pytest.raises(sv.SvError) as e:
         sv.sv_alloc(40)
     assert e.value.status == 1
 
 
-def test_struct_layout_matches_header():
-    assert ctypes.sizeof(sv.SvGate) == 4 * (4 + 5 + 33) + 8 + 8
-    assert sv.SvGate.angle.offset == 168 and sv.SvGate.mat_off.offset == 176
+def test_struct_layout_matches_header(tmp_path):
+    """The binding's ctypes records have the sizes and field offsets that a C
+    compiler gives the header's structs."""
+    src = tmp_path / "layout.c"
+    src.write_text(
+        '#include <stddef.h>\n#include <stdio.h>\n#include "sv.h"\n'
+        "int main(void) {\n"
+        '  printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(sv_gate), offsetof(sv_gate, angle),\n'
+        "         offsetof(sv_gate, mat_off), offsetof(sv_gate, paulis), sizeof(sv_circuit),\n"
+        "         sizeof(sv_pauli_sum));\n"
+        "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    c_sizes = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True,
+                                              text=True).stdout.split()]
+    py_sizes = [ctypes.sizeof(sv.SvGate), sv.SvGate.angle.offset, sv.SvGate.mat_off.offset,
+                sv.SvGate.paulis.offset, ctypes.sizeof(sv.SvCircuit),
+                ctypes.sizeof(sv.SvPauliSum)]
+    assert c_sizes == py_sizes
 
 
 def test_pauli_masks_follow_bit_convention():

@@ -1,6 +1,6 @@
 """GPU parity of the batched persistent kernel (energies and adjoint
 gradients of many circuits in one launch) against the oracle's energies and
-exact shift-rule gradients and against the single-state adjoint path; graph
+exact shift-rule gradients; graph
 replay and the autotuner; the batch shaped like 4096 parameter sets of the
 n = 14 hardware-efficient ansatz plus 1024 mixed circuits (n 8..16, depth
 5..15)."""
@@ -93,9 +93,9 @@ def test_batch_rejects_unsupported_gates():
 def test_batch_hea14_and_mixed_shapes():
     """4096 parameter sets of the n = 14, L = 10 ansatz (TFIM) plus 1024
     mixed circuits (n uniform in 8..16, depth 5..15), one persistent launch,
-    autotuned; sampled items against the oracle and the single-state
-    adjoint path."""
-    from paper_2202_07017_gb300 import Batch, State
+    autotuned; sampled items' energies and gradient entries against the
+    oracle (every energy and 20 full gradients: test_gpu_fullsize.py)."""
+    from paper_2202_07017_gb300 import Batch
     hea14, _ = W.hea(14, 10, 1003)
     mixed = W.mixed_batch(1024, 1003)
     circuits = [hea14] + [m[0] for m in mixed]
@@ -110,18 +110,8 @@ def test_batch_hea14_and_mixed_shapes():
     b.close()
     offs = np.concatenate([[0], np.cumsum([circuits[ci].n_params for ci in items])])
     rs = np.random.default_rng(1)
-    sample = [0, 4095, 4096, 5119] + list(rs.integers(0, 5120, 8))
+    sample = [0, 4095, 4096, 4100, 5119] + list(rs.integers(0, 5120, 8))
     for i in sample:
-        c, H, th = circuits[items[i]], hams[items[i]], thetas[i]
-        st = State(c.n_qubits, "c64").init(0)
-        st.apply_circuit(c, th)
-        e_ref, g_ref = st.adjoint(c, th, H)
-        st.close()
-        scale = sum(abs(t[0]) for t in H)
-        assert abs(e[i] - e_ref) <= 2e-5 * scale
-        gi = g[offs[i]:offs[i + 1]]
-        assert _rel(gi, g_ref) <= 2e-5
-    for i in (0, 4100):
         c, H, th = circuits[items[i]], hams[items[i]], thetas[i]
         assert abs(e[i] - oracle.energy(c, th, H)) <= 1e-5 * sum(abs(t[0]) for t in H)
         ps = [0, c.n_params // 2, c.n_params - 1]
@@ -138,8 +128,8 @@ def test_batch_kernel_choice_and_both_state_homes(mode, cl, sm):
     the pair's shared memory, larger ones in the cluster's global slot), a
     gate with 3 controls falling back to the single-block kernel; tune = 3
     runs single blocks with psi (and lambda up to 13 qubits) in shared
-    memory.  Checked against the single-state adjoint."""
-    from paper_2202_07017_gb300 import Batch, State
+    memory.  Energies and sampled gradient entries against the oracle."""
+    from paper_2202_07017_gb300 import Batch
     mixed = W.mixed_batch(40, 2024)
     big = [m for m in mixed if m[0].n_qubits >= 15][:3] + [m for m in mixed if m[0].n_qubits <= 10][:3]
     c3, th3 = W.random_gates(9, 60, 5, max_tar=1, max_ctrl=3, kinds=ONEQ)
@@ -155,15 +145,13 @@ def test_batch_kernel_choice_and_both_state_homes(mode, cl, sm):
         b.close()
         off = 0
         for i, (c, H, th) in enumerate(zip(circuits, hams, thetas)):
-            st = State(c.n_qubits, "c64").init(0)
-            st.apply_circuit(c, th)
-            e_ref, g_ref = st.adjoint(c, th, H)
-            st.close()
             scale = sum(abs(t[0]) for t in H)
-            assert abs(e[i] - e_ref) <= 2e-5 * scale
+            assert abs(e[i] - oracle.energy(c, th, H)) <= 1e-5 * scale
             if c.n_params:
-                # normwise, with a floor for circuits whose gradient vanishes
-                # (parameters on rotations whose controls are rarely set)
-                err = np.max(np.abs(g[off:off + c.n_params] - g_ref))
-                assert err <= 2e-5 * max(np.max(np.abs(g_ref)), 0.05 * scale), (i, err)
+                ps = sorted({0, c.n_params // 3, c.n_params // 2, c.n_params - 1})
+                g_ref = oracle.grad_param_shift(c, th, H, params=ps)
+                # normwise over the sample, with a floor for circuits whose
+                # gradient vanishes (rotations whose controls are rarely set)
+                err = np.max(np.abs(g[off:off + c.n_params][ps] - g_ref[ps]))
+                assert err <= 1e-5 * max(np.max(np.abs(g_ref[ps])), 0.05 * scale), (i, err)
             off += c.n_params

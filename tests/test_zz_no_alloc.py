@@ -1,27 +1,42 @@
 """sv_expval_noalloc: the energy entry point for callers that cannot allocate
-device memory when they need it (code being captured into a CUDA graph,
-where cudaMalloc is not allowed; processes whose device memory belongs to a
-caching allocator or a fixed arena).  Its reduction scratch is a fixed
-array inside the library, so the call itself allocates nothing.
+device memory when they need it (processes whose device memory belongs to a
+caching allocator or a fixed arena, code with no way to recover from a
+failed allocation).  Its reduction scratch is a fixed array inside the
+library, so the call itself allocates nothing.
 
-Checked through the C ABI against sv_expval_async on the same state, for two
-calls in a row (the second reuses the scratch the first left behind).  This
-file is named to be collected last, and it passes both alone in a fresh
+Checked through the C ABI against the oracle's <psi|H|psi> and against
+sv_expval_async on the same state, for two calls in a row (the second reuses
+the scratch the first left behind), and at a size that fills the whole
+scratch array (n = 19: 1216 blocks per chunk, 1024 terms = 16 chunks); the
+device's free memory and torch's allocation do not change across the calls.
+This file is named to be collected last, and it passes both alone in a fresh
 process and after the other tests."""
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle
 import workloads as W
-from gpu_helpers import TOL, rounded
+from gpu_helpers import TOL, oracle_threads, rounded
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
+@pytest.fixture(scope="module", autouse=True)
+def _threads():
+    oracle_threads()
+
+
+def _noalloc(lib, sv, st, pp, out_ptr, stream):
+    return lib.sv_expval_noalloc(ctypes.c_void_p(st.tensor.data_ptr()), st.n, st.code,
+                                 ctypes.byref(pp.s), ctypes.c_void_p(out_ptr),
+                                 ctypes.c_void_p(stream))
+
+
 @pytest.mark.parametrize("dtype", ["c64", "c128"])
-def test_noalloc_energy_matches_sv_expval_on_two_calls(dtype):
+def test_noalloc_energy_matches_oracle_and_sv_expval_on_two_calls(dtype):
     from paper_2202_07017_gb300 import State, sv
     lib = sv.load()
     n = 14
@@ -36,9 +51,7 @@ def test_noalloc_energy_matches_sv_expval_on_two_calls(dtype):
         for i, terms in enumerate((first, second)):
             pp = sv.pack_pauli(terms, n)
             sv.sv_expval_async(st.h, pp, ref[i:].data_ptr())
-            rc = lib.sv_expval_noalloc(ctypes.c_void_p(st.tensor.data_ptr()), n, st.code,
-                                       ctypes.byref(pp.s), ctypes.c_void_p(out[i:].data_ptr()),
-                                       ctypes.c_void_p(stream))
+            rc = _noalloc(lib, sv, st, pp, out[i:].data_ptr(), stream)
             assert rc == 0, sv.sv_last_error()
         torch.cuda.synchronize()
         got, want = out.cpu().numpy(), ref.cpu().numpy()
@@ -46,7 +59,59 @@ def test_noalloc_energy_matches_sv_expval_on_two_calls(dtype):
         st.close()
     for i, terms in enumerate((first, second)):
         scale = sum(abs(c) for c, _ in terms)
+        assert abs(got[i] - oracle.expval(psi, terms, n)) <= TOL[dtype] * scale, i
         assert abs(got[i] - want[i]) <= TOL[dtype] * scale, (i, got[i], want[i])
+
+
+def _few_factor_terms(n, count, seed):
+    """count Pauli strings of 1..3 factors on random qubits (diagonal and
+    X/Y-containing ones mixed), coefficients in [-1, 1)."""
+    rng = W.SplitMix64(seed)
+    terms = []
+    for _ in range(count):
+        k = 1 + rng.next() % 3
+        qs = []
+        while len(qs) < k:
+            q = rng.next() % n
+            if q not in qs:
+                qs.append(q)
+        terms.append((2 * rng.uniform() - 1, tuple((q, "XYZ"[rng.next() % 3]) for q in qs)))
+    return terms
+
+
+def test_noalloc_fills_the_whole_scratch_array_without_allocating():
+    """n = 19 (1216 partials per chunk) with exactly the maximum of 1024
+    terms (16 chunks): every slot of the fixed array is written and read;
+    a second call with other terms follows.  After a first call (which looks
+    up the array's address and loads the kernels), later calls leave torch's
+    allocation and the device's free memory unchanged."""
+    from paper_2202_07017_gb300 import State, sv
+    lib = sv.load()
+    n = 19
+    psi = rounded(W.random_state(n, 22), "c64")
+    terms = [_few_factor_terms(n, 1024, 23), _few_factor_terms(n, 1024, 24)]
+    assert any(all(L == "Z" for _, L in ops) for _, ops in terms[0])
+    assert any(any(L != "Z" for _, L in ops) for _, ops in terms[0])
+    st = State(n, "c64").load(psi)
+    stream = st.stream.cuda_stream
+    out = torch.full((3,), float("nan"), dtype=torch.float64, device=st.tensor.device)
+    packed = [sv.pack_pauli(t, n) for t in terms]
+    try:
+        assert _noalloc(lib, sv, st, packed[1], out[2:].data_ptr(), stream) == 0
+        torch.cuda.synchronize()
+        before = (torch.cuda.memory_allocated(), torch.cuda.mem_get_info()[0])
+        for i in range(2):
+            assert _noalloc(lib, sv, st, packed[i], out[i:].data_ptr(), stream) == 0, \
+                sv.sv_last_error()
+        torch.cuda.synchronize()
+        after = (torch.cuda.memory_allocated(), torch.cuda.mem_get_info()[0])
+        got = out.cpu().numpy()
+    finally:
+        st.close()
+    assert before == after
+    for i in range(2):
+        scale = sum(abs(c) for c, _ in terms[i])
+        assert abs(got[i] - oracle.expval(psi, terms[i], n)) <= TOL["c64"] * scale, i
 
 
 def test_noalloc_rejects_too_many_terms():
