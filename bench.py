@@ -144,6 +144,30 @@ def cpu_oracle_sample(n: int, n_gates: int, threads: int):
     return n_gates / dt, dt, desc
 
 
+def qft_reference(n: int, x: int, idx: np.ndarray) -> np.ndarray:
+    """Closed form of the QFT of |x> at the amplitude indices idx (the
+    circuit's final swaps give the DFT with a + sign):
+    exp(2 pi i ((x y) mod 2^n) / 2^n) / 2^(n/2); x y in exact integers."""
+    xy = (np.uint64(x) * idx.astype(np.uint64)) & np.uint64((1 << n) - 1)
+    return np.exp(2j * np.pi * (xy.astype(np.float64) / float(1 << n))) / 2 ** (n / 2)
+
+
+def sample_indices(n: int, count: int = 1 << 16, seed: int = 2804) -> np.ndarray:
+    import workloads as W
+    raw = W.splitmix64_block(seed, 0, count) & np.uint64((1 << n) - 1)
+    return np.unique(np.concatenate([raw, np.array([0, (1 << n) - 1], np.uint64)]))
+
+
+def qft_sample_error(psi: np.ndarray, n: int, x: int) -> dict:
+    """Error of a QFT output against its closed form on seeded amplitude
+    indices: max |dpsi| and the root-mean-square |dpsi| scaled to the norm
+    of the whole difference (sqrt(2^n) * RMS, an estimate of ||dpsi||_2)."""
+    idx = sample_indices(n)
+    d = np.abs(psi[idx.astype(np.int64)].astype(np.complex128) - qft_reference(n, x, idx))
+    return {"max_abs": float(d.max()), "l2_estimate": float(np.sqrt(np.mean(d * d) * 2.0 ** n)),
+            "samples": int(idx.size)}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -170,6 +194,188 @@ def run_reference(args, rank, world):
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def host_info() -> dict:
+    """Host cores and RAM of the machine the oracle runs on."""
+    ram = None
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemTotal:"):
+                    ram = int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    import platform
+    return {"cores": os.cpu_count() or 1, "ram_bytes": ram, "machine": platform.machine()}
+
+
+def oracle_timings() -> dict:
+    """The oracle as it stands, timed per configuration on 1 thread and on
+    every host core, each on a bounded sample of the configuration's work
+    (units per second scaled from the sample; the sample is stated)."""
+    import oracle
+    import workloads as W
+    cores = os.cpu_count() or 1
+    out = {"host": host_info()}
+
+    def timed(fn):
+        t0 = time.perf_counter()
+        fn()
+        return time.perf_counter() - t0
+
+    cases = []
+    c0, th0 = W.random_layered(12, 20, 1000)
+    cases.append(("C0 random layered n=12 complex128 depth 20", "gate-apps/s",
+                  lambda: oracle.run(c0, th0), len(c0.gates), "the whole circuit", len(c0.gates)))
+    q = W.qft(30)
+    x = W.random_basis_index(30, SEED_QFT)
+    q2 = W.Circuit(30, q.gates[:2], 0)
+    cases.append(("C1 QFT n=30 (oracle in complex128)", "gate-apps/s",
+                  lambda: oracle.run(q2, None, basis=x), 2, "first 2 gates (H, controlled-U1)",
+                  len(q.gates)))
+    c2, th2 = W.hea(20, 10, 1002)
+    H2 = W.tfim(20)
+    cases.append(("C2 HEA n=20 L=10 energy", "energies/s",
+                  lambda: oracle.energy(c2, th2, H2), 1, "one energy (circuit + TFIM)", 1))
+    c3, th3 = W.hea(14, 10, 1003)
+    H3 = W.tfim(14)
+    cases.append(("C3 batch item: HEA n=14 L=10 energy", "energies/s",
+                  lambda: oracle.energy(c3, th3, H3), 1, "one of the 4096 items", 1))
+    c4, th4 = W.random_layered(28, 40, 1004)
+    c4s = W.Circuit(28, c4.gates[:2], c4.n_params)
+    cases.append(("C4 random layered n=28 (oracle in complex128)", "gate-apps/s",
+                  lambda: oracle.run(c4s, th4), 2, "first 2 gates (RX, RY)", len(c4.gates)))
+    rows = []
+    for name, unit, fn, units, sample, total in cases:
+        row = {"config": name, "unit": unit, "sample": sample}
+        for label, t in (("1_thread", 1), ("all_cores", cores)):
+            oracle.set_threads(t)
+            secs = timed(fn)
+            row[label] = {"threads": t, "seconds": secs, "value": units / secs}
+        if unit == "gate-apps/s":
+            row["full_circuit_estimate_s_all_cores"] = total / row["all_cores"]["value"]
+        rows.append(row)
+    oracle.set_threads(cores)
+    out["configs"] = rows
+    return out
+
+
+def measured_alu_peaks(torch) -> dict:
+    """Library GEMM rates on this GPU as ALU denominators (the driver's
+    MEASURED_PEAKS.json has HBM and bf16 only): cuBLAS fp32 SGEMM without
+    TF32 (FFMA issue) and fp64 DGEMM, best of a few 8192^3 / 4096^3 runs."""
+    out = {}
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        for name, dt, n, reps in (("fp32_ffma_tflops", torch.float32, 8192, 5),
+                                  ("fp64_tflops", torch.float64, 4096, 3)):
+            a = torch.randn(n, n, dtype=dt, device="cuda")
+            b = torch.randn(n, n, dtype=dt, device="cuda")
+            torch.matmul(a, b)
+            torch.cuda.synchronize()
+            best = float("inf")
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.matmul(a, b)
+                e1.record()
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1) / 1e3)
+            out[name] = 2.0 * n ** 3 / best / 1e12
+            del a, b
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    out["how"] = ("torch.matmul (cuBLAS) fp32 8192^3 with TF32 off and fp64 4096^3, "
+                  "best of a few, CUDA events; one FMA = 2 flops")
+    return out
+
+
+def _state_errors(got: np.ndarray, ref: np.ndarray) -> dict:
+    d = np.abs(np.asarray(got, np.complex128) - ref)
+    g = np.asarray(got, np.complex128)
+    return {"max_abs": float(d.max()), "l2": float(np.sqrt(np.sum(d * d))),
+            "norm_err": float(abs(1.0 - np.vdot(g, g).real))}
+
+
+def _rel(g, ref) -> float:
+    return float(np.max(np.abs(np.asarray(g) - ref)) / max(float(np.max(np.abs(ref))), 1e-300))
+
+
+def accuracy(torch, n28_golden: bool = True) -> dict:
+    """Each configuration's result against the complex128 oracle (or a closed
+    form), on the same seeded inputs: max |dpsi|, ||dpsi||_2 and
+    |1 - ||psi||^2| of states; energy and normwise gradient errors."""
+    import oracle
+    import workloads as W
+    from paper_2202_07017_gb300 import Batch, State
+    oracle.set_threads(os.cpu_count() or 1)
+    out = {}
+    # C0: full 4096-amplitude output, complex128
+    c0, th0 = W.random_layered(12, 20, 1000)
+    st = State(12, "c128").init(0)
+    out["C0_layered_n12_c128"] = _state_errors(st.apply_circuit(c0, th0).numpy(),
+                                                oracle.run(c0, th0))
+    st.close()
+    # C2: HEA n=20 L=10, TFIM, complex64: state, energy, sampled gradients
+    c2, th2 = W.hea(20, 10, 1002)
+    H2 = W.tfim(20)
+    ref2 = oracle.run(c2, th2)
+    e_ref = oracle.expval(ref2, H2, 20)
+    ps = [0, 19, 57, 100, 133, 150, 181, 199]
+    g_ref = oracle.grad_param_shift(c2, th2, H2, params=ps)
+    row = {}
+    for fk in (0, 4):
+        st = State(20, "c64").init(0)
+        e, g = st.grad(c2, th2, H2, [], fuse_k=fk)
+        row[f"fuse_k={fk}"] = dict(_state_errors(st.numpy(), ref2), energy_err=abs(e - e_ref),
+                                   grad_rel_err_sampled=_rel(g[ps], g_ref[ps]))
+        st.close()
+    row["gradient_sample"] = ps
+    out["C2_hea_n20_tfim_c64"] = row
+    # C3: sampled items of the batch, energies and two items' gradients
+    hea14, _ = W.hea(14, 10, 1003)
+    mixed = W.mixed_batch(1024, 1003)
+    circuits = [hea14] + [m[0] for m in mixed]
+    hams = [W.tfim(14)] + [m[2] for m in mixed]
+    items = [0] * 4096 + list(range(1, 1025))
+    thetas = [W.hea_theta(14, 10, 1003 + i) for i in range(4096)] + [m[1] for m in mixed]
+    b = Batch(circuits, hams, items, tune=False)
+    e, g = b.run(torch.tensor(np.concatenate(thetas), dtype=torch.float64, device="cuda"))
+    e, g = e.cpu().numpy(), g.cpu().numpy()
+    b.close()
+    offs = np.concatenate([[0], np.cumsum([len(t) for t in thetas])])
+    picks = list(range(0, len(items), 64)) + [len(items) - 1]
+    e_err = []
+    for i in picks:
+        c = circuits[items[i]]
+        e_err.append(abs(e[i] - oracle.energy(c, thetas[i], hams[items[i]])))
+    g_err = []
+    for i in (5, 4096 + 3):
+        c = circuits[items[i]]
+        gr = oracle.grad_param_shift(c, thetas[i], hams[items[i]])
+        g_err.append(_rel(g[offs[i]:offs[i + 1]], gr))
+    out["C3_batch_c64"] = {"items_checked_energy": len(picks), "max_energy_err": max(e_err),
+                           "items_checked_gradient": 2, "max_grad_rel_err": max(g_err)}
+    # C4 n=28: fused forward state against the oracle's stored run
+    gold = os.path.join(ROOT, "tests", "golden", "layered_n28_d40.npz")
+    if n28_golden and os.path.exists(gold):
+        z = np.load(gold)
+        c4, th4 = W.random_layered(28, 40, 1004)
+        st = State(28, "c64").init(0)
+        st.apply_circuit(c4, th4, 4)
+        idx = torch.from_numpy(z["idx"].astype(np.int64)).to(st.tensor.device)
+        got = st.tensor[idx].cpu().numpy().astype(np.complex128)
+        e4 = st.expval(W.sum_z(28))
+        nrm = st.norm()
+        st.close()
+        d = np.abs(got - z["amp"])
+        out["C4_layered_n28_c64_fused"] = {
+            "sampled_amplitudes": int(d.size), "max_abs": float(d.max()),
+            "rms_rel": float(np.sqrt(np.mean(d * d) / np.mean(np.abs(z["amp"]) ** 2))),
+            "norm_err": abs(1 - nrm), "energy_err": abs(e4 - float(z["energy"]))}
+    return out
 
 
 def adjoint_ratio(torch, reps=3):
@@ -272,10 +478,15 @@ def fused_layered(torch, n=33, depth=40, k=4):
     finally:
         sv_free(h)
     pass_bytes = 2 * 8 * 2 ** n
+    # arithmetic of the layer programs: per circuit layer every qubit's
+    # RX RY RZ product is one dense 2x2 on its bit, 8 FMAs per amplitude
+    # (16 per pair); the CZ brick folds into a real +-1 diagonal
+    ffma = float(depth) * n * 8 * 2 ** n
     return {"workload": f"random layered n={n} complex64 depth {depth} ({len(c.gates)} gates), "
                         f"fused register groups of <= {k} qubits",
             "passes": npass, "fused_s": t_full, "gate_apps_per_s": len(c.gates) / t_full,
             "fused_pass_gbs": npass * pass_bytes / t_full / 1e9,
+            "alg_ffma": ffma, "ffma_tflops": 2 * ffma / t_full / 1e12,
             "first_2_layers": {"gates": len(layer2.gates), "fused_s": t2_f, "unfused_s": t2_u,
                                "speedup": t2_u / t2_f},
             "unfused_full_estimate_s": t2_u * len(c.gates) / len(layer2.gates)}
@@ -287,11 +498,13 @@ def qft_c128(torch, n=30, reps=2):
     import workloads as W
     from paper_2202_07017_gb300 import (C128, pack_circuit, sv_alloc, sv_apply_circuit, sv_free,
                                         sv_init, sv_profile_start, sv_profile_stop)
+    from paper_2202_07017_gb300 import State
     circ = W.qft(n)
     pc = pack_circuit(circ)
     x = W.random_basis_index(n, SEED_QFT)
     stream = torch.cuda.current_stream()
-    h = sv_alloc(n, C128, stream.cuda_stream)
+    st = State(n, "c128")
+    h = st.h
     try:
         sv_init(h, x)
         sv_apply_circuit(h, pc, None, 0)  # warm-up
@@ -305,18 +518,39 @@ def qft_c128(torch, n=30, reps=2):
         e1.record(stream)
         torch.cuda.synchronize()
         prof = sv_profile_stop()
+        idx = sample_indices(n)
+        got = st.tensor[torch.from_numpy(idx.astype(np.int64)).to(st.tensor.device)].cpu().numpy()
+        d = np.abs(got - qft_reference(n, x, idx))
+        err = {"max_abs": float(d.max()), "l2_estimate": float(np.sqrt(np.mean(d * d) * 2.0 ** n)),
+               "norm_err": abs(1.0 - st.norm()), "samples": int(idx.size)}
     finally:
-        sv_free(h)
+        st.close()
     secs = e0.elapsed_time(e1) / 1e3 / reps
     kernels = {}
     for name, (cnt, ms) in prof.items():
         b = algorithmic_bytes(name, n, 16)
         kernels[name] = {"launches": cnt, "avg_ms": ms / cnt,
                          "achieved_gbs": b * cnt / (ms / 1e3) / 1e9}
+        f = fp64_instructions(name, n)
+        if f:
+            kernels[name]["fp64_instr_per_launch"] = f
+            kernels[name]["fp64_tinstr_per_s"] = f * cnt / (ms / 1e3) / 1e12
     return {"workload": f"qft n={n} complex128, unfused, seeded basis input, "
                         f"{len(circ.gates)} gates", "state_bytes": 16 << n,
             "ms_per_step": 1e3 * secs, "gate_apps_per_s": len(circ.gates) / secs,
-            "kernels": kernels}
+            "kernels": kernels, "error_vs_closed_form": err}
+
+
+def fp64_instructions(kernel: str, n: int) -> float:
+    """fp64 arithmetic instructions per launch of the complex128 QFT kernels:
+    H (a real 2x2) costs 4 multiplies and 4 fused multiply-adds per
+    amplitude pair; a controlled U1 phase 2 multiplies and 2 FMAs per
+    touched amplitude (2^(n-2)); SWAP and initialisation none."""
+    if kernel.startswith("k1q_c128"):
+        return 8.0 * 2 ** (n - 1)
+    if kernel.startswith("kphase_c128"):
+        return 4.0 * 2 ** (n - 2)
+    return 0.0
 
 
 def layered_adjoint(torch, n=28, depth=40):
@@ -498,6 +732,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-adj28", action="store_true")
     ap.add_argument("--no-c128", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--adj-n", type=int, default=28,
                     help="qubits of the layered-circuit adjoint measurement")
     ap.add_argument("--batch-tune", type=int, default=1, choices=[0, 1, 2, 3],
@@ -606,34 +841,42 @@ def main():
     if rank == 0:
         e2e = None
         if not args.no_e2e:
-            # page-locked input/output buffer from the library (sv_host_alloc)
-            hv = sv_host_alloc(1 << n)
+            # page-locked input and output buffers from the library
+            # (sv_host_alloc): every step uploads the seeded basis state and
+            # downloads the step's result into a separate buffer
+            hin = sv_host_alloc(1 << n)
+            hout = sv_host_alloc(1 << n)
             try:
-                hv[:] = 0
-                hv[x] = 1.0
-                ts, phases = [], []
+                hin[:] = 0
+                hin[x] = 1.0
+                ts, phases, errs = [], [], []
                 for i in range(1 + 4):
                     t0 = time.perf_counter()
-                    sv_upload(h, hv)
+                    sv_upload(h, hin)
                     torch.cuda.synchronize()
                     t1 = time.perf_counter()
                     sv_apply_circuit(h, pc, None, 0)
                     torch.cuda.synchronize()
                     t2 = time.perf_counter()
-                    sv_download(h, hv)
+                    sv_download(h, hout)
                     t3 = time.perf_counter()
                     if i:
                         ts.append(t3 - t0)
                         phases.append((t1 - t0, t2 - t1, t3 - t2))
+                    errs.append(qft_sample_error(hout, n, x))
             finally:
-                sv_host_free(hv)
+                sv_host_free(hin)
+                sv_host_free(hout)
             ph = np.median(np.array(phases), axis=0)
             e2e = {"value": n_gates / float(np.median(ts)), "unit": UNIT,
                    "h2d_bytes_per_step": 8 << n, "d2h_bytes_per_step": 8 << n,
                    "ms_per_step": 1e3 * float(np.median(ts)),
                    "upload_ms": 1e3 * float(ph[0]), "circuit_ms": 1e3 * float(ph[1]),
                    "download_ms": 1e3 * float(ph[2]),
-                   "path": "sv_upload (sv_host_alloc buffer) + sv_apply_circuit + sv_download"}
+                   "path": "sv_upload (sv_host_alloc buffer) + sv_apply_circuit + sv_download",
+                   "output_check": {"max_abs_err_vs_closed_form": max(e["max_abs"] for e in errs),
+                                    "sampled_amplitudes": errs[0]["samples"],
+                                    "every_step_from_the_seeded_input": True}}
         meas = sampling(torch, h, n)
         red = reductions(torch, h, n)
         adj = adjoint_ratio(torch)
@@ -641,6 +884,28 @@ def main():
         batch = None if args.no_batch else batch_solves(torch, tune=args.batch_tune)
         adj28 = None if args.no_adj28 else layered_adjoint(torch, n=args.adj_n)
         c128 = None if args.no_c128 else qft_c128(torch, n=n)
+        alu = measured_alu_peaks(torch)
+        acc = None if args.no_accuracy else accuracy(torch)
+        if acc is not None and e2e is not None:
+            acc["C1_qft_n30_c64"] = e2e["output_check"]
+        if acc is not None and c128 is not None:
+            acc["C1_qft_n30_c128"] = c128["error_vs_closed_form"]
+        rooflines = {}
+        if fused is not None:
+            rooflines["kfused_tma_c64 (random layered n=%d)" % args.fused_n] = {
+                "hbm": {"achieved_gbs": fused["fused_pass_gbs"], "peak_gbs": peak,
+                        "frac": fused["fused_pass_gbs"] / peak},
+                "ffma": {"achieved_tflops": fused["ffma_tflops"],
+                         "peak_tflops": alu["fp32_ffma_tflops"],
+                         "frac": fused["ffma_tflops"] / alu["fp32_ffma_tflops"]}}
+        if c128 is not None:
+            for name, kk in c128["kernels"].items():
+                if "fp64_tinstr_per_s" in kk:
+                    rooflines[name + " (qft n=30)"] = {
+                        "bound": "alu (fp64)", "achieved_tinstr_per_s": kk["fp64_tinstr_per_s"],
+                        "peak_tinstr_per_s": alu["fp64_tflops"] / 2,
+                        "frac": kk["fp64_tinstr_per_s"] / (alu["fp64_tflops"] / 2),
+                        "hbm_frac": kk["achieved_gbs"] / peak}
         cpu = None
         if not args.no_cpu:
             threads = os.cpu_count() or 1
@@ -680,6 +945,10 @@ def main():
             "qft_c128": c128,
             "measure": meas,
             "reductions": red,
+            "accuracy": acc,
+            "alu_peaks": alu,
+            "rooflines": rooflines,
+            "oracle_timings": None if args.no_cpu else oracle_timings(),
         }
     sv_free(h)
     if out is not None:
