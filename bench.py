@@ -441,6 +441,56 @@ def _fused_grad_times(torch, c, theta, pc, pp, ck, reps):
             "energy": e}
 
 
+def qaoa_maxcut(torch, n=24, p=4, reps=3, n_check=16, check=True):
+    """QAOA on MaxCut (3-regular graph, p layers; PAULI "ZZ" cost rotations
+    and "X" mixer rotations, 2p parameters), complex64: forward (init +
+    circuit + energy) and forward + adjoint gradient, unfused and fused; with
+    check (the accuracy leg), the same generator at n_check qubits against
+    the oracle's energy and its exact two-term shift rule."""
+    import workloads as W
+    from paper_2202_07017_gb300 import (C64, pack_circuit, pack_pauli, sv_adjoint, sv_alloc,
+                                        sv_apply_circuit, sv_expval, sv_free, sv_init)
+    out = {"workload": f"QAOA MaxCut, random 3-regular graph n={n}, p={p} "
+                       f"({2 * p} parameters), complex64"}
+    for nq, key in ((n, "timed"), (n_check, "check"))[:2 if check else 1]:
+        edges = W.random_regular_graph(nq, 3, 4000 + nq)
+        c, theta = W.qaoa(nq, edges, p, 4100 + nq)
+        H = W.maxcut(edges)
+        pc, pp = pack_circuit(c), pack_pauli(H, nq)
+        h = sv_alloc(nq, C64, torch.cuda.current_stream().cuda_stream)
+        try:
+            fw, gr = [], []
+            for i in range(reps + 1):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                sv_init(h, 0)
+                sv_apply_circuit(h, pc, theta, 0)
+                e = sv_expval(h, pp)
+                t1 = time.perf_counter()
+                e2, g = sv_adjoint(h, pc, theta, pp)
+                t2 = time.perf_counter()
+                if i:
+                    fw.append(t1 - t0)
+                    gr.append(t2 - t1)
+        finally:
+            sv_free(h)
+        if key == "timed":
+            f, gm = float(np.median(fw)), float(np.median(gr))
+            fused = _fused_grad_times(torch, c, theta, pc, pp, [], reps)
+            out.update({"gates": len(c.gates), "forward_ms": 1e3 * f, "grad_ms": 1e3 * gm,
+                        "grad_over_forward": gm / f, "energy": e,
+                        "fused": {"forward_ms": 1e3 * fused["forward_s"],
+                                  "forward_plus_grad_ms": 1e3 * fused["forward_plus_grad_s"],
+                                  "grad_over_forward": fused["grad_over_forward"]}})
+        else:
+            import oracle
+            e_ref = oracle.energy(c, theta, H)
+            g_ref = oracle.grad_param_shift(c, theta, H)
+            out["error_vs_oracle"] = {"n_qubits": nq, "energy_abs": abs(e2 - e_ref),
+                                      "grad_rel_max": _rel(g, g_ref)}
+    return out
+
+
 def fused_layered(torch, n=33, depth=40, k=4):
     """Random layered circuit (RX, RY, RZ on every qubit + CZ brick), n = 33
     complex64 (64 GiB), depth 40: fused qubit-block passes for the whole
@@ -657,17 +707,19 @@ def sampling(torch, h, n, shots=1 << 20):
 
 
 def reductions(torch, h, n, reps=3):
-    """Norm, sum-Z energy (diagonal terms only) and TFIM energy of the n = 30
-    state already in `h` (the QFT output): per-kernel times from the
-    library's CUDA events and GB/s on one read of the state (8 * 2^n bytes;
-    an X term also reads each amplitude's partner)."""
+    """Norm, sum-Z energy (diagonal terms only: one staged pass) and TFIM
+    energy (three passes: the X terms' bits in three staged sets) of the
+    n = 30 state already in `h` (the QFT output): per-kernel times from the
+    library's CUDA events, GB/s of each pass (one read of the state,
+    8 * 2^n bytes) and the call's time against a single read."""
     import workloads as W
     from paper_2202_07017_gb300 import sv_expval, sv_norm, sv_profile_start, sv_profile_stop
     out = {"workload": f"reductions over the n={n} complex64 QFT state",
            "alg_bytes_per_launch": 8 * 2 ** n}
+    peak, _ = hbm_peak()
     cases = (("norm", "knorm", lambda: sv_norm(h)),
-             ("energy_sum_z", "kexpval", lambda: sv_expval(h, W.sum_z(n))),
-             ("energy_tfim", "kexpval", lambda: sv_expval(h, W.tfim(n))))
+             ("energy_sum_z", "kpauli_energy_c64", lambda: sv_expval(h, W.sum_z(n))),
+             ("energy_tfim", "kpauli_energy_c64", lambda: sv_expval(h, W.tfim(n))))
     for name, kern, fn in cases:
         fn()
         sv_profile_start()
@@ -675,9 +727,16 @@ def reductions(torch, h, n, reps=3):
             v = fn()
         prof = sv_profile_stop()
         cnt, ms = prof.get(kern, (0, float("nan")))
-        out[name] = {"value": v, "kernel": kern, "launches": cnt,
-                     "avg_ms": ms / cnt if cnt else None,
-                     "achieved_gbs": 8 * 2 ** n / (ms / cnt / 1e3) / 1e9 if cnt else None}
+        total_ms = sum(t for _, t in prof.values()) / reps
+        per_call = cnt // reps if cnt else 0
+        # one read of the state per pass: 8 * 2^n bytes per launch
+        out[name] = {"value": v, "kernel": kern, "passes": per_call,
+                     "ms_per_call": total_ms,
+                     "avg_ms_per_pass": ms / cnt if cnt else None,
+                     "pass_gbs": 8 * 2 ** n / (ms / cnt / 1e3) / 1e9 if cnt else None,
+                     "pass_frac": 8 * 2 ** n / (ms / cnt / 1e3) / 1e9 / peak if cnt else None,
+                     "one_read_frac": 8 * 2 ** n / (total_ms / 1e3) / 1e9 / peak,
+                     "kernels_ms": {k: t / reps for k, (c, t) in prof.items()}}
     return out
 
 
@@ -880,6 +939,7 @@ def main():
         meas = sampling(torch, h, n)
         red = reductions(torch, h, n)
         adj = adjoint_ratio(torch)
+        qaoa = qaoa_maxcut(torch, check=not args.no_accuracy)
         fused = None if args.no_fused else fused_layered(torch, n=args.fused_n)
         batch = None if args.no_batch else batch_solves(torch, tune=args.batch_tune)
         adj28 = None if args.no_adj28 else layered_adjoint(torch, n=args.adj_n)
@@ -939,6 +999,7 @@ def main():
             "gpu_launches": launches,
             "clocks": clk,
             "adjoint": adj,
+            "qaoa": qaoa,
             "fused": fused,
             "batch": batch,
             "adjoint_n28": adj28,

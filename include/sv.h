@@ -152,11 +152,14 @@ sv_status sv_set_stream(sv_state s, void* cuda_stream);
  *     output with dither (a pseudo-random term below one fp32 step added
  *     before the final rounding, keyed by amplitude and launch), so equal
  *     amplitudes do not repeat one rounding error gate after gate; the
- *     fused qubit-block passes round to nearest.
- *   SV_ROUNDING_DITHERED: the fused passes' dense 2x2 products dither too
- *     (about twice their arithmetic); for circuits whose states keep many
- *     equal amplitudes, such as Grover's search, whose norm otherwise drifts
- *     linearly with the iteration count.
+ *     fused qubit-block passes round to nearest (their 1-qubit products as
+ *     scaled real rotations between diagonals).
+ *   SV_ROUNDING_DITHERED: the fused passes keep dense 2x2 products and
+ *     dither them too (about twice their arithmetic); for circuits whose
+ *     states repeat, such as Grover's search (many equal amplitudes) or a
+ *     Clifford brick applied thousands of times, where round-to-nearest
+ *     repeats its errors period after period and the norm drifts linearly
+ *     with the repetition count.
  * Results are reproducible: the dither restarts with sv_init / sv_upload.
  * complex128 states ignore the mode.  SV_ERR_INVALID for another value. */
 typedef enum { SV_ROUNDING_DEFAULT = 0, SV_ROUNDING_DITHERED = 1 } sv_rounding;

@@ -24,10 +24,12 @@
 // in software by the fallback kernel - which spreads the strided
 // register-group accesses of a warp over the banks.
 #include <algorithm>
+#include <array>
 #include <map>
 #include <mutex>
 #include <numeric>
 
+#include "slice_geom.cuh"
 #include "sv_device.cuh"
 #include "tma.cuh"
 
@@ -48,14 +50,20 @@ struct FOpDev {
   R m[8];                       // FG_1Q: G00 G01 G10 G11 (re, im); FG_PHASE: m[0..1]
 };
 
-// One layer of a layered group: a dense 2x2 on every group bit i with bit i
-// of u1 set (the 2x2s act on different bits and commute), then a diagonal
-// over the group's 2^k local indices (dk: 0 none, 1 real, 2 complex).
-// Coefficients at coef[off...]: the 2x2s in bit order (8 values each,
-// row-major re/im), then the diagonal (2^k real or 2^k re/im pairs).
+// One layer of a layered group: a scaled real rotation on every group bit i
+// with bit i of rot set, a dense 2x2 on every bit with bit i of u1 set (the
+// 2x2s act on different bits and commute), then a diagonal over the group's
+// 2^k local indices (dk: 0 none, 1 real, 2 complex).  The rotation on bit i
+// is S = [[1, -t], [t, 1]] (form bit i clear) or [[t, -1], [1, t]] (set),
+// |t| <= 1: one FMA per output component.  Coefficients at coef[off...]:
+// the rotations' t in slots 0..3 by bit (if rot), the 2x2s in bit order
+// (8 values each, row-major re/im), then the diagonal (2^k real or 2^k re/im
+// pairs).
 struct FLayerDev {
   uint8_t u1, dk;
   uint16_t off;
+  uint8_t rot, form;
+  uint16_t pad;
 };
 
 template <typename R>
@@ -79,7 +87,7 @@ struct FusedParams {
   uint8_t gk[kFMaxGroups];
   uint8_t gbits[kFMaxGroups][5];
   uint16_t gop[kFMaxGroups + 1];
-  uint8_t gkind[kFMaxGroups];        // 1: the group runs as layers glay[g]..glay[g+1]
+  uint8_t gkind[kFMaxGroups];        // 1, 2: the group runs as layers glay[g]..glay[g+1] (2: no dense 2x2)
   uint16_t glay[kFMaxGroups + 1];
   int ncoef;                         // coefficients in coef[] (elements of R)
   FLayerDev layers[kFMaxLayers];
@@ -338,6 +346,56 @@ __device__ __forceinline__ void dense_bit(const R* c, R (&re)[1 << KG], R (&im)[
   }
 }
 
+// (a, b) <- S (a, b) on every register pair of group bit B, S the scaled
+// rotation [[1, -t], [t, 1]] (F false) or [[t, -1], [1, t]] (F true)
+template <int KG, int B, bool F, typename R>
+__device__ __forceinline__ void rot_bit(R t, R (&re)[1 << KG], R (&im)[1 << KG]) {
+#pragma unroll
+  for (int r = 0; r < (1 << KG); ++r) {
+    if (r & (1 << B)) continue;
+    const int r1 = r | (1 << B);
+    const R a = re[r], b = im[r], c = re[r1], d = im[r1];
+    if constexpr (F) {
+      re[r] = fma(t, a, -c);
+      im[r] = fma(t, b, -d);
+      re[r1] = fma(t, c, a);
+      im[r1] = fma(t, d, b);
+    } else {
+      re[r] = fma(-t, c, a);
+      im[r] = fma(-t, d, b);
+      re[r1] = fma(t, a, c);
+      im[r1] = fma(t, b, d);
+    }
+  }
+}
+
+// the four rotation slots of a layer (16-byte aligned)
+template <typename R>
+__device__ __forceinline__ void load_tau4(const R* c, R (&tv)[4]) {
+  if constexpr (sizeof(R) == 4) {
+    const float4 v = *reinterpret_cast<const float4*>(c);
+    tv[0] = v.x;
+    tv[1] = v.y;
+    tv[2] = v.z;
+    tv[3] = v.w;
+  } else {
+    const double2 v0 = reinterpret_cast<const double2*>(c)[0];
+    const double2 v1 = reinterpret_cast<const double2*>(c)[1];
+    tv[0] = v0.x;
+    tv[1] = v0.y;
+    tv[2] = v1.x;
+    tv[3] = v1.y;
+  }
+}
+
+template <int KG, int B, typename R>
+__device__ __forceinline__ void rot_bit_f(bool f1, R t, R (&re)[1 << KG], R (&im)[1 << KG]) {
+  if (f1)
+    rot_bit<KG, B, true, R>(t, re, im);
+  else
+    rot_bit<KG, B, false, R>(t, re, im);
+}
+
 // dense_bit with the final rounding of every output dithered (mv2_dither),
 // pair r keyed by mix32(h + r): complex64 only
 template <int KG, int B>
@@ -413,6 +471,21 @@ __device__ __forceinline__ void run_layers(typename Cplx2<R>::T* sm, int m, cons
     for (int l = l0; l < l1; ++l) {
       const FLayerDev L = lay[l];
       const R* c = coef + L.off;
+      if (L.rot) {
+        R tv[4];
+        load_tau4<R>(c, tv);
+#pragma unroll
+        for (int i = 0; i < KG; ++i) {
+          if (L.rot & (1 << i)) {
+            const bool f1 = (L.form >> i) & 1;
+            if (i == 0) rot_bit_f<KG, 0, R>(f1, tv[0], re, im);
+            if constexpr (KG > 1) if (i == 1) rot_bit_f<KG, (KG > 1 ? 1 : 0), R>(f1, tv[KG > 1 ? 1 : 0], re, im);
+            if constexpr (KG > 2) if (i == 2) rot_bit_f<KG, (KG > 2 ? 2 : 0), R>(f1, tv[KG > 2 ? 2 : 0], re, im);
+            if constexpr (KG > 3) if (i == 3) rot_bit_f<KG, (KG > 3 ? 3 : 0), R>(f1, tv[KG > 3 ? 3 : 0], re, im);
+          }
+        }
+        c += 4;
+      }
 #pragma unroll
       for (int i = 0; i < KG; ++i) {
         if (L.u1 & (1 << i)) {
@@ -476,6 +549,130 @@ __device__ __forceinline__ void run_layers(typename Cplx2<R>::T* sm, int m, cons
       sm[sb ^ off(r)] = v;
     }
   }
+}
+
+// Two sub-blocks per thread (s and s + kFThreads: a slice of 2^13 amplitudes
+// in 4-qubit groups) through one layer program in rotation form (no dense
+// 2x2: the registers of two tiles fit beside the rotations, not beside the
+// 2x2 coefficients) together: each layer's
+// coefficients are read once for both, and the two tiles' operations are
+// independent, so a warp has twice the arithmetic in flight between the
+// dependent steps of one tile (rotation on bit 0, then bit 1, ..., then the
+// diagonal).
+template <int KG, int B, bool F, typename R>
+__device__ __forceinline__ void rot_bit2(R t, R (&re)[2][1 << KG], R (&im)[2][1 << KG]) {
+#pragma unroll
+  for (int r = 0; r < (1 << KG); ++r) {
+    if (r & (1 << B)) continue;
+    const int r1 = r | (1 << B);
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const R a = re[u][r], b = im[u][r], c = re[u][r1], d = im[u][r1];
+      if constexpr (F) {
+        re[u][r] = fma(t, a, -c);
+        im[u][r] = fma(t, b, -d);
+        re[u][r1] = fma(t, c, a);
+        im[u][r1] = fma(t, d, b);
+      } else {
+        re[u][r] = fma(-t, c, a);
+        im[u][r] = fma(-t, d, b);
+        re[u][r1] = fma(t, a, c);
+        im[u][r1] = fma(t, b, d);
+      }
+    }
+  }
+}
+
+template <int KG, int B, typename R>
+__device__ __forceinline__ void rot_bit2_f(bool f1, R t, R (&re)[2][1 << KG],
+                                           R (&im)[2][1 << KG]) {
+  if (f1)
+    rot_bit2<KG, B, true, R>(t, re, im);
+  else
+    rot_bit2<KG, B, false, R>(t, re, im);
+}
+
+template <int KG, typename R>
+__device__ __forceinline__ void run_layers_x2(typename Cplx2<R>::T* sm, const uint8_t* gb,
+                                              const FLayerDev* lay, int l0, int l1,
+                                              const R* coef) {
+  typedef typename Cplx2<R>::T V2;
+  constexpr int D = 1 << KG;
+  int sw[KG], lm[KG];
+#pragma unroll
+  for (int i = 0; i < KG; ++i) {
+    sw[i] = swz<R>(1 << gb[i]);
+    lm[i] = (1 << gb[i]) - 1;
+  }
+  int sb[2];
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    int b = threadIdx.x + u * kFThreads;
+#pragma unroll
+    for (int i = 0; i < KG; ++i) b = ((b & ~lm[i]) << 1) | (b & lm[i]);
+    sb[u] = swz<R>(b);
+  }
+  R re[2][D], im[2][D];
+#pragma unroll
+  for (int r = 0; r < D; ++r)
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const V2 v = sm[sb[u] ^ reg_off<KG>(r, sw)];
+      re[u][r] = v.x;
+      im[u][r] = v.y;
+    }
+  for (int l = l0; l < l1; ++l) {
+    const FLayerDev L = lay[l];
+    const R* c = coef + L.off;
+    if (L.rot) {
+      R tv[4];
+      load_tau4<R>(c, tv);
+#pragma unroll
+      for (int i = 0; i < KG; ++i) {
+        if (L.rot & (1 << i)) {
+          const bool f1 = (L.form >> i) & 1;
+          if (i == 0) rot_bit2_f<KG, 0, R>(f1, tv[0], re, im);
+          if constexpr (KG > 1) if (i == 1) rot_bit2_f<KG, (KG > 1 ? 1 : 0), R>(f1, tv[KG > 1 ? 1 : 0], re, im);
+          if constexpr (KG > 2) if (i == 2) rot_bit2_f<KG, (KG > 2 ? 2 : 0), R>(f1, tv[KG > 2 ? 2 : 0], re, im);
+          if constexpr (KG > 3) if (i == 3) rot_bit2_f<KG, (KG > 3 ? 3 : 0), R>(f1, tv[KG > 3 ? 3 : 0], re, im);
+        }
+      }
+      c += 4;
+    }
+    if (L.dk == 1) {
+#pragma unroll
+      for (int r = 0; r < D; ++r) {
+        const R d = c[r];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          re[u][r] *= d;
+          im[u][r] *= d;
+        }
+      }
+    } else if (L.dk == 2) {
+#pragma unroll
+      for (int r = 0; r < D; ++r) {
+        const V2 d = *reinterpret_cast<const V2*>(c + 2 * r);
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const R xr = re[u][r], xi = im[u][r];
+          re[u][r] = d.x * xr - d.y * xi;
+          im[u][r] = d.x * xi + d.y * xr;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < D; ++r)
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      int sbr = sb[u];
+      asm volatile("mov.b32 %0, %1;" : "=r"(sbr) : "r"(sb[u]));  // store addresses recomputed
+      V2 v;
+      v.x = re[u][r];
+      v.y = im[u][r];
+      sm[sbr ^ reg_off<KG>(r, sw)] = v;
+    }
 }
 
 // ---- the pass kernel ------------------------------------------------------------
@@ -613,6 +810,10 @@ __global__ void __launch_bounds__(kFThreads, MINB)
   const int lane = threadIdx.x & 31;
   R* csm = reinterpret_cast<R*>(smem_raw + (sbuf - raw) + P.slice_bytes);
   for (int i = threadIdx.x; i < P.ncoef; i += kFThreads) csm[i] = P.coef[i];
+  // the layer table beside the coefficients: read per layer by every thread,
+  // from shared memory rather than the parameter space
+  FLayerDev* lsm = reinterpret_cast<FLayerDev*>(csm + ((P.ncoef + 1) & ~1));
+  for (int i = threadIdx.x; i < P.glay[P.ngroups]; i += kFThreads) lsm[i] = P.layers[i];
   if (threadIdx.x == 0) {
     mbar_init(barp, 1);
     fence_proxy_async_smem();
@@ -641,12 +842,14 @@ __global__ void __launch_bounds__(kFThreads, MINB)
     for (int g = 0; g < P.ngroups; ++g) {
       if (MODE == 4)
         run_layers<KGF, R, false, true>(
-            sm, P.m, P.gbits[g], P.layers, P.glay[g], P.glay[g + 1], csm,
+            sm, P.m, P.gbits[g], lsm, P.glay[g], P.glay[g + 1], csm,
             mix32(P.dseed ^ (uint32_t)blk ^ ((uint32_t)(blk >> 32) + (uint32_t)g * 0x85ebca6bu)));
+      else if (MODE == 3 && KGF == 4 && P.m == 13 && P.gkind[g] == 2)  // two sub-blocks per thread
+        run_layers_x2<KGF, R>(sm, P.gbits[g], lsm, P.glay[g], P.glay[g + 1], csm);
       else if (MODE == 3)
-        run_layers<KGF, R, false>(sm, P.m, P.gbits[g], P.layers, P.glay[g], P.glay[g + 1], csm);
+        run_layers<KGF, R, false>(sm, P.m, P.gbits[g], lsm, P.glay[g], P.glay[g + 1], csm);
       else if (MODE == 1 && P.gkind[g])
-        run_layers<KGF, R, true>(sm, P.m, P.gbits[g], P.layers, P.glay[g], P.glay[g + 1], csm);
+        run_layers<KGF, R, true>(sm, P.m, P.gbits[g], lsm, P.glay[g], P.glay[g + 1], csm);
       else
         run_group<KGF, R>(sm, P.m, P.gbits[g], P.ops, P.gop[g], P.gop[g + 1]);
       if (g + 1 < P.ngroups) __syncthreads();
@@ -1003,6 +1206,8 @@ __global__ void __launch_bounds__(kFThreads, MINB)
   }
 }
 
+}  // namespace
+
 // ---- host: local order, TMA geometry, parameters -----------------------------------
 // TMA view of the state in 8-byte words (w = 1 or 2 per amplitude, lw =
 // log2 w): dim 0 = the 16 words of a 128-byte row, dim 1 = rows (amplitude
@@ -1010,16 +1215,6 @@ __global__ void __launch_bounds__(kFThreads, MINB)
 // spanning up to the next chosen run (the last up to n).  Box: the whole row,
 // the low run, the chosen runs.  Fails (fallback kernel) if the low run is
 // shorter than a row or a box is smaller than 1024 bytes.
-struct TmaGeom {
-  int rank = 0;
-  int tlo[5] = {0, 0, 0, 0, 0}, thi[5] = {0, 0, 0, 0, 0};
-  uint64_t dims[5] = {0, 0, 0, 0, 0}, strides[4] = {0, 0, 0, 0};
-  uint32_t box[5] = {0, 0, 0, 0, 0};
-  std::vector<int> order;  // staged bits in local (shared-memory) order
-  std::vector<int> sw;     // staged bits enumerated as separate boxes
-  int box_bits = 0;        // log2 amplitudes per box
-};
-
 bool tma_geometry(const std::vector<int>& S, int L, int n, int lw, TmaGeom* g) {
   const int lo1 = 4 - lw;  // amplitude bits inside one row
   if (L < lo1 || n > 34) return false;
@@ -1122,11 +1317,6 @@ bool verify_tma(const TmaGeom& g, const std::vector<int>& S, int n, int lw, uint
   return true;
 }
 
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
-                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
-                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
 EncodeTiledFn encode_fn() {
   static EncodeTiledFn fn = nullptr;
   static std::once_flag once;
@@ -1141,6 +1331,45 @@ EncodeTiledFn encode_fn() {
   });
   return fn;
 }
+
+bool build_slice(const TmaGeom& g, const std::vector<int>& S, int n, int lw, void* data,
+                 SliceDev* d) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn || (reinterpret_cast<uintptr_t>(data) & 15) || g.rank < 2 || g.rank > 5) return false;
+  if (!verify_tma(g, S, n, lw, 0) ||
+      !verify_tma(g, S, n, lw, (uint64_t(1) << (n - (int)S.size())) - 1))
+    return false;
+  cuuint64_t dims[5], strides[4];
+  cuuint32_t box[5], estr[5] = {1, 1, 1, 1, 1};
+  for (int k = 0; k < g.rank; ++k) {
+    dims[k] = g.dims[k];
+    box[k] = g.box[k];
+    if (k + 1 < g.rank) strides[k] = g.strides[k];
+  }
+  const uint64_t run_bytes = uint64_t(g.box[1]) * 128;
+  const CUtensorMapL2promotion prom = run_bytes >= 256 ? CU_TENSOR_MAP_L2_PROMOTION_L2_256B
+                                                       : CU_TENSOR_MAP_L2_PROMOTION_L2_128B;
+  if (fn(&d->tmap, CU_TENSOR_MAP_DATA_TYPE_UINT64, (cuuint32_t)g.rank, data, dims, strides, box,
+         estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, prom,
+         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return false;
+  if ((int)g.sw.size() > 12 || (int)S.size() > 24) return false;
+  *reinterpret_cast<Ins<uint64_t>*>(&d->blk) = make_ins<uint64_t>(S);
+  d->m = (int)S.size();
+  d->rank = g.rank;
+  for (int k = 0; k < 5; ++k) {
+    d->tlo[k] = (uint8_t)g.tlo[k];
+    d->thi[k] = (uint8_t)g.thi[k];
+  }
+  d->nsw = (int)g.sw.size();
+  for (int j = 0; j < d->nsw; ++j) d->swpos[j] = (uint8_t)g.sw[j];
+  d->ncopies = 1 << d->nsw;
+  d->box_bytes = (uint32_t)((8u << lw) << g.box_bits);
+  d->slice_bytes = d->box_bytes * (uint32_t)d->ncopies;
+  return true;
+}
+
+namespace {
 
 template <typename R>
 bool build_tma(const TmaGeom& g, void* data, FusedParams<R>* P, CUtensorMap* map = nullptr) {
@@ -1183,13 +1412,18 @@ bool build_tma(const TmaGeom& g, void* data, FusedParams<R>* P, CUtensorMap* map
 // gates on one bit multiply; diagonal gates multiply into the layer's
 // diagonal.  All products in fp64; the coefficients are rounded with the
 // state's error feedback (drift; the layers' 2x2s and diagonals act on the
-// whole state).  Returns false (and leaves nl, nc) if the group keeps its
-// gate list.
+// whole state).  With rotform every dense 2x2 is split into a scaled real
+// rotation between diagonals (see rotation_form below).  Returns 0 (and
+// leaves nl, nc) if the group keeps its gate list, 2 for a layer program in
+// rotation form throughout, 1 for one with dense 2x2s.
 template <typename R>
-bool layer_group(const FusedPass& pass, int g, const int* pos_of, FusedParams<R>* P, int* nlp,
-                 int* ncp, double* drift) {
+int layer_group(const FusedPass& pass, int g, const int* pos_of, FusedParams<R>* P, int* nlp,
+                int* ncp, double* drift, bool rotform) {
   struct LayerH {
     int u1 = 0, dtouch = 0;
+    int rot = 0, form = 0;  // rotation form: bits with scaled rotations tau[i]
+    double tau[5] = {0, 0, 0, 0, 0};
+    double msq = 1.0;  // exact mean squared modulus of Dg
     cd U[5][4];
     cd Dg[32];
     LayerH() {
@@ -1198,6 +1432,120 @@ bool layer_group(const FusedPass& pass, int g, const int* pos_of, FusedParams<R>
     bool empty() const { return !u1 && !dtouch; }
   };
   auto cmul = [](cd a, cd b) { return cd{a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; };
+  auto cdiv = [](cd x, cd y) {
+    const double d = y.re * y.re + y.im * y.im;
+    return cd{(x.re * y.re + x.im * y.im) / d, (x.im * y.re - x.re * y.im) / d};
+  };
+  auto scl = [](cd x, double f) { return cd{x.re * f, x.im * f}; };
+  // U = diag(a) S diag(b), S = [[1, -tau], [tau, 1]] (form 0, |u00| >= |u01|)
+  // or [[tau, -1], [1, tau]] (form 1), tau <= 1 (a ZYZ Euler split:
+  // U = e^{i phi} RZ RY RZ with RY = cos [[1, -tan], [tan, 1]]).  False if U
+  // is not unitary or the split does not reproduce it to 1e-12.
+  auto decompose = [&](const cd* u, cd* a, cd* b, double* tau, int* form) {
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 2; ++j) {
+        double re = 0, im = 0;
+        for (int r = 0; r < 2; ++r) {  // (U^dagger U)_ij
+          const cd x = u[r * 2 + i], y = u[r * 2 + j];
+          re += x.re * y.re + x.im * y.im;
+          im += x.re * y.im - x.im * y.re;
+        }
+        if (std::fabs(re - (i == j ? 1.0 : 0.0)) > 1e-12 || std::fabs(im) > 1e-12) return false;
+      }
+    const double c = std::hypot(u[0].re, u[0].im), s = std::hypot(u[1].re, u[1].im);
+    if (c >= s) {
+      *form = 0;
+      *tau = s / c;
+      a[0] = u[0];
+      b[0] = {1.0, 0.0};
+      if (s == 0) {
+        b[1] = {1.0, 0.0};
+        a[1] = u[3];
+      } else {
+        b[1] = scl(cdiv(u[1], scl(a[0], *tau)), -1.0);
+        a[1] = cdiv(u[3], b[1]);
+      }
+    } else {
+      *form = 1;
+      *tau = c / s;
+      b[1] = {1.0, 0.0};
+      a[0] = scl(u[1], -1.0);
+      if (c == 0) {
+        b[0] = {1.0, 0.0};
+        a[1] = u[2];
+      } else {
+        b[0] = cdiv(u[0], scl(a[0], *tau));
+        a[1] = cdiv(u[2], b[0]);
+      }
+    }
+    const double S[4] = {*form ? *tau : 1.0, -(*form ? 1.0 : *tau), *form ? 1.0 : *tau,
+                         *form ? *tau : 1.0};
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 2; ++j) {
+        const cd v = scl(cmul(a[i], b[j]), S[i * 2 + j]);
+        if (std::fabs(v.re - u[i * 2 + j].re) > 1e-12 || std::fabs(v.im - u[i * 2 + j].im) > 1e-12)
+          return false;
+      }
+    return true;
+  };
+  // The layers in rotation form: each dense 2x2 of layer l becomes
+  // A_l S_l B_l; diagonals commute, so B_0 runs first as a diagonal-only
+  // layer and layer l becomes the rotations S_l and the one diagonal
+  // E_l = B_{l+1} Dg_l A_l.  tau is rounded to the state's precision and A
+  // rescaled so that A S B stays unitary in fp64 (the rounding moves the
+  // rotation angle, not the norm).  False (nothing changed) if some 2x2 is
+  // not unitary.
+  auto rotation_form = [&](const std::vector<LayerH>& in, int k, std::vector<LayerH>* out) {
+    const int D = 1 << k;
+    const size_t NL = in.size();
+    std::vector<std::array<cd, 32>> A(NL), B(NL);
+    std::vector<LayerH> mid(NL);
+    for (size_t l = 0; l < NL; ++l) {
+      for (int r = 0; r < D; ++r) A[l][r] = B[l][r] = {1.0, 0.0};
+      const LayerH& h = in[l];
+      LayerH& o = mid[l];
+      o.rot = h.u1;
+      for (int t = 0; t < k; ++t) {
+        if (!((h.u1 >> t) & 1)) continue;
+        cd a[2], b[2];
+        double tau;
+        int f;
+        if (!decompose(h.U[t], a, b, &tau, &f)) return false;
+        const double tr = (double)(R)tau;
+        const double sc = std::sqrt((1.0 + tau * tau) / (1.0 + tr * tr));
+        a[0] = scl(a[0], sc);
+        a[1] = scl(a[1], sc);
+        o.tau[t] = tr;
+        if (f) o.form |= 1 << t;
+        for (int r = 0; r < D; ++r) {
+          A[l][r] = cmul(A[l][r], a[(r >> t) & 1]);
+          B[l][r] = cmul(B[l][r], b[(r >> t) & 1]);
+        }
+      }
+    }
+    out->clear();
+    bool id = true;
+    for (int r = 0; r < D; ++r)
+      if (B[0][r].re != 1.0 || B[0][r].im != 0.0) id = false;
+    if (!id) {
+      LayerH f0;
+      for (int r = 0; r < D; ++r) f0.Dg[r] = B[0][r];
+      out->push_back(f0);
+    }
+    for (size_t l = 0; l < NL; ++l) {
+      LayerH o = mid[l];
+      double msq = 0.0;
+      for (int r = 0; r < D; ++r) {
+        cd e = cmul(in[l].Dg[r], A[l][r]);
+        if (l + 1 < NL) e = cmul(B[l + 1][r], e);
+        o.Dg[r] = e;
+        msq += e.re * e.re + e.im * e.im;
+      }
+      o.msq = msq / D;
+      out->push_back(o);
+    }
+    return true;
+  };
   int& nl = *nlp;
   int& nc = *ncp;
   const int cap = (int)(sizeof(P->coef) / sizeof(R));
@@ -1212,7 +1560,7 @@ bool layer_group(const FusedPass& pass, int g, const int* pos_of, FusedParams<R>
                          f.m[2].im == 0;
       if (!(f.type == FG_PHASE || (f.type == FG_1Q && (f.cmask == 0 || diag1)))) conv = false;
     }
-    if (!conv) return false;
+    if (!conv) return 0;
     int lb[5];
     for (int i = 0; i < k; ++i) lb[i] = pos_of[pass.S[grp.bits[i]]];
     std::sort(lb, lb + k);
@@ -1269,8 +1617,12 @@ bool layer_group(const FusedPass& pass, int g, const int* pos_of, FusedParams<R>
       }
       if (!ok) break;
     }
-    if (!ok) return false;
+    if (!ok) return 0;
     if (L.back().empty()) L.pop_back();
+    if (rotform) {
+      std::vector<LayerH> R2;
+      if (rotation_form(L, k, &R2)) L.swap(R2);
+    }
     // coefficient count and capacity
     int need = 0;
     std::vector<int> dks;
@@ -1282,11 +1634,12 @@ bool layer_group(const FusedPass& pass, int g, const int* pos_of, FusedParams<R>
       }
       const int dk = one ? 0 : real ? 1 : 2;
       dks.push_back(dk);
+      need += h.rot ? 4 : 0;
       need += 8 * __builtin_popcount(h.u1);
       need += dk == 0 ? 0 : dk == 1 ? D : 2 * D;
       need = (need + 3) & ~3;  // 16-byte alignment of the next layer (float)
     }
-    if (nl + (int)L.size() > kFMaxLayers || nc + need > cap) return false;
+    if (nl + (int)L.size() > kFMaxLayers || nc + need > cap) return 0;
     double* fb = sizeof(R) == 4 ? drift : nullptr;
     for (size_t li = 0; li < L.size(); ++li) {
       LayerH& h = L[li];
@@ -1294,6 +1647,12 @@ bool layer_group(const FusedPass& pass, int g, const int* pos_of, FusedParams<R>
       d.u1 = (uint8_t)h.u1;
       d.dk = (uint8_t)dks[li];
       d.off = (uint16_t)nc;
+      d.rot = (uint8_t)h.rot;
+      d.form = (uint8_t)h.form;
+      d.pad = 0;
+      if (h.rot) {  // tau of bit i in slot i (0 where bit i has no rotation)
+        for (int i = 0; i < 4; ++i) P->coef[nc++] = ((h.rot >> i) & 1) ? (R)h.tau[i] : R(0);
+      }
       for (int i = 0; i < k; ++i)
         if ((h.u1 >> i) & 1) {
           feedback_round(h.U[i], 2, fb);
@@ -1302,10 +1661,11 @@ bool layer_group(const FusedPass& pass, int g, const int* pos_of, FusedParams<R>
             P->coef[nc++] = (R)h.U[i][e].im;
           }
         }
-      if (dks[li] == 1) {  // entries +-1: exact
+      if (dks[li] == 1) {  // real entries (+-1 in gate-list form: exact)
+        feedback_round_diag(h.Dg, D, fb, h.msq);
         for (int r = 0; r < D; ++r) P->coef[nc++] = (R)h.Dg[r].re;
       } else if (dks[li] == 2) {
-        feedback_round_diag(h.Dg, D, fb);
+        feedback_round_diag(h.Dg, D, fb, h.msq);
         for (int r = 0; r < D; ++r) {
           P->coef[nc++] = (R)h.Dg[r].re;
           P->coef[nc++] = (R)h.Dg[r].im;
@@ -1313,7 +1673,9 @@ bool layer_group(const FusedPass& pass, int g, const int* pos_of, FusedParams<R>
       }
       while (nc & 3) P->coef[nc++] = 0;
     }
-    return true;
+    bool dense = false;
+    for (const LayerH& h : L) dense = dense || h.u1 != 0;
+    return dense ? 1 : 2;
   }
 }
 
@@ -1323,7 +1685,7 @@ bool layer_group(const FusedPass& pass, int g, const int* pos_of, FusedParams<R>
 // otherwise a reverse-sweep pass (gate lists, plain rounding).
 template <typename R>
 bool build_params(const FusedPass& pass, const std::vector<int>& order, FusedParams<R>* P,
-                  bool forward = true, double* drift = nullptr) {
+                  bool forward = true, double* drift = nullptr, bool rotform = false) {
   P->ngrad = 0;
   P->extra_tx = 0;
   P->dseed = 0;
@@ -1431,7 +1793,7 @@ bool build_params(const FusedPass& pass, const std::vector<int>& order, FusedPar
     double* fb = sizeof(R) == 4 ? drift : nullptr;
     for (int g = 0; g < P->ngroups; ++g) {
       P->glay[g] = (uint16_t)nl;
-      P->gkind[g] = layer_group(pass, g, pos_of, P, &nl, &nc, fb) ? 1 : 0;
+      P->gkind[g] = (uint8_t)layer_group(pass, g, pos_of, P, &nl, &nc, fb, rotform);
       if (P->gkind[g] || !fb) continue;
       const FusedGroup& grp = pass.groups[g];
       for (size_t j = 0; j < grp.ops.size(); ++j) {
@@ -1498,7 +1860,10 @@ sv_status run_pass(void* data, int n, cudaStream_t st, const FusedPass& pass, Ro
   bool tma = tma_geometry(pass.S, pass.L, n, lw, &geo);
   std::vector<int> order = tma ? geo.order : pass.S;
   const double drift0 = drift ? *drift : 0.0;
-  if (!build_params(pass, order, &P, true, drift)) {
+  // layer programs in rotation form, except where every dense 2x2 is to be
+  // rounded with dither (that mode keeps the dense form)
+  const bool dither_all = sizeof(R) == 4 && rc && rc->mode == SV_ROUNDING_DITHERED;
+  if (!build_params(pass, order, &P, true, drift, !dither_all)) {
     set_error("fused pass exceeds kernel capacity");
     return SV_ERR_INVALID;
   }
@@ -1509,11 +1874,10 @@ sv_status run_pass(void* data, int n, cudaStream_t st, const FusedPass& pass, Ro
   }
   if (tma) tma = build_tma(geo, data, &P);
   if (!tma && order != pass.S && drift) *drift = drift0;  // rebuilt below
-  if (!tma && order != pass.S && !build_params(pass, pass.S, &P, true, drift)) {
+  if (!tma && order != pass.S && !build_params(pass, pass.S, &P, true, drift, !dither_all)) {
     set_error("fused pass exceeds kernel capacity");
     return SV_ERR_INVALID;
   }
-  const bool dither_all = sizeof(R) == 4 && rc && rc->mode == SV_ROUNDING_DITHERED;
   if (dither_all) P.dseed = rc->next_seed();
   const uint64_t nblk = uint64_t(1) << (n - P.m);
   const size_t amp = sizeof(R) * 2;
@@ -1521,10 +1885,11 @@ sv_status run_pass(void* data, int n, cudaStream_t st, const FusedPass& pass, Ro
                                     : (tma ? "kfused_tma_c128" : "kfused_c128"));
   if (tma) {
     int nlay = 0;
-    for (int g = 0; g < P.ngroups; ++g) nlay += P.gkind[g];
+    for (int g = 0; g < P.ngroups; ++g) nlay += P.gkind[g] != 0;
     const int mode = nlay == 0 ? 0 : nlay == P.ngroups ? (dither_all ? 4 : 3) : 1;
     typename PassKernels<R>::Tma kern = PassKernels<R>::tma(kg, mode);
-    const size_t smem = (amp << P.m) + 1024 + sizeof(R) * (size_t)P.ncoef;
+    const size_t smem = (amp << P.m) + 1024 + sizeof(R) * (size_t)((P.ncoef + 1) & ~1) +
+                        sizeof(FLayerDev) * (size_t)P.glay[P.ngroups];
     // resident blocks per SM for this kernel and shared-memory size
     static std::map<std::pair<const void*, size_t>, int> resident;
     int& res = resident[{reinterpret_cast<const void*>(kern), smem}];

@@ -157,7 +157,7 @@ void feedback_round(cd* m, int d, double* drift) {
   *drift += std::log(t / d);
 }
 
-void feedback_round_diag(cd* dg, int d, double* drift) {
+void feedback_round_diag(cd* dg, int d, double* drift, double mean_sq) {
   if (!drift) return;
   bool exact = true;
   for (int e = 0; e < d && exact; ++e) exact = fp32_number(dg[e].re) && fp32_number(dg[e].im);
@@ -169,7 +169,7 @@ void feedback_round_diag(cd* dg, int d, double* drift) {
     dg[e].im *= f;
     t += sq32(dg[e]);
   }
-  *drift += std::log(t / d);
+  *drift += std::log(t / (d * mean_sq));
 }
 
 void feedback_round_pair(double* c, cd* k, double* drift) {
@@ -744,6 +744,8 @@ sv_status sv_norm(sv_state s, double* out) {
 }
 
 static sv_status expval_into(sv_state s, const sv_pauli_sum* H, double* dst) {
+  const sv_status staged = expval_staged(s, H, dst);
+  if (staged != SV_ERR_UNSUPPORTED) return staged;
   std::vector<PauliDev> chunks;
   pauli_chunks(H, &chunks);
   if (chunks.empty()) {
@@ -1096,8 +1098,8 @@ sv_status sv_sync(sv_state s) {
   if (!valid_state(s)) return SV_ERR_INVALID;
   SV_CUDA_TRY(cudaStreamSynchronize(s->stream));
   SV_CUDA_TRY(cudaGetLastError());
-  if (take_fused_status()) {
-    set_error("a fused pass gave up waiting for its bulk copies");
+  if (take_fused_status() | take_pauli_status()) {
+    set_error("a bulk-copy pass gave up waiting for its copies");
     return SV_ERR_TIMEOUT;
   }
   return SV_OK;

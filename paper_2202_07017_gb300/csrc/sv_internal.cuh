@@ -74,10 +74,13 @@ bool gate_matrix(const sv_gate& g, const double* theta, const double* pool, Host
 // feedback_round scales the d x d row-major matrix m in place (when drift is
 // not null and some entry is not an fp32 number) and adds the log of the
 // rounded matrix's mean squared column norm to *drift.  feedback_round_diag
-// does the same for a diagonal of d entries.  feedback_round_pair treats a
-// Pauli rotation c I + k P (P^2 = I, Hermitian) with factor |c|^2 + |k|^2.
+// does the same for a diagonal of d entries whose exact mean squared modulus
+// is mean_sq (1 for a unitary diagonal; a scaled one, as in the rotation
+// form of the fused layer programs, states its own).  feedback_round_pair
+// treats a Pauli rotation c I + k P (P^2 = I, Hermitian) with factor
+// |c|^2 + |k|^2.
 void feedback_round(cd* m, int d, double* drift);
-void feedback_round_diag(cd* dg, int d, double* drift);
+void feedback_round_diag(cd* dg, int d, double* drift, double mean_sq = 1.0);
 void feedback_round_pair(double* c, cd* k, double* drift);
 
 // A state's complex64 rounding context: the feedback factor above and the
@@ -172,6 +175,11 @@ sv_status launch_expval_partials(sv_state s, const PauliDev& P, double* partials
 sv_status launch_apply_pauli(void* out, const void* in, sv_dtype dt, int n, cudaStream_t st,
                              const PauliDev& P, bool accumulate, double* partials,
                              int* nparts);
+// <psi|H|psi> into the device double dst by staged passes (pauli_kernels.cu);
+// SV_ERR_UNSUPPORTED with nothing launched when passes do not apply.
+sv_status expval_staged(sv_state s, const sv_pauli_sum* H, double* dst);
+// Reads and clears the Pauli-pass status word (kWaitTimeout).
+unsigned take_pauli_status();
 // dst[j] = sum_{i<count} src[j * count + i] for j < slots (fixed order).
 sv_status launch_finish(const double* src, int count, int slots, double* dst,
                         cudaStream_t st, bool add_to_dst);
