@@ -54,15 +54,15 @@ struct FOpDev {
 // with bit i of rot set, a dense 2x2 on every bit with bit i of u1 set (the
 // 2x2s act on different bits and commute), then a diagonal over the group's
 // 2^k local indices (dk: 0 none, 1 real, 2 complex).  The rotation on bit i
-// is S = [[1, -t], [t, 1]] (form bit i clear) or [[t, -1], [1, t]] (set),
-// |t| <= 1: one FMA per output component.  Coefficients at coef[off...]:
-// the rotations' t in slots 0..3 by bit (if rot), the 2x2s in bit order
+// is S = [[1, -t], [t, 1]], |t| <= 1: one FMA per output component.
+// Coefficients at coef[off...]: the rotations' t in slots 0..3 by bit (if
+// rot), the 2x2s in bit order
 // (8 values each, row-major re/im), then the diagonal (2^k real or 2^k re/im
 // pairs).
 struct FLayerDev {
   uint8_t u1, dk;
   uint16_t off;
-  uint8_t rot, form;
+  uint8_t rot, pad8;
   uint16_t pad;
 };
 
@@ -88,6 +88,7 @@ struct FusedParams {
   uint8_t gbits[kFMaxGroups][5];
   uint16_t gop[kFMaxGroups + 1];
   uint8_t gkind[kFMaxGroups];        // 1, 2: the group runs as layers glay[g]..glay[g+1] (2: no dense 2x2)
+  uint8_t gxm[kFMaxGroups];          // layer programs: register relabelling the stores undo
   uint16_t glay[kFMaxGroups + 1];
   int ncoef;                         // coefficients in coef[] (elements of R)
   FLayerDev layers[kFMaxLayers];
@@ -388,12 +389,14 @@ __device__ __forceinline__ void load_tau4(const R* c, R (&tv)[4]) {
   }
 }
 
-template <int KG, int B, typename R>
-__device__ __forceinline__ void rot_bit_f(bool f1, R t, R (&re)[1 << KG], R (&im)[1 << KG]) {
-  if (f1)
-    rot_bit<KG, B, true, R>(t, re, im);
-  else
-    rot_bit<KG, B, false, R>(t, re, im);
+// S(t) on group bit i of a register tile, i a compile-time index after unrolling
+template <int KG, typename R>
+__device__ __forceinline__ void rot_bit_at(int i, const R (&tv)[4], R (&re)[1 << KG],
+                                           R (&im)[1 << KG]) {
+  if (i == 0) rot_bit<KG, 0, false, R>(tv[0], re, im);
+  if constexpr (KG > 1) if (i == 1) rot_bit<KG, (KG > 1 ? 1 : 0), false, R>(tv[KG > 1 ? 1 : 0], re, im);
+  if constexpr (KG > 2) if (i == 2) rot_bit<KG, (KG > 2 ? 2 : 0), false, R>(tv[KG > 2 ? 2 : 0], re, im);
+  if constexpr (KG > 3) if (i == 3) rot_bit<KG, (KG > 3 ? 3 : 0), false, R>(tv[KG > 3 ? 3 : 0], re, im);
 }
 
 // dense_bit with the final rounding of every output dithered (mv2_dither),
@@ -429,15 +432,18 @@ __device__ __forceinline__ int reg_off(int r, const int (&sw)[KG]) {
 
 // DITHER (complex64): every dense 2x2 rounds its outputs with dither (see
 // mv2_dither), keyed by dseed and the sub-block.
+// xm: the program's final register relabelling (register r holds group
+// index r ^ xm; stored back at its place).
 template <int KG, typename R, bool TABLE, bool DITHER = false>
 __device__ __forceinline__ void run_layers(typename Cplx2<R>::T* sm, int m, const uint8_t* gb,
                                            const FLayerDev* lay, int l0, int l1, const R* coef,
-                                           uint32_t dseed = 0) {
+                                           uint32_t dseed = 0, int xm = 0) {
   typedef typename Cplx2<R>::T V2;
   constexpr int D = 1 << KG;
   int sw[KG];
 #pragma unroll
   for (int i = 0; i < KG; ++i) sw[i] = swz<R>(1 << gb[i]);
+  const int xoff = reg_off<KG>(xm, sw);
   int soff[TABLE ? D : 1];
   if constexpr (TABLE) {
     soff[0] = 0;
@@ -474,15 +480,13 @@ __device__ __forceinline__ void run_layers(typename Cplx2<R>::T* sm, int m, cons
       if (L.rot) {
         R tv[4];
         load_tau4<R>(c, tv);
+        if (L.rot == (1 << KG) - 1) {  // every bit: one straight-line block
 #pragma unroll
-        for (int i = 0; i < KG; ++i) {
-          if (L.rot & (1 << i)) {
-            const bool f1 = (L.form >> i) & 1;
-            if (i == 0) rot_bit_f<KG, 0, R>(f1, tv[0], re, im);
-            if constexpr (KG > 1) if (i == 1) rot_bit_f<KG, (KG > 1 ? 1 : 0), R>(f1, tv[KG > 1 ? 1 : 0], re, im);
-            if constexpr (KG > 2) if (i == 2) rot_bit_f<KG, (KG > 2 ? 2 : 0), R>(f1, tv[KG > 2 ? 2 : 0], re, im);
-            if constexpr (KG > 3) if (i == 3) rot_bit_f<KG, (KG > 3 ? 3 : 0), R>(f1, tv[KG > 3 ? 3 : 0], re, im);
-          }
+          for (int i = 0; i < KG; ++i) rot_bit_at<KG, R>(i, tv, re, im);
+        } else {
+#pragma unroll
+          for (int i = 0; i < KG; ++i)
+            if (L.rot & (1 << i)) rot_bit_at<KG, R>(i, tv, re, im);
         }
         c += 4;
       }
@@ -546,7 +550,7 @@ __device__ __forceinline__ void run_layers(typename Cplx2<R>::T* sm, int m, cons
       V2 v;
       v.x = re[r];
       v.y = im[r];
-      sm[sb ^ off(r)] = v;
+      sm[sb ^ off(r) ^ xoff] = v;
     }
   }
 }
@@ -583,19 +587,19 @@ __device__ __forceinline__ void rot_bit2(R t, R (&re)[2][1 << KG], R (&im)[2][1 
   }
 }
 
-template <int KG, int B, typename R>
-__device__ __forceinline__ void rot_bit2_f(bool f1, R t, R (&re)[2][1 << KG],
-                                           R (&im)[2][1 << KG]) {
-  if (f1)
-    rot_bit2<KG, B, true, R>(t, re, im);
-  else
-    rot_bit2<KG, B, false, R>(t, re, im);
+template <int KG, typename R>
+__device__ __forceinline__ void rot_bit2_at(int i, const R (&tv)[4], R (&re)[2][1 << KG],
+                                            R (&im)[2][1 << KG]) {
+  if (i == 0) rot_bit2<KG, 0, false, R>(tv[0], re, im);
+  if constexpr (KG > 1) if (i == 1) rot_bit2<KG, (KG > 1 ? 1 : 0), false, R>(tv[KG > 1 ? 1 : 0], re, im);
+  if constexpr (KG > 2) if (i == 2) rot_bit2<KG, (KG > 2 ? 2 : 0), false, R>(tv[KG > 2 ? 2 : 0], re, im);
+  if constexpr (KG > 3) if (i == 3) rot_bit2<KG, (KG > 3 ? 3 : 0), false, R>(tv[KG > 3 ? 3 : 0], re, im);
 }
 
 template <int KG, typename R>
 __device__ __forceinline__ void run_layers_x2(typename Cplx2<R>::T* sm, const uint8_t* gb,
                                               const FLayerDev* lay, int l0, int l1,
-                                              const R* coef) {
+                                              const R* coef, int xm) {
   typedef typename Cplx2<R>::T V2;
   constexpr int D = 1 << KG;
   int sw[KG], lm[KG];
@@ -627,15 +631,13 @@ __device__ __forceinline__ void run_layers_x2(typename Cplx2<R>::T* sm, const ui
     if (L.rot) {
       R tv[4];
       load_tau4<R>(c, tv);
+      if (L.rot == (1 << KG) - 1) {  // every bit: one straight-line block
 #pragma unroll
-      for (int i = 0; i < KG; ++i) {
-        if (L.rot & (1 << i)) {
-          const bool f1 = (L.form >> i) & 1;
-          if (i == 0) rot_bit2_f<KG, 0, R>(f1, tv[0], re, im);
-          if constexpr (KG > 1) if (i == 1) rot_bit2_f<KG, (KG > 1 ? 1 : 0), R>(f1, tv[KG > 1 ? 1 : 0], re, im);
-          if constexpr (KG > 2) if (i == 2) rot_bit2_f<KG, (KG > 2 ? 2 : 0), R>(f1, tv[KG > 2 ? 2 : 0], re, im);
-          if constexpr (KG > 3) if (i == 3) rot_bit2_f<KG, (KG > 3 ? 3 : 0), R>(f1, tv[KG > 3 ? 3 : 0], re, im);
-        }
+        for (int i = 0; i < KG; ++i) rot_bit2_at<KG, R>(i, tv, re, im);
+      } else {
+#pragma unroll
+        for (int i = 0; i < KG; ++i)
+          if (L.rot & (1 << i)) rot_bit2_at<KG, R>(i, tv, re, im);
       }
       c += 4;
     }
@@ -666,8 +668,8 @@ __device__ __forceinline__ void run_layers_x2(typename Cplx2<R>::T* sm, const ui
   for (int r = 0; r < D; ++r)
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
-      int sbr = sb[u];
-      asm volatile("mov.b32 %0, %1;" : "=r"(sbr) : "r"(sb[u]));  // store addresses recomputed
+      int sbr = sb[u] ^ reg_off<KG>(xm, sw);
+      asm volatile("mov.b32 %0, %1;" : "=r"(sbr) : "r"(sbr));  // store addresses recomputed
       V2 v;
       v.x = re[u][r];
       v.y = im[u][r];
@@ -731,7 +733,8 @@ __global__ void __launch_bounds__(kFThreads, sizeof(R) == 4 ? 3 : 2)
     for (int g = 0; g < P.ngroups; ++g) {
       const uint8_t* gb = P.gbits[g];
       if (P.gkind[g])
-        run_layers<KGF, R, true>(sm, P.m, gb, P.layers, P.glay[g], P.glay[g + 1], csm);
+        run_layers<KGF, R, true>(sm, P.m, gb, P.layers, P.glay[g], P.glay[g + 1], csm, 0,
+                                 P.gxm[g]);
       else
         run_group<KGF, R>(sm, P.m, gb, P.ops, P.gop[g], P.gop[g + 1]);
       __syncthreads();
@@ -844,12 +847,15 @@ __global__ void __launch_bounds__(kFThreads, MINB)
         run_layers<KGF, R, false, true>(
             sm, P.m, P.gbits[g], lsm, P.glay[g], P.glay[g + 1], csm,
             mix32(P.dseed ^ (uint32_t)blk ^ ((uint32_t)(blk >> 32) + (uint32_t)g * 0x85ebca6bu)));
-      else if (MODE == 3 && KGF == 4 && P.m == 13 && P.gkind[g] == 2)  // two sub-blocks per thread
-        run_layers_x2<KGF, R>(sm, P.gbits[g], lsm, P.glay[g], P.glay[g + 1], csm);
+      else if (MODE == 3 && KGF == 4 && sizeof(R) == 4 && P.m == 13 && P.gkind[g] == 2)
+        run_layers_x2<KGF, R>(sm, P.gbits[g], lsm, P.glay[g], P.glay[g + 1], csm,
+                              P.gxm[g]);  // two sub-blocks per thread (complex64 slices)
       else if (MODE == 3)
-        run_layers<KGF, R, false>(sm, P.m, P.gbits[g], lsm, P.glay[g], P.glay[g + 1], csm);
+        run_layers<KGF, R, false>(sm, P.m, P.gbits[g], lsm, P.glay[g], P.glay[g + 1], csm, 0,
+                                  P.gxm[g]);
       else if (MODE == 1 && P.gkind[g])
-        run_layers<KGF, R, true>(sm, P.m, P.gbits[g], lsm, P.glay[g], P.glay[g + 1], csm);
+        run_layers<KGF, R, true>(sm, P.m, P.gbits[g], lsm, P.glay[g], P.glay[g + 1], csm, 0,
+                                 P.gxm[g]);
       else
         run_group<KGF, R>(sm, P.m, P.gbits[g], P.ops, P.gop[g], P.gop[g + 1]);
       if (g + 1 < P.ngroups) __syncthreads();
@@ -1120,6 +1126,22 @@ __device__ __forceinline__ void store_pair(uint32_t s1, uint32_t s2, const CUten
   tma_store<RANK>(m2, c, s2);
 }
 
+// Shared memory of a reverse-sweep block after its two slices: the per-warp
+// gradient accumulators, then the operation list, then the gradient
+// generators (each part 16-byte aligned).
+template <typename R>
+__host__ __device__ constexpr size_t adj_ops_offset(int ngrad) {
+  return (sizeof(KahanAcc<R>) * (kFThreads / 32) * (size_t)ngrad + 15) & ~size_t(15);
+}
+template <typename R>
+__host__ __device__ constexpr size_t adj_coef_offset(int ngrad, int nops) {
+  return (adj_ops_offset<R>(ngrad) + sizeof(FOpDev<R>) * (size_t)nops + 15) & ~size_t(15);
+}
+template <typename R>
+__host__ __device__ constexpr size_t adj_tail_bytes(int ngrad, int nops) {
+  return adj_coef_offset<R>(ngrad, nops) + sizeof(R) * 4 * (size_t)ngrad;
+}
+
 // Reverse-sweep pass: as kfused_tma, staging the psi slice (tmap) and the
 // lambda slice (tmap2) on one mbarrier.  Gradient sums: per warp and
 // gradient operation a compensated sum in shared memory, then per block
@@ -1140,6 +1162,14 @@ __global__ void __launch_bounds__(kFThreads, MINB)
   constexpr int nw = kFThreads / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < nw * P.ngrad; i += kFThreads) gacc[i] = KahanAcc<R>{0, 0};
+  // the operation list and the gradient generators beside the accumulators:
+  // every thread reads them per operation, from shared memory rather than
+  // the parameter space
+  unsigned char* tail = reinterpret_cast<unsigned char*>(gacc);
+  FOpDev<R>* osm = reinterpret_cast<FOpDev<R>*>(tail + adj_ops_offset<R>(P.ngrad));
+  R* gsm = reinterpret_cast<R*>(tail + adj_coef_offset<R>(P.ngrad, P.gop[P.ngroups]));
+  for (int i = threadIdx.x; i < P.gop[P.ngroups]; i += kFThreads) osm[i] = P.ops[i];
+  for (int i = threadIdx.x; i < 4 * P.ngrad; i += kFThreads) gsm[i] = P.coef[i];
   const uint32_t barp = smem_addr(&bar);
   if (threadIdx.x == 0) {
     mbar_init(barp, 1);
@@ -1173,7 +1203,7 @@ __global__ void __launch_bounds__(kFThreads, MINB)
       break;
     }
     for (int g = 0; g < P.ngroups; ++g) {
-      run_group_adj<KGF, R>(smp, sml, P.m, P.gbits[g], P.ops, P.gop[g], P.gop[g + 1], P.coef,
+      run_group_adj<KGF, R>(smp, sml, P.m, P.gbits[g], osm, P.gop[g], P.gop[g + 1], gsm,
                             gacc + warp * P.ngrad);
       if (g + 1 < P.ngroups) __syncthreads();
     }
@@ -1495,7 +1525,8 @@ int layer_group(const FusedPass& pass, int g, const int* pos_of, FusedParams<R>*
   // rescaled so that A S B stays unitary in fp64 (the rounding moves the
   // rotation angle, not the norm).  False (nothing changed) if some 2x2 is
   // not unitary.
-  auto rotation_form = [&](const std::vector<LayerH>& in, int k, std::vector<LayerH>* out) {
+  auto rotation_form = [&](const std::vector<LayerH>& in, int k, std::vector<LayerH>* out,
+                           int* xmask) {
     const int D = 1 << k;
     const size_t NL = in.size();
     std::vector<std::array<cd, 32>> A(NL), B(NL);
@@ -1544,6 +1575,30 @@ int layer_group(const FusedPass& pass, int g, const int* pos_of, FusedParams<R>*
       o.msq = msq / D;
       out->push_back(o);
     }
+    // One rotation shape on the device: [[t, -1], [1, t]] = X Z S(-t) with
+    // S(t) = [[1, -t], [t, 1]].  X on a bit relabels the registers instead of
+    // moving them (mask M: register p holds logical index p ^ M; X S(t) X =
+    // S(-t), so a rotation on a flipped bit negates t); the layer's X's come
+    // after its rotations (other bits commute), and X Z = -Z X puts -Z into
+    // the layer's diagonal, which is then read at p ^ M.  The group's stores
+    // undo M.
+    int M = 0;
+    for (LayerH& o : *out) {
+      const int F = o.form;
+      for (int t = 0; t < k; ++t)
+        if ((o.rot >> t) & 1)
+          o.tau[t] *= (((F ^ M) >> t) & 1) ? -1.0 : 1.0;
+      cd Dl[32];
+      for (int r = 0; r < D; ++r) {
+        Dl[r] = o.Dg[r];
+        for (int t = 0; t < k; ++t)
+          if ((F >> t) & 1) Dl[r] = scl(Dl[r], ((r >> t) & 1) ? 1.0 : -1.0);  // -Z_t
+      }
+      M ^= F;
+      for (int p = 0; p < D; ++p) o.Dg[p] = Dl[p ^ M];
+      o.form = 0;
+    }
+    *xmask = M;
     return true;
   };
   int& nl = *nlp;
@@ -1576,6 +1631,7 @@ int layer_group(const FusedPass& pass, int g, const int* pos_of, FusedParams<R>*
       return r;
     };
     std::vector<LayerH> L(1);
+    int gxm = 0;  // the rotation form's final register relabelling
     bool ok = true;
     for (int oi : grp.ops) {
       const FGate& f = pass.gates[oi];
@@ -1621,7 +1677,11 @@ int layer_group(const FusedPass& pass, int g, const int* pos_of, FusedParams<R>*
     if (L.back().empty()) L.pop_back();
     if (rotform) {
       std::vector<LayerH> R2;
-      if (rotation_form(L, k, &R2)) L.swap(R2);
+      int xm = 0;
+      if (rotation_form(L, k, &R2, &xm)) {
+        L.swap(R2);
+        gxm = xm;
+      }
     }
     // coefficient count and capacity
     int need = 0;
@@ -1648,7 +1708,7 @@ int layer_group(const FusedPass& pass, int g, const int* pos_of, FusedParams<R>*
       d.dk = (uint8_t)dks[li];
       d.off = (uint16_t)nc;
       d.rot = (uint8_t)h.rot;
-      d.form = (uint8_t)h.form;
+      d.pad8 = 0;
       d.pad = 0;
       if (h.rot) {  // tau of bit i in slot i (0 where bit i has no rotation)
         for (int i = 0; i < 4; ++i) P->coef[nc++] = ((h.rot >> i) & 1) ? (R)h.tau[i] : R(0);
@@ -1675,6 +1735,7 @@ int layer_group(const FusedPass& pass, int g, const int* pos_of, FusedParams<R>*
     }
     bool dense = false;
     for (const LayerH& h : L) dense = dense || h.u1 != 0;
+    P->gxm[g] = (uint8_t)gxm;
     return dense ? 1 : 2;
   }
 }
@@ -1793,6 +1854,7 @@ bool build_params(const FusedPass& pass, const std::vector<int>& order, FusedPar
     double* fb = sizeof(R) == 4 ? drift : nullptr;
     for (int g = 0; g < P->ngroups; ++g) {
       P->glay[g] = (uint16_t)nl;
+      P->gxm[g] = 0;
       P->gkind[g] = (uint8_t)layer_group(pass, g, pos_of, P, &nl, &nc, fb, rotform);
       if (P->gkind[g] || !fb) continue;
       const FusedGroup& grp = pass.groups[g];
@@ -1812,7 +1874,7 @@ bool build_params(const FusedPass& pass, const std::vector<int>& order, FusedPar
     P->ncoef = nc;
   } else {  // reverse sweeps run gate lists; coef[] holds gradient generators
     for (int g = 0; g <= P->ngroups; ++g) P->glay[g] = 0;
-    for (int g = 0; g < P->ngroups; ++g) P->gkind[g] = 0;
+    for (int g = 0; g < P->ngroups; ++g) P->gkind[g] = P->gxm[g] = 0;
     P->ncoef = 4 * P->ngrad;
   }
   return true;
@@ -1965,8 +2027,7 @@ sv_status run_adj_pass(void* psi, void* lam, int n, cudaStream_t st, const Fused
                     : kg == 2 ? kfused_adj<R, 2, MB>
                     : kg == 3 ? kfused_adj<R, 3, MB>
                               : kfused_adj<R, (KMAX > 3 ? 4 : 3), 2>;
-  const size_t smem =
-      1024 + 2 * (size_t)P.slice_bytes + sizeof(KahanAcc<R>) * (kFThreads / 32) * P.ngrad;
+  const size_t smem = 1024 + 2 * (size_t)P.slice_bytes + adj_tail_bytes<R>(P.ngrad, P.gop[P.ngroups]);
   static std::map<std::pair<const void*, size_t>, int> resident;
   int& res = resident[{reinterpret_cast<const void*>(kern), smem}];
   if (!res) {
