@@ -528,6 +528,111 @@ __global__ void __launch_bounds__(kDThreads, 3)
   if (threadIdx.x == 0) partials[blockIdx.x] = e;
 }
 
+// lambda = D psi for the diagonal part D = diag(d), d(x) = sum_k c_k
+// (-1)^{popcount(x & z_k)} (Sec. 3: H psi for the adjoint sweep), in one
+// streaming read and write, with the tiles of kdiag_energy.  Per thread the
+// key coefficients C_q = sum over the key's terms of c_k (-1)^{popcount(t &
+// zt_k)} are formed once; per loop trip J the signed C_q gather into v[rho]
+// and the tile's diagonal is the Walsh-Hadamard transform d_r = sum_rho
+// (-1)^{popcount(r & rho)} v_rho.  accumulate: out += D psi (a later chunk of
+// keys).  partials (or null): per block sum_x d(x) |psi_x|^2, this chunk's
+// part of <psi|D|psi>.
+template <typename R>
+__global__ void __launch_bounds__(kDThreads, 2)
+    kdiag_apply(typename Cplx2P<R>::T* __restrict__ out,
+                const typename Cplx2P<R>::T* __restrict__ psi, const __grid_constant__ DiagDev<R> D,
+                int accumulate, double* __restrict__ partials) {
+  typedef typename Cplx2P<R>::T V2;
+  constexpr bool C64 = sizeof(R) == 4;
+  constexpr int NT = C64 ? 16 : 8;  // amplitudes of a tile
+  __shared__ R cq[kDKeys][kDThreads];
+  const uint32_t t = blockIdx.x * kDThreads + threadIdx.x;
+  const uint64_t T = uint64_t(1) << D.tb;
+#pragma unroll
+  for (int q = 0; q < kDKeys; ++q) cq[q][threadIdx.x] = R(0);
+  for (int k = 0; k < D.nt; ++k) {
+    const R c = D.c[k];
+    cq[D.key[k]][threadIdx.x] += (__popc(t & D.zt[k]) & 1) ? -c : c;
+  }
+  CompSum<R> acc;
+  for (uint32_t J = 0; J < D.jmax; ++J) {
+    R v[NT];
+#pragma unroll
+    for (int r = 0; r < NT; ++r) v[r] = R(0);
+    for (int q = 0; q < D.nk; ++q) {
+      const R c = cq[q][threadIdx.x];
+      const R sv = (__popc(J & D.zj[q]) & 1) ? -c : c;
+      if (q < D.nk0) {
+        v[0] += sv;
+      } else {
+        const int rho = D.rho[q];
+#pragma unroll
+        for (int r = 1; r < NT; ++r) v[r] += (rho == r) ? sv : R(0);
+      }
+    }
+#pragma unroll
+    for (int i = 0; (1 << i) < NT; ++i)
+#pragma unroll
+      for (int r = 0; r < NT; ++r) {
+        if (r & (1 << i)) continue;
+        const R x = v[r], y = v[r | (1 << i)];
+        v[r] = x + y;
+        v[r | (1 << i)] = x - y;
+      }
+    if constexpr (C64) {
+      const float4* p4 = reinterpret_cast<const float4*>(psi);
+      float4* o4 = reinterpret_cast<float4*>(out);
+      float4 a[8], b[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) a[u] = p4[t + T * (uint64_t)(u + 8 * J)];
+      if (accumulate) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) b[u] = o4[t + T * (uint64_t)(u + 8 * J)];
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const float d0 = v[2 * u], d1 = v[2 * u + 1];
+        float4 w = make_float4(d0 * a[u].x, d0 * a[u].y, d1 * a[u].z, d1 * a[u].w);
+        if (accumulate) {
+          w.x += b[u].x;
+          w.y += b[u].y;
+          w.z += b[u].z;
+          w.w += b[u].w;
+        }
+        o4[t + T * (uint64_t)(u + 8 * J)] = w;
+        if (partials) {
+          acc.add(d0 * (a[u].x * a[u].x + a[u].y * a[u].y));
+          acc.add(d1 * (a[u].z * a[u].z + a[u].w * a[u].w));
+        }
+      }
+    } else {
+      V2 a[8], b[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) a[u] = psi[t + T * (uint64_t)(u + 8 * J)];
+      if (accumulate) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) b[u] = out[t + T * (uint64_t)(u + 8 * J)];
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        V2 w;
+        w.x = v[u] * a[u].x;
+        w.y = v[u] * a[u].y;
+        if (accumulate) {
+          w.x += b[u].x;
+          w.y += b[u].y;
+        }
+        out[t + T * (uint64_t)(u + 8 * J)] = w;
+        if (partials) acc.add(v[u] * (a[u].x * a[u].x + a[u].y * a[u].y));
+      }
+    }
+  }
+  if (partials) {
+    const double e = block_sum(acc.value());
+    if (threadIdx.x == 0) partials[blockIdx.x] = e;
+  }
+}
+
 __device__ unsigned g_pauli_status = 0;
 
 // ---- host: pass planning -------------------------------------------------------
@@ -754,6 +859,95 @@ bool lean_pass(const PauliPassDev<R>& P, XPassDev* X) {
   return true;
 }
 
+// The diagonal terms of T (x mask 0) as launches of kdiag_energy /
+// kdiag_apply: up to kDKeys keys (tile pattern rho, iteration mask zJ) and
+// kDTerms terms each, keys with rho = 0 first; tb thread bits.
+void diag_chunks(int n, bool c64, const std::vector<TermH>& T, int tb,
+                 std::vector<DiagDev<float>>* dfs, std::vector<DiagDev<double>>* dds) {
+  std::vector<DiagDev<double>> chunks;  // built in fp64, converted below
+  DiagDev<double> cur{};
+  std::map<std::pair<int, uint32_t>, int> keys;
+  auto flush = [&]() {
+    if (cur.nt == 0) return;
+    // keys with rho = 0 first
+    std::vector<int> order;
+    for (int q = 0; q < cur.nk; ++q)
+      if (cur.rho[q] == 0) order.push_back(q);
+    for (int q = 0; q < cur.nk; ++q)
+      if (cur.rho[q] != 0) order.push_back(q);
+    DiagDev<double> d = cur;
+    std::vector<int> pos(cur.nk);
+    for (int i = 0; i < cur.nk; ++i) {
+      pos[order[i]] = i;
+      d.rho[i] = cur.rho[order[i]];
+      d.zj[i] = cur.zj[order[i]];
+    }
+    d.nk0 = 0;
+    while (d.nk0 < d.nk && d.rho[d.nk0] == 0) ++d.nk0;
+    for (int k = 0; k < d.nt; ++k) d.key[k] = (uint8_t)pos[cur.key[k]];
+    chunks.push_back(d);
+    cur = DiagDev<double>{};
+    keys.clear();
+  };
+  for (int k = 0; k < (int)T.size(); ++k) {
+    if (T[k].xm != 0) continue;
+    const uint64_t zm = T[k].zm;
+    int rho;
+    uint32_t zt, zj;
+    if (c64) {
+      rho = (int)((zm & 1) | (((zm >> (tb + 1)) & 7) << 1));
+      zt = (uint32_t)((zm >> 1) & ((uint64_t(1) << tb) - 1));
+      zj = (uint32_t)(zm >> (tb + 4));
+    } else {
+      rho = (int)((zm >> tb) & 7);
+      zt = (uint32_t)(zm & ((uint64_t(1) << tb) - 1));
+      zj = (uint32_t)(zm >> (tb + 3));
+    }
+    const std::pair<int, uint32_t> kk{rho, zj};
+    if (cur.nt == kDTerms || (!keys.count(kk) && cur.nk == kDKeys)) flush();
+    auto it = keys.find(kk);
+    int q;
+    if (it == keys.end()) {
+      q = cur.nk++;
+      cur.rho[q] = (uint8_t)rho;
+      cur.zj[q] = zj;
+      keys[kk] = q;
+    } else {
+      q = it->second;
+    }
+    cur.key[cur.nt] = (uint8_t)q;
+    cur.zt[cur.nt] = zt;
+    cur.c[cur.nt] = T[k].cre;
+    ++cur.nt;
+  }
+  flush();
+  const uint32_t jmax = (uint32_t)(uint64_t(1) << (n - (c64 ? 1 : 0) - 3 - tb));
+  for (DiagDev<double>& d : chunks) {
+    d.tb = tb;
+    d.jmax = jmax;
+    if (c64) {
+      DiagDev<float> f{};
+      f.nk = d.nk;
+      f.nk0 = d.nk0;
+      for (int q = 0; q < kDKeys; ++q) {
+        f.rho[q] = d.rho[q];
+        f.zj[q] = d.zj[q];
+      }
+      f.nt = d.nt;
+      for (int k = 0; k < kDTerms; ++k) {
+        f.key[k] = d.key[k];
+        f.zt[k] = d.zt[k];
+        f.c[k] = (float)d.c[k];
+      }
+      f.tb = d.tb;
+      f.jmax = d.jmax;
+      dfs->push_back(f);
+    } else {
+      dds->push_back(d);
+    }
+  }
+}
+
 }  // namespace
 
 // <psi|H|psi> of the state into the device double dst by staged passes:
@@ -778,94 +972,9 @@ sv_status expval_staged(sv_state s, const sv_pauli_sum* H, double* dst) {
   // thread bits: enough blocks for many waves over the SMs (2^20 threads at
   // n >= 27), at least 8 loop trips per thread where the state allows
   const int tb = std::min(20, std::max(8, s->n - (c64 ? 4 : 3) - 3));
-  const int tile_bits = c64 ? 4 : 3;
   std::vector<DiagDev<float>> dfs;
   std::vector<DiagDev<double>> dds;
-  {
-    std::vector<DiagDev<double>> chunks;  // built in fp64, converted below
-    DiagDev<double> cur{};
-    std::map<std::pair<int, uint32_t>, int> keys;
-    auto flush = [&]() {
-      if (cur.nt == 0) return;
-      // keys with rho = 0 first
-      std::vector<int> order;
-      for (int q = 0; q < cur.nk; ++q)
-        if (cur.rho[q] == 0) order.push_back(q);
-      for (int q = 0; q < cur.nk; ++q)
-        if (cur.rho[q] != 0) order.push_back(q);
-      DiagDev<double> d = cur;
-      std::vector<int> pos(cur.nk);
-      for (int i = 0; i < cur.nk; ++i) {
-        pos[order[i]] = i;
-        d.rho[i] = cur.rho[order[i]];
-        d.zj[i] = cur.zj[order[i]];
-      }
-      d.nk0 = 0;
-      while (d.nk0 < d.nk && d.rho[d.nk0] == 0) ++d.nk0;
-      for (int k = 0; k < d.nt; ++k) d.key[k] = (uint8_t)pos[cur.key[k]];
-      chunks.push_back(d);
-      cur = DiagDev<double>{};
-      keys.clear();
-    };
-    for (int k = 0; k < H->n_terms; ++k) {
-      if (T[k].xm != 0) continue;
-      const uint64_t zm = T[k].zm;
-      int rho;
-      uint32_t zt, zj;
-      if (c64) {
-        rho = (int)((zm & 1) | (((zm >> (tb + 1)) & 7) << 1));
-        zt = (uint32_t)((zm >> 1) & ((uint64_t(1) << tb) - 1));
-        zj = (uint32_t)(zm >> (tb + 4));
-      } else {
-        rho = (int)((zm >> tb) & 7);
-        zt = (uint32_t)(zm & ((uint64_t(1) << tb) - 1));
-        zj = (uint32_t)(zm >> (tb + 3));
-      }
-      const std::pair<int, uint32_t> kk{rho, zj};
-      if (cur.nt == kDTerms || (!keys.count(kk) && cur.nk == kDKeys)) flush();
-      auto it = keys.find(kk);
-      int q;
-      if (it == keys.end()) {
-        q = cur.nk++;
-        cur.rho[q] = (uint8_t)rho;
-        cur.zj[q] = zj;
-        keys[kk] = q;
-      } else {
-        q = it->second;
-      }
-      cur.key[cur.nt] = (uint8_t)q;
-      cur.zt[cur.nt] = zt;
-      cur.c[cur.nt] = T[k].cre;
-      ++cur.nt;
-    }
-    flush();
-    const uint32_t jmax = (uint32_t)(uint64_t(1) << (s->n - (c64 ? 1 : 0) - 3 - tb));
-    for (DiagDev<double>& d : chunks) {
-      d.tb = tb;
-      d.jmax = jmax;
-      if (c64) {
-        DiagDev<float> f{};
-        f.nk = d.nk;
-        f.nk0 = d.nk0;
-        for (int q = 0; q < kDKeys; ++q) {
-          f.rho[q] = d.rho[q];
-          f.zj[q] = d.zj[q];
-        }
-        f.nt = d.nt;
-        for (int k = 0; k < kDTerms; ++k) {
-          f.key[k] = d.key[k];
-          f.zt[k] = d.zt[k];
-          f.c[k] = (float)d.c[k];
-        }
-        f.tb = d.tb;
-        f.jmax = d.jmax;
-        dfs.push_back(f);
-      } else {
-        dds.push_back(d);
-      }
-    }
-    (void)tile_bits;
-  }
+  diag_chunks(s->n, c64, T, tb, &dfs, &dds);
   const size_t ndiag = c64 ? dfs.size() : dds.size();
   // off-diagonal terms: staged passes
   std::vector<TermH> Toff;
@@ -998,6 +1107,70 @@ sv_status expval_staged(sv_state s, const sv_pauli_sum* H, double* dst) {
     total += np1;
   }
   return launch_finish(s->partials, total, 1, dst, s->stream, false);
+}
+
+// lambda = H psi into out, and <psi|H|psi> into the device double energy_dst
+// if it is not null: the diagonal terms by the streaming kdiag_apply, the
+// other terms by the per-amplitude kernel adding on top (its last launch
+// forms the energy of the whole lambda).  SV_ERR_UNSUPPORTED (nothing
+// launched) for states under 16 qubits or sums without diagonal terms.
+sv_status apply_pauli_staged(void* out, const void* in, sv_state s, const sv_pauli_sum* H,
+                             double* energy_dst) {
+  const bool c64 = s->dt == SV_C64;
+  if (s->n < 16 || H->n_terms == 0) return SV_ERR_UNSUPPORTED;
+  std::vector<TermH> T;
+  std::vector<uint64_t> rxm, rzm;
+  std::vector<double> rcf;
+  for (int k = 0; k < H->n_terms; ++k) {
+    if (H->xmask[k] == 0) {
+      T.push_back({0, H->zmask[k], H->coeff[k], 0.0});
+    } else {
+      rxm.push_back(H->xmask[k]);
+      rzm.push_back(H->zmask[k]);
+      rcf.push_back(H->coeff[k]);
+    }
+  }
+  if (T.empty()) return SV_ERR_UNSUPPORTED;
+  const int tb = std::min(20, std::max(8, s->n - (c64 ? 4 : 3) - 3));
+  std::vector<DiagDev<float>> dfs;
+  std::vector<DiagDev<double>> dds;
+  diag_chunks(s->n, c64, T, tb, &dfs, &dds);
+  const size_t ndiag = c64 ? dfs.size() : dds.size();
+  std::vector<PauliDev> chunks;
+  if (!rxm.empty()) {
+    sv_pauli_sum sub{(int32_t)rxm.size(), rxm.data(), rzm.data(), rcf.data()};
+    pauli_chunks(&sub, &chunks);
+  }
+  const unsigned dgrid = (unsigned)((uint64_t(1) << tb) / kDThreads);
+  const bool diag_energy = energy_dst && chunks.empty();
+  const size_t need = diag_energy ? ndiag * dgrid : energy_dst ? (size_t)kRedMaxBlocks : 0;
+  sv_status st = need ? ensure_partials(s, need) : SV_OK;
+  if (st) return st;
+  int total = 0;
+  for (size_t i = 0; i < ndiag; ++i) {
+    ProfScope prof(s->stream, c64 ? "kdiag_apply_c64" : "kdiag_apply_c128");
+    double* part = diag_energy ? s->partials + total : nullptr;
+    if (c64)
+      kdiag_apply<float><<<dgrid, kDThreads, 0, s->stream>>>(
+          (float2*)out, (const float2*)in, dfs[i], i > 0 ? 1 : 0, part);
+    else
+      kdiag_apply<double><<<dgrid, kDThreads, 0, s->stream>>>(
+          (double2*)out, (const double2*)in, dds[i], i > 0 ? 1 : 0, part);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    st = check_launch("diagonal apply kernel");
+    if (st) return st;
+    if (diag_energy) total += (int)dgrid;
+  }
+  int np = 0;
+  for (size_t i = 0; i < chunks.size(); ++i) {
+    const bool last = i + 1 == chunks.size();
+    st = launch_apply_pauli(out, in, s->dt, s->n, s->stream, chunks[i], true,
+                            (last && energy_dst) ? s->partials : nullptr, &np);
+    if (st) return st;
+  }
+  if (energy_dst)
+    return launch_finish(s->partials, diag_energy ? total : np, 1, energy_dst, s->stream, false);
+  return SV_OK;
 }
 
 unsigned take_pauli_status() {

@@ -784,6 +784,10 @@ sv_status sv_expval_async(sv_state s, const sv_pauli_sum* H, double* dev_out) {
 
 static sv_status apply_pauli_into(void* out, const void* in, sv_state s, const sv_pauli_sum* H,
                                   double* energy_dst) {
+  {
+    const sv_status st = apply_pauli_staged(out, in, s, H, energy_dst);
+    if (st != SV_ERR_UNSUPPORTED) return st;
+  }
   std::vector<PauliDev> chunks;
   pauli_chunks(H, &chunks);
   if (chunks.empty()) {
@@ -814,6 +818,10 @@ sv_status sv_apply_pauli_sum(sv_state out, sv_state in, const sv_pauli_sum* H) {
     return SV_ERR_INVALID;
   }
   if (!valid_pauli(in, H)) return SV_ERR_INVALID;
+  {
+    const sv_status st = apply_pauli_staged(out->data, in->data, in, H, nullptr);
+    if (st != SV_ERR_UNSUPPORTED) return st;
+  }
   std::vector<PauliDev> chunks;
   pauli_chunks(H, &chunks);
   if (chunks.empty()) {

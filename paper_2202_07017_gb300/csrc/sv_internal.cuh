@@ -178,6 +178,11 @@ sv_status launch_apply_pauli(void* out, const void* in, sv_dtype dt, int n, cuda
 // <psi|H|psi> into the device double dst by staged passes (pauli_kernels.cu);
 // SV_ERR_UNSUPPORTED with nothing launched when passes do not apply.
 sv_status expval_staged(sv_state s, const sv_pauli_sum* H, double* dst);
+// lambda = H psi (and <psi|H|psi> into energy_dst if not null) with the
+// diagonal terms streamed; SV_ERR_UNSUPPORTED (nothing launched) where it
+// does not apply (under 16 qubits, no diagonal term).
+sv_status apply_pauli_staged(void* out, const void* in, sv_state s, const sv_pauli_sum* H,
+                             double* energy_dst);
 // Reads and clears the Pauli-pass status word (kWaitTimeout).
 unsigned take_pauli_status();
 // dst[j] = sum_{i<count} src[j * count + i] for j < slots (fixed order).

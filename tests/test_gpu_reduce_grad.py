@@ -87,6 +87,49 @@ def test_apply_pauli_sum(dtype):
     assert max_err(got, ref) <= TOL[dtype] * sum(abs(c) for c, _ in terms)
 
 
+def _pauli_apply_ref(psi, n, terms):
+    P = {"X": np.array([[0, 1], [1, 0]]), "Y": np.array([[0, -1j], [1j, 0]]),
+         "Z": np.array([[1, 0], [0, -1]])}
+    ref = np.zeros_like(psi)
+    for c, ops in terms:
+        phi = psi.copy()
+        for q, L in ops:
+            phi = oracle.apply_gate(phi, n, [q], [], P[L])
+        ref += c * phi
+    return ref
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("case", ["sum_z", "many_keys", "mixed"])
+def test_apply_pauli_sum_streamed_diagonal(dtype, case):
+    """H psi at n = 19 with the diagonal terms streamed (one launch per 16
+    keys, later launches adding on top) and any other terms added by the
+    per-amplitude kernel: against the oracle's term-by-term sum."""
+    from paper_2202_07017_gb300 import State, sv_apply_pauli_sum
+    n = 19
+    rng = W.SplitMix64(31)
+    if case == "sum_z":
+        terms = W.sum_z(n) + [(0.25, ())]
+    elif case == "many_keys":  # Z strings on many iteration-bit patterns: several launches
+        terms = []
+        for _ in range(40):
+            qs = sorted({int(rng.next() % n) for _ in range(1 + rng.next() % 3)})
+            terms.append((2 * rng.uniform() - 1, tuple((q, "Z") for q in qs)))
+    else:
+        terms = W.tfim(n) + W.random_pauli_sum(n, 6, 32)
+    psi = rounded(W.random_state(n, 33), dtype)
+    a = _state(n, dtype, psi)
+    b = State(n, dtype)
+    try:
+        sv_apply_pauli_sum(b.h, a.h, terms)
+        got = b.numpy()
+    finally:
+        a.close()
+        b.close()
+    ref = _pauli_apply_ref(psi, n, terms)
+    assert max_err(got, ref) <= TOL[dtype] * sum(abs(c) for c, _ in terms)
+
+
 def _adjoint(c, theta, terms, dtype, psi0=None, checkpoints=None):
     from paper_2202_07017_gb300 import State
     st = State(c.n_qubits, dtype)
