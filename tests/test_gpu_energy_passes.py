@@ -5,7 +5,8 @@ staged passes (the state read in shared-memory slices, terms with x bits
 inside one tile pairing registers); terms that fit no pass fall back to the
 per-amplitude kernel.  Against the oracle's <psi|H|psi> on random
 states and Pauli sums of every shape, and against the closed form of a
-product state at n = 30 (transverse-field Ising chain: three passes)."""
+product state at n = 30 and n = 33 (transverse-field Ising chain: three and
+four passes)."""
 import math
 
 import numpy as np
@@ -101,13 +102,14 @@ def test_single_x_terms_take_the_lean_pass(dtype):
     assert abs(e - oracle.expval(psi, terms, n)) <= TOL[dtype] * sum(abs(c) for c, _ in terms)
 
 
-def test_tfim_and_sum_z_on_a_product_state_n30():
-    """RY(a_q) on every qubit of |0..0> (complex64, n = 30): <Z_q> = cos a_q
-    and <X_q> = sin a_q exactly, so <sum Z> and the transverse-field Ising
-    energy have closed forms; the chain's X terms need three passes."""
+@pytest.mark.parametrize("n,x_passes", [(30, 3), (33, 4)])
+def test_tfim_and_sum_z_on_a_product_state(n, x_passes):
+    """RY(a_q) on every qubit of |0..0> (complex64, n = 30, and n = 33 with
+    64-bit amplitude indices): <Z_q> = cos a_q and <X_q> = sin a_q exactly, so
+    <sum Z> and the transverse-field Ising energy have closed forms; the
+    chain's X terms need three passes at n = 30 and four at n = 33."""
     from paper_2202_07017_gb300 import State, sv_profile_start, sv_profile_stop
-    n = 30
-    a = np.array([0.1 + 0.09 * q for q in range(n)])
+    a = np.array([0.1 + 0.9 * q / n for q in range(n)])
     c = W.Circuit(n, [W.Gate("RY", (q,), (), q) for q in range(n)], n)
     st = State(n, "c64").init(0)
     try:
@@ -122,7 +124,7 @@ def test_tfim_and_sum_z_on_a_product_state_n30():
     assert abs(ez - cz.sum()) <= TOL["c64"] * n
     ref = float(np.sum(cz[:-1] * cz[1:]) + 0.7 * sx.sum())
     assert abs(et - ref) <= TOL["c64"] * (n - 1 + 0.7 * n)
-    # diagonal terms: one streaming read per call; the chain's X terms: three
+    # diagonal terms: one streaming read per call; the chain's X terms:
     # passes of the single-X kernel
-    assert prof["kdiag_energy_c64"][0] == 2 and prof["kpauli_xbits_c64"][0] == 3, prof
+    assert prof["kdiag_energy_c64"][0] == 2 and prof["kpauli_xbits_c64"][0] == x_passes, prof
     assert "kexpval" not in prof, prof
