@@ -416,7 +416,8 @@ def _fused_grad_times(torch, c, theta, pc, pp, ck, reps):
     """Forward (init + fused circuit, k = 4 + energy) and forward + gradient
     through sv_grad_fused (fused forward and fused reverse sweep)."""
     from paper_2202_07017_gb300 import (C64, sv_alloc, sv_apply_circuit, sv_expval, sv_free,
-                                        sv_grad_fused, sv_init)
+                                        sv_grad_fused, sv_init, sv_profile_start,
+                                        sv_profile_stop)
     h = sv_alloc(c.n_qubits, C64, torch.cuda.current_stream().cuda_stream)
     try:
         sv_init(h, 0)
@@ -430,15 +431,21 @@ def _fused_grad_times(torch, c, theta, pc, pp, ck, reps):
             sv_expval(h, pp)
             t1 = time.perf_counter()
             sv_init(h, 0)
+            sv_profile_start()
             e, g = sv_grad_fused(h, pc, theta, pp, ck, 4)
             t2 = time.perf_counter()
+            prof = sv_profile_stop()
             fw.append(t1 - t0)
             fg.append(t2 - t1)
     finally:
         sv_free(h)
     f, t = float(np.median(fw)), float(np.median(fg))
+    cnt, ms = prof.get("kfused_adj_c64", (0, 0.0))
+    # a reverse pass reads and writes psi and lambda once: 4 * 8 * 2^n bytes
+    adj = ({"passes": cnt, "ms": ms, "achieved_gbs": cnt * 32.0 * 2 ** c.n_qubits / (ms / 1e3) / 1e9}
+           if cnt else None)
     return {"forward_s": f, "forward_plus_grad_s": t, "grad_over_forward": (t - f) / f,
-            "energy": e}
+            "energy": e, "reverse_passes": adj}
 
 
 def qaoa_maxcut(torch, n=24, p=4, reps=3, n_check=16, check=True):
@@ -645,7 +652,7 @@ def batch_solves(torch, reps=5, tune=1):
     adjoint gradients, complex64: one persistent launch per step, replayed
     from a CUDA graph, tile chosen by the autotuner."""
     import workloads as W
-    from paper_2202_07017_gb300 import Batch
+    from paper_2202_07017_gb300 import Batch, sv_batch_plan
     hea14, _ = W.hea(14, 10, 1003)
     mixed = W.mixed_batch(1024, 1003)
     circuits = [hea14] + [m[0] for m in mixed]
@@ -670,13 +677,27 @@ def batch_solves(torch, reps=5, tune=1):
     ev[1].record(st)
     torch.cuda.synchronize()
     secs = ev[0].elapsed_time(ev[1]) / 1e3 / reps
+    # state traffic of the register groups (each group reads and writes the
+    # item's states once: psi forward, psi and lambda backward, plus lambda =
+    # H psi), against the nominal shared-memory bandwidth of the SMs
+    groups = sv_batch_plan(circuits, hams, b.k)
+    nq = [c.n_qubits for c in circuits]
+    state_bytes = 0.0
+    for it in items:
+        amp = 8.0 * 2 ** nq[it]
+        state_bytes += amp * (2 * groups[it] + 2 + 4 * groups[it])
+    smem_peak = 152 * 128 * 2.07e9 / 1e9  # GB/s: 128 bytes per clock per SM at 2070 MHz
     out = {"workload": "4096 x HEA n=14 L=10 + 1024 mixed HEA (n 8..16, L 5..15), TFIM, "
                        "energy + adjoint gradient, complex64, one persistent launch (CUDA graph)",
            "items": len(items), "ms_per_launch": 1e3 * secs, "items_per_s": len(items) / secs,
            "gradients_per_s": len(theta) / secs,
            "tile": {"k": b.k, "threads": b.threads, "blocks": b.blocks, "cluster": b.cluster,
                     "smem_states": b.smem_states},
-           "create_and_tune_s": t_create}
+           "create_and_tune_s": t_create,
+           "state_traffic": {"bytes_per_launch": state_bytes,
+                             "achieved_gbs": state_bytes / secs / 1e9,
+                             "smem_peak_gbs_nominal": smem_peak,
+                             "frac": state_bytes / secs / 1e9 / smem_peak}}
     b.close()
     return out
 
@@ -708,10 +729,11 @@ def sampling(torch, h, n, shots=1 << 20):
 
 
 def reductions(torch, h, n, reps=3):
-    """Norm, sum-Z energy (diagonal terms only: one staged pass) and TFIM
-    energy (three passes: the X terms' bits in three staged sets) of the
-    n = 30 state already in `h` (the QFT output): per-kernel times from the
-    library's CUDA events, GB/s of each pass (one read of the state,
+    """Norm, sum-Z energy (diagonal terms only: one streaming read,
+    kdiag_energy) and TFIM energy (its diagonal terms in one streaming read,
+    its X terms in three staged passes of kpauli_xbits) of the n = 30 state
+    already in `h` (the QFT output): per-kernel times from the library's CUDA
+    events, GB/s of each launch of the named kernel (one read of the state,
     8 * 2^n bytes) and the call's time against a single read."""
     import workloads as W
     from paper_2202_07017_gb300 import sv_expval, sv_norm, sv_profile_start, sv_profile_stop
@@ -719,8 +741,8 @@ def reductions(torch, h, n, reps=3):
            "alg_bytes_per_launch": 8 * 2 ** n}
     peak, _ = hbm_peak()
     cases = (("norm", "knorm", lambda: sv_norm(h)),
-             ("energy_sum_z", "kpauli_energy_c64", lambda: sv_expval(h, W.sum_z(n))),
-             ("energy_tfim", "kpauli_energy_c64", lambda: sv_expval(h, W.tfim(n))))
+             ("energy_sum_z", "kdiag_energy_c64", lambda: sv_expval(h, W.sum_z(n))),
+             ("energy_tfim", "kpauli_xbits_c64", lambda: sv_expval(h, W.tfim(n))))
     for name, kern, fn in cases:
         fn()
         sv_profile_start()
@@ -959,6 +981,20 @@ def main():
                 "fma_pipe": {"achieved_tops": fused["fma_tops"],
                              "peak_tops": alu["fp32_ffma_tflops"] / 2,
                              "frac": fused["fma_tops"] / (alu["fp32_ffma_tflops"] / 2)}}
+        if adj28 is not None and adj28["fused"].get("reverse_passes"):
+            rp = adj28["fused"]["reverse_passes"]
+            rooflines["kfused_adj_c64 (layered n=%d)" % args.adj_n] = {
+                "bound": "hbm", "achieved_gbs": rp["achieved_gbs"], "peak_gbs": peak,
+                "frac": rp["achieved_gbs"] / peak}
+        if batch is not None:
+            rooflines["kbatch (C3)"] = {"bound": "shared memory (nominal)",
+                                        **batch["state_traffic"]}
+        for key in ("energy_sum_z", "energy_tfim"):
+            r = red[key]
+            if r.get("pass_gbs"):
+                rooflines[f"{r['kernel']} ({key[7:]} n={n})"] = {
+                    "bound": "hbm", "achieved_gbs": r["pass_gbs"], "peak_gbs": peak,
+                    "frac": r["pass_frac"], "launches_per_call": r["passes"]}
         if c128 is not None:
             for name, kk in c128["kernels"].items():
                 if "fp64_tinstr_per_s" in kk:
