@@ -847,10 +847,10 @@ __global__ void __launch_bounds__(kFThreads, MINB)
         run_layers<KGF, R, false, true>(
             sm, P.m, P.gbits[g], lsm, P.glay[g], P.glay[g + 1], csm,
             mix32(P.dseed ^ (uint32_t)blk ^ ((uint32_t)(blk >> 32) + (uint32_t)g * 0x85ebca6bu)));
-      else if (MODE == 3 && KGF == 4 && sizeof(R) == 4 && P.m == 13 && P.gkind[g] == 2)
-        run_layers_x2<KGF, R>(sm, P.gbits[g], lsm, P.glay[g], P.glay[g + 1], csm,
-                              P.gxm[g]);  // two sub-blocks per thread (complex64 slices)
-      else if (MODE == 3)
+      else if (MODE == 3 && KGF == 4 && sizeof(R) == 4 && P.m == 13 && P.gkind[g] == 2) {
+        if constexpr (sizeof(R) == 4)  // two sub-blocks per thread (complex64 slices)
+          run_layers_x2<KGF, R>(sm, P.gbits[g], lsm, P.glay[g], P.glay[g + 1], csm, P.gxm[g]);
+      } else if (MODE == 3)
         run_layers<KGF, R, false>(sm, P.m, P.gbits[g], lsm, P.glay[g], P.glay[g + 1], csm, 0,
                                   P.gxm[g]);
       else if (MODE == 1 && P.gkind[g])
