@@ -558,54 +558,46 @@ __device__ __forceinline__ void run_layers(typename Cplx2<R>::T* sm, int m, cons
 // Two sub-blocks per thread (s and s + kFThreads: a slice of 2^13 amplitudes
 // in 4-qubit groups) through one layer program in rotation form (no dense
 // 2x2: the registers of two tiles fit beside the rotations, not beside the
-// 2x2 coefficients) together: each layer's
-// coefficients are read once for both, and the two tiles' operations are
-// independent, so a warp has twice the arithmetic in flight between the
-// dependent steps of one tile (rotation on bit 0, then bit 1, ..., then the
-// diagonal).
-template <int KG, int B, bool F, typename R>
-__device__ __forceinline__ void rot_bit2(R t, R (&re)[2][1 << KG], R (&im)[2][1 << KG]) {
+// 2x2 coefficients) together: each layer's coefficients are read once for
+// both, and the two tiles' operations are independent, so a warp has twice
+// the arithmetic in flight between the dependent steps of one tile
+// (rotation on bit 0, then bit 1, ..., then the diagonal).
+// The registers hold each amplitude as a (re, im) pair, so the rotation's
+// four FMAs per register pair - every one scaling both parts of an amplitude
+// by the same t - issue as two paired fp32 FMAs (fma.rn.f32x2): half the
+// instructions for the same arithmetic.  Complex64 only.
+template <int KG, int B>
+__device__ __forceinline__ void rot_bit2p(float t, float2 (&v)[2][1 << KG]) {
+  const float2 tp = make_float2(t, t), tn = make_float2(-t, -t);
 #pragma unroll
   for (int r = 0; r < (1 << KG); ++r) {
     if (r & (1 << B)) continue;
     const int r1 = r | (1 << B);
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
-      const R a = re[u][r], b = im[u][r], c = re[u][r1], d = im[u][r1];
-      if constexpr (F) {
-        re[u][r] = fma(t, a, -c);
-        im[u][r] = fma(t, b, -d);
-        re[u][r1] = fma(t, c, a);
-        im[u][r1] = fma(t, d, b);
-      } else {
-        re[u][r] = fma(-t, c, a);
-        im[u][r] = fma(-t, d, b);
-        re[u][r1] = fma(t, a, c);
-        im[u][r1] = fma(t, b, d);
-      }
+      const float2 a = v[u][r], c = v[u][r1];
+      v[u][r] = __ffma2_rn(tn, c, a);   // a - t c
+      v[u][r1] = __ffma2_rn(tp, a, c);  // t a + c
     }
   }
 }
 
-template <int KG, typename R>
-__device__ __forceinline__ void rot_bit2_at(int i, const R (&tv)[4], R (&re)[2][1 << KG],
-                                            R (&im)[2][1 << KG]) {
-  if (i == 0) rot_bit2<KG, 0, false, R>(tv[0], re, im);
-  if constexpr (KG > 1) if (i == 1) rot_bit2<KG, (KG > 1 ? 1 : 0), false, R>(tv[KG > 1 ? 1 : 0], re, im);
-  if constexpr (KG > 2) if (i == 2) rot_bit2<KG, (KG > 2 ? 2 : 0), false, R>(tv[KG > 2 ? 2 : 0], re, im);
-  if constexpr (KG > 3) if (i == 3) rot_bit2<KG, (KG > 3 ? 3 : 0), false, R>(tv[KG > 3 ? 3 : 0], re, im);
+template <int KG>
+__device__ __forceinline__ void rot_bit2p_at(int i, const float (&tv)[4], float2 (&v)[2][1 << KG]) {
+  if (i == 0) rot_bit2p<KG, 0>(tv[0], v);
+  if constexpr (KG > 1) if (i == 1) rot_bit2p<KG, (KG > 1 ? 1 : 0)>(tv[KG > 1 ? 1 : 0], v);
+  if constexpr (KG > 2) if (i == 2) rot_bit2p<KG, (KG > 2 ? 2 : 0)>(tv[KG > 2 ? 2 : 0], v);
+  if constexpr (KG > 3) if (i == 3) rot_bit2p<KG, (KG > 3 ? 3 : 0)>(tv[KG > 3 ? 3 : 0], v);
 }
 
-template <int KG, typename R>
-__device__ __forceinline__ void run_layers_x2(typename Cplx2<R>::T* sm, const uint8_t* gb,
-                                              const FLayerDev* lay, int l0, int l1,
-                                              const R* coef, int xm) {
-  typedef typename Cplx2<R>::T V2;
+template <int KG>
+__device__ __forceinline__ void run_layers_x2(float2* sm, const uint8_t* gb, const FLayerDev* lay,
+                                              int l0, int l1, const float* coef, int xm) {
   constexpr int D = 1 << KG;
   int sw[KG], lm[KG];
 #pragma unroll
   for (int i = 0; i < KG; ++i) {
-    sw[i] = swz<R>(1 << gb[i]);
+    sw[i] = swz<float>(1 << gb[i]);
     lm[i] = (1 << gb[i]) - 1;
   }
   int sb[2];
@@ -614,52 +606,45 @@ __device__ __forceinline__ void run_layers_x2(typename Cplx2<R>::T* sm, const ui
     int b = threadIdx.x + u * kFThreads;
 #pragma unroll
     for (int i = 0; i < KG; ++i) b = ((b & ~lm[i]) << 1) | (b & lm[i]);
-    sb[u] = swz<R>(b);
+    sb[u] = swz<float>(b);
   }
-  R re[2][D], im[2][D];
+  float2 v[2][D];
 #pragma unroll
   for (int r = 0; r < D; ++r)
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const V2 v = sm[sb[u] ^ reg_off<KG>(r, sw)];
-      re[u][r] = v.x;
-      im[u][r] = v.y;
-    }
+    for (int u = 0; u < 2; ++u) v[u][r] = sm[sb[u] ^ reg_off<KG>(r, sw)];
   for (int l = l0; l < l1; ++l) {
     const FLayerDev L = lay[l];
-    const R* c = coef + L.off;
+    const float* c = coef + L.off;
     if (L.rot) {
-      R tv[4];
-      load_tau4<R>(c, tv);
+      float tv[4];
+      load_tau4<float>(c, tv);
       if (L.rot == (1 << KG) - 1) {  // every bit: one straight-line block
 #pragma unroll
-        for (int i = 0; i < KG; ++i) rot_bit2_at<KG, R>(i, tv, re, im);
+        for (int i = 0; i < KG; ++i) rot_bit2p_at<KG>(i, tv, v);
       } else {
 #pragma unroll
         for (int i = 0; i < KG; ++i)
-          if (L.rot & (1 << i)) rot_bit2_at<KG, R>(i, tv, re, im);
+          if (L.rot & (1 << i)) rot_bit2p_at<KG>(i, tv, v);
       }
       c += 4;
     }
     if (L.dk == 1) {
 #pragma unroll
       for (int r = 0; r < D; ++r) {
-        const R d = c[r];
+        const float2 d = make_float2(c[r], c[r]);
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          re[u][r] *= d;
-          im[u][r] *= d;
-        }
+        for (int u = 0; u < 2; ++u) v[u][r] = __fmul2_rn(d, v[u][r]);
       }
     } else if (L.dk == 2) {
 #pragma unroll
       for (int r = 0; r < D; ++r) {
-        const V2 d = *reinterpret_cast<const V2*>(c + 2 * r);
+        const float2 d = *reinterpret_cast<const float2*>(c + 2 * r);
+        const float2 dr = make_float2(d.x, d.x), di = make_float2(-d.y, d.y);
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const R xr = re[u][r], xi = im[u][r];
-          re[u][r] = d.x * xr - d.y * xi;
-          im[u][r] = d.x * xi + d.y * xr;
+        for (int u = 0; u < 2; ++u) {  // (dr xr - di xi, dr xi + di xr)
+          const float2 x = v[u][r];
+          v[u][r] = __ffma2_rn(di, make_float2(x.y, x.x), __fmul2_rn(dr, x));
         }
       }
     }
@@ -670,10 +655,7 @@ __device__ __forceinline__ void run_layers_x2(typename Cplx2<R>::T* sm, const ui
     for (int u = 0; u < 2; ++u) {
       int sbr = sb[u] ^ reg_off<KG>(xm, sw);
       asm volatile("mov.b32 %0, %1;" : "=r"(sbr) : "r"(sbr));  // store addresses recomputed
-      V2 v;
-      v.x = re[u][r];
-      v.y = im[u][r];
-      sm[sbr ^ reg_off<KG>(r, sw)] = v;
+      sm[sbr ^ reg_off<KG>(r, sw)] = v[u][r];
     }
 }
 
@@ -849,7 +831,7 @@ __global__ void __launch_bounds__(kFThreads, MINB)
             mix32(P.dseed ^ (uint32_t)blk ^ ((uint32_t)(blk >> 32) + (uint32_t)g * 0x85ebca6bu)));
       else if (MODE == 3 && KGF == 4 && sizeof(R) == 4 && P.m == 13 && P.gkind[g] == 2) {
         if constexpr (sizeof(R) == 4)  // two sub-blocks per thread (complex64 slices)
-          run_layers_x2<KGF, R>(sm, P.gbits[g], lsm, P.glay[g], P.glay[g + 1], csm, P.gxm[g]);
+          run_layers_x2<KGF>(sm, P.gbits[g], lsm, P.glay[g], P.glay[g + 1], csm, P.gxm[g]);
       } else if (MODE == 3)
         run_layers<KGF, R, false>(sm, P.m, P.gbits[g], lsm, P.glay[g], P.glay[g + 1], csm, 0,
                                   P.gxm[g]);
