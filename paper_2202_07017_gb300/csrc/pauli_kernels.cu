@@ -332,18 +332,25 @@ __global__ void __launch_bounds__(kPThreads, 1)
                  double* __restrict__ partials, unsigned* __restrict__ status) {
   typedef typename Cplx2P<R>::T V2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t bars[kXBuf];
+  __shared__ __align__(8) uint64_t bars[kXBuf];   // full: the slice's bytes have landed
+  __shared__ __align__(8) uint64_t ebars[kXBuf];  // empty: every warp is done with it
+  constexpr int kWarps = kPThreads / 32;
   const uint32_t raw = smem_addr(smem_raw);
   const uint32_t sbuf0 = (raw + 1023u) & ~1023u;  // slice bytes: multiples of 1024
   const uint32_t sbytes = P.geo.slice_bytes;
   const int lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    for (int j = 0; j < kXBuf; ++j) mbar_init(smem_addr(&bars[j]), 1);
+    for (int j = 0; j < kXBuf; ++j) {
+      mbar_init(smem_addr(&bars[j]), 1);
+      mbar_init(smem_addr(&ebars[j]), kWarps);
+    }
     fence_proxy_async_smem();
   }
   __syncthreads();
   CompSum<R> acc[kPG * kXGroups];
-  uint32_t parity = 0, pending = 0;  // bit j: buffer j
+  // bit j: buffer j.  used: filled before (its refill waits until every warp
+  // released the previous fill); eparity: phase of its empty barrier
+  uint32_t parity = 0, pending = 0, used = 0, eparity = 0;
   const int nsub = 1 << (P.geo.m - kPG);
   for (int j = 0; j < kXBuf - 1; ++j) {
     const uint64_t b = blockIdx.x + (uint64_t)j * gridDim.x;
@@ -351,24 +358,35 @@ __global__ void __launch_bounds__(kPThreads, 1)
       if (threadIdx.x < 32)
         issue_slice<R>(P.geo, b, sbuf0 + (uint32_t)j * sbytes, smem_addr(&bars[j]), lane);
       pending |= 1u << j;
+      used |= 1u << j;
     }
   }
   int cur = 0;
   for (uint64_t blk = blockIdx.x; blk < n_blocks; blk += gridDim.x) {
-    // slice blk + (kXBuf - 1) grid strides into the buffer the previous
-    // iteration released (its closing __syncthreads)
+    // slice blk + (kXBuf - 1) grid strides into the buffer of the previous
+    // iteration, once all warps have released it: no block-wide barrier, the
+    // other warps run on into the slices already loaded
     const int nxt = cur == 0 ? kXBuf - 1 : cur - 1;
     const uint64_t nb = blk + (uint64_t)(kXBuf - 1) * gridDim.x;
     if (nb < n_blocks) {
-      if (threadIdx.x < 32)
-        issue_slice<R>(P.geo, nb, sbuf0 + (uint32_t)nxt * sbytes, smem_addr(&bars[nxt]), lane);
+      if (threadIdx.x < 32) {
+        bool free_ok = true;
+        if ((used >> nxt) & 1)
+          free_ok = mbar_wait_bounded(smem_addr(&ebars[nxt]), (eparity >> nxt) & 1);
+        if (free_ok)
+          issue_slice<R>(P.geo, nb, sbuf0 + (uint32_t)nxt * sbytes, smem_addr(&bars[nxt]), lane);
+        else if (lane == 0)
+          atomicOr(status, kWaitTimeout);
+      }
+      if ((used >> nxt) & 1) eparity ^= 1u << nxt;
+      used |= 1u << nxt;
       pending |= 1u << nxt;
     }
     const bool ok = mbar_wait_bounded(smem_addr(&bars[cur]), (parity >> cur) & 1);
     parity ^= 1u << cur;
     pending &= ~(1u << cur);
-    if (__syncthreads_or(!ok)) {
-      if (threadIdx.x == 0) atomicOr(status, kWaitTimeout);
+    if (!ok) {  // this warp stops; the others give up at their own bounded waits
+      if (lane == 0) atomicOr(status, kWaitTimeout);
       break;
     }
     const V2* sm = reinterpret_cast<const V2*>(smem_raw + (sbuf0 + (uint32_t)cur * sbytes - raw));
@@ -419,7 +437,8 @@ __global__ void __launch_bounds__(kPThreads, 1)
         for (int i = 0; i < kPG; ++i) acc[kPG * g + i].add(A[i]);
       }
     }
-    __syncthreads();  // every thread is done with this buffer
+    __syncwarp();  // this warp is done with the buffer
+    if (lane == 0) mbar_arrive(smem_addr(&ebars[cur]));
     cur = cur + 1 == kXBuf ? 0 : cur + 1;
   }
   // copies still in flight (a block that gave up): wait for them, bounded
