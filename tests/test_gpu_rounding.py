@@ -1,4 +1,4 @@
-"""Complex64 coefficient rounding does not bias the norm (the benchmark spec bar
+"""Complex64 coefficient rounding does not bias the norm (the complex64 bar
 |1 - ||psi||^2| <= 1e-5 for complex64, reached with no renormalisation).
 
 fp32 rounds 1/sqrt2 to h with 2h^2 = 1 - 3.4e-8, so a rounded Hadamard
