@@ -42,6 +42,22 @@ def test_fused_structured_n20(dtype, make):
     assert max_err(got, unfused) <= TOL[dtype]
 
 
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("max_ctrl", [0, 1])
+def test_fused_layer_programs_n22(dtype, max_ctrl):
+    """At n = 22 the passes stage 2^13 (complex64) amplitudes: 1-qubit gates of
+    every kind (dense unitaries, rotations, H, X, Y with zero diagonals, phases)
+    run as layer programs in rotation form - both rotation shapes, register
+    relabelling, two sub-blocks per thread - and, with controls, beside gate
+    lists in the same pass; against the oracle."""
+    n = 22
+    c, theta = W.random_gates(n, 160, 2200 + max_ctrl, max_tar=1, max_ctrl=max_ctrl,
+                              kinds=("H", "X", "Y", "Z", "RX", "RY", "RZ", "U1", "MATRIX"))
+    psi = rounded(W.random_state(n, 23), dtype)
+    got = gpu_run(c, theta, psi, dtype, fuse_k=4)
+    assert max_err(got, oracle.run(c, theta, psi)) <= TOL[dtype]
+
+
 def test_fused_layered_n33_inverse_and_unfused_prefix():
     """Random layered circuit, n = 33 (64 GiB complex64), depth 40, fused
     k <= 4: U then U^dagger returns |0...0> (sampled amplitudes and norm);
