@@ -498,6 +498,66 @@ def qaoa_maxcut(torch, n=24, p=4, reps=3, n_check=16, check=True):
     return out
 
 
+def followons(torch, n_grover=20, n_trotter=28, steps=10):
+    """The scope table's follow-on workloads, timed with CUDA events:
+    Grover's search (complex64, n_grover qubits, the optimal iteration count;
+    the oracle and the diffusion as n-1-controlled Z gates) unfused and fused,
+    with the marked state's probability against its closed form
+    sin^2((2k+1) asin 2^(-n/2)); and a first-order Trotter evolution of the
+    transverse-field Ising chain (n_trotter qubits, `steps` steps, one Pauli
+    rotation pass per term, consecutive diagonal terms merged), with its norm
+    error."""
+    import math
+    import workloads as W
+    from paper_2202_07017_gb300 import State
+    st_ = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        ev[0].record(st_)
+        fn()
+        ev[1].record(st_)
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1]) / 1e3
+
+    out = {}
+    n = n_grover
+    th = math.asin(2.0 ** (-n / 2))
+    k = int(math.floor(math.pi / (4 * th)))
+    marked = 0xB3C5A5 % (1 << n)
+    c = W.grover(n, marked, k)
+    g = {"workload": f"Grover search n={n}, {k} iterations ({len(c.gates)} gates, "
+                     f"{n - 1}-controlled Z), complex64", "gates": len(c.gates)}
+    for fk, mode in ((0, "default"), (4, "dithered")):
+        s = State(n, "c64")
+        s.set_rounding(mode)
+        s.init(0)
+        s.apply_circuit(c, None, fk)  # warm-up
+        s.init(0)
+        secs = timed(lambda: s.apply_circuit(c, None, fk))
+        p = s.probabilities(list(range(n)))
+        s.close()
+        g["fused" if fk else "unfused"] = {
+            "seconds": secs, "gate_apps_per_s": len(c.gates) / secs,
+            "p_marked_err": abs(float(p[marked]) - math.sin((2 * k + 1) * th) ** 2),
+            "norm_err": abs(1.0 - float(np.sum(p))), "rounding": mode}
+    out["grover"] = g
+    n = n_trotter
+    s = State(n, "c64").init(0)
+    H = W.tfim(n)
+    s.trotter(H, 0.1, 1, 1)  # warm-up
+    s.init(0)
+    secs = timed(lambda: s.trotter(H, 1.0, steps, 1))
+    nrm = s.norm()
+    s.close()
+    out["trotter"] = {"workload": f"first-order Trotter, TFIM n={n}, {steps} steps "
+                                  f"({steps * len(H)} term exponentials), complex64",
+                      "seconds": secs, "exponentials_per_s": steps * len(H) / secs,
+                      "norm_err": abs(1.0 - nrm)}
+    return out
+
+
 def fused_layered(torch, n=33, depth=40, k=4):
     """Random layered circuit (RX, RY, RZ on every qubit + CZ brick), n = 33
     complex64 (64 GiB), depth 40: fused qubit-block passes for the whole
@@ -963,6 +1023,7 @@ def main():
         red = reductions(torch, h, n)
         adj = adjoint_ratio(torch)
         qaoa = qaoa_maxcut(torch, check=not args.no_accuracy)
+        follow = followons(torch)
         fused = None if args.no_fused else fused_layered(torch, n=args.fused_n)
         batch = None if args.no_batch else batch_solves(torch, tune=args.batch_tune)
         adj28 = None if args.no_adj28 else layered_adjoint(torch, n=args.adj_n)
@@ -1037,6 +1098,7 @@ def main():
             "clocks": clk,
             "adjoint": adj,
             "qaoa": qaoa,
+            "followons": follow,
             "fused": fused,
             "batch": batch,
             "adjoint_n28": adj28,
