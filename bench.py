@@ -709,8 +709,9 @@ def layered_adjoint(torch, n=28, depth=40):
 def batch_solves(torch, reps=5, tune=1):
     """4096 parameter sets of the n = 14, L = 10 hardware-efficient ansatz
     plus 1024 mixed ansatz circuits (n 8..16, depth 5..15), TFIM energies and
-    adjoint gradients, complex64: one persistent launch per step, replayed
-    from a CUDA graph, tile chosen by the autotuner."""
+    adjoint gradients (every gate and term real: the autotuner may pick the
+    real-amplitude kernel): one persistent launch per step, replayed from a
+    CUDA graph, tile chosen by the autotuner."""
     import workloads as W
     from paper_2202_07017_gb300 import Batch, sv_batch_plan
     hea14, _ = W.hea(14, 10, 1003)
@@ -744,15 +745,16 @@ def batch_solves(torch, reps=5, tune=1):
     nq = [c.n_qubits for c in circuits]
     state_bytes = 0.0
     for it in items:
-        amp = 8.0 * 2 ** nq[it]
+        amp = (4.0 if b.real else 8.0) * 2 ** nq[it]
         state_bytes += amp * (2 * groups[it] + 2 + 4 * groups[it])
     smem_peak = 152 * 128 * 2.07e9 / 1e9  # GB/s: 128 bytes per clock per SM at 2070 MHz
+    states = ("real fp32 states (every gate and term real)" if b.real else "complex64")
     out = {"workload": "4096 x HEA n=14 L=10 + 1024 mixed HEA (n 8..16, L 5..15), TFIM, "
-                       "energy + adjoint gradient, complex64, one persistent launch (CUDA graph)",
+                       f"energy + adjoint gradient, {states}, one persistent launch (CUDA graph)",
            "items": len(items), "ms_per_launch": 1e3 * secs, "items_per_s": len(items) / secs,
            "gradients_per_s": len(theta) / secs,
            "tile": {"k": b.k, "threads": b.threads, "blocks": b.blocks, "cluster": b.cluster,
-                    "smem_states": b.smem_states},
+                    "smem_states": b.smem_states, "real_states": b.real},
            "create_and_tune_s": t_create,
            "state_traffic": {"bytes_per_launch": state_bytes,
                              "achieved_gbs": state_bytes / secs / 1e9,
@@ -877,9 +879,9 @@ def main():
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--adj-n", type=int, default=28,
                     help="qubits of the layered-circuit adjoint measurement")
-    ap.add_argument("--batch-tune", type=int, default=1, choices=[0, 1, 2, 3],
+    ap.add_argument("--batch-tune", type=int, default=1, choices=[0, 1, 2, 3, 4],
                     help="batch kernel choice: 1 autotune (default), 0 default tile, "
-                         "2 clusters, 3 shared-memory states")
+                         "2 clusters, 3 shared-memory states, 4 real states")
     ap.add_argument("--fused-n", type=int, default=33,
                     help="qubits of the fused layered-circuit measurement")
     ap.add_argument("--gate-table", choices=["c64", "c128"],

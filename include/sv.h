@@ -372,7 +372,11 @@ sv_status sv_grad_fused(sv_state s, const sv_circuit* c, const double* theta,
  * workspace slot that stays in L1/L2, or (a variant the autotuner may pick)
  * psi of up to 14 qubits and lambda of up to 13 in shared memory.  Energies
  * and gradients accumulate per warp in compensated fp32 and across warps in
- * fp64, in a fixed order.
+ * fp64, in a fixed order.  A batch whose gates are all real (H X Z RY, with
+ * controls) and whose terms are all real matrices (an even number of Y
+ * factors) keeps real states: a variant the autotuner may pick carries psi
+ * and lambda as fp32 real vectors (psi of up to 15 qubits and lambda of up to
+ * 14 in shared memory), with the same results up to rounding.
  *
  * Limits: <= SV_BATCH_MAX_QUBITS qubits, <= 480 gates and <= 256
  * parameters per circuit, <= 64 Pauli terms per Hamiltonian; gates are the
@@ -392,9 +396,12 @@ sv_status sv_grad_fused(sv_state s, const sv_circuit* c, const double* theta,
  * memory up to 14 qubits, or two-block clusters of 512 threads that split each item's psi and lambda by
  * their top bit over the pair and keep them in shared memory up to 14 qubits,
  * k <= 3) on the batch and keeps the fastest (this synchronises the device).
+ * For a real batch the autotuner also times the real-amplitude kernel
+ * (single blocks of 512 threads, k in {3,4,5}).
  * tune = 2: the cluster kernel with k = 3 (the tune = 0 tile if a gate has 3
  * controls); tune = 3: single blocks of 512 threads with states in shared
- * memory, k = 4.  Other values: SV_ERR_INVALID.  The handle is
+ * memory, k = 4; tune = 4: the real-amplitude kernel, k = 4 (SV_ERR_INVALID
+ * for a batch that is not real).  Other values: SV_ERR_INVALID.  The handle is
  * library-owned; sv_batch_free releases it. */
 #define SV_BATCH_MAX_QUBITS 18
 typedef struct sv_batch_s* sv_batch;
@@ -406,7 +413,8 @@ sv_status sv_batch_create(const sv_circuit* circuits, const sv_pauli_sum* hamilt
 /* Host-only dry run of the batch planner (no GPU call): validates the
  * circuits and Hamiltonians as sv_batch_create does and writes, per
  * circuit, the number of register groups of width k (max(2, widest gate)
- * <= k <= 4) its gates are scheduled into.  Errors: SV_ERR_INVALID. */
+ * <= k <= 5; 5 is the real-amplitude kernel's widest) its gates are
+ * scheduled into.  Errors: SV_ERR_INVALID. */
 sv_status sv_batch_plan(const sv_circuit* circuits, const sv_pauli_sum* hamiltonians,
                         int n_circuits, int k, int32_t* groups_per_circuit);
 
@@ -415,9 +423,10 @@ sv_status sv_batch_info(sv_batch b, int* k, int* threads, int* blocks, int* tota
 
 /* The chosen kernel: cluster_size 2 for the two-block cluster kernel (each
  * item's psi and lambda split by their top bit over the pair), else 1;
- * smem_states 1 if the kernel keeps small items' states in shared memory.
- * SV_ERR_INVALID for a null handle or output. */
-sv_status sv_batch_kernel(sv_batch b, int* cluster_size, int* smem_states);
+ * smem_states 1 if the kernel keeps small items' states in shared memory;
+ * real_states 1 for the real-amplitude kernel.  SV_ERR_INVALID for a null
+ * handle or output. */
+sv_status sv_batch_kernel(sv_batch b, int* cluster_size, int* smem_states, int* real_states);
 
 /* One persistent launch (a queue reset plus the kernel) on cuda_stream;
  * dev_theta, dev_energy (n_items) and dev_grad (total_params) are device

@@ -140,13 +140,14 @@ class State:
 
 class Batch:
     """Energies and adjoint gradients of many small circuits in one persistent
-    launch (complex64, fp64 accumulation).  theta / energy / grad are torch
+    launch (complex64 - or real fp32 states for a batch of real gates and
+    terms - with fp64 accumulation).  theta / energy / grad are torch
     CUDA float64 tensors; parameters are packed per item in item order."""
 
     def __init__(self, circuits, hamiltonians, item_circuit, tune=True):
         self.h, self.packed = sv_batch_create(circuits, hamiltonians, item_circuit, tune)
         self.k, self.threads, self.blocks, self.total_params = sv_batch_info(self.h)
-        self.cluster, self.smem_states = sv_batch_kernel(self.h)
+        self.cluster, self.smem_states, self.real = sv_batch_kernel(self.h)
         self.n_items = len(self.packed.items)
 
     def run(self, theta, energy=None, grad=None, graph: bool = False, stream=None):

@@ -613,6 +613,311 @@ __global__ void __launch_bounds__(MAXT, MINB) kbatch(const BatchArgs A) {
   }
 }
 
+// ---- real-amplitude batches ------------------------------------------------------
+// Gates whose matrices are real (H, X, Z, RY and their controlled forms)
+// map |0...0> to real states, and a Hamiltonian whose terms are real
+// matrices (coefficient times i^{#Y} real, as for the transverse-field Ising
+// model) maps a real state to a real lambda = H psi.  A batch made only of
+// such items runs psi and lambda as real vectors: half the bytes and half the
+// multiply-adds of the complex kernel, and both states of an n = 14 item
+// (2 x 64 KiB) in shared memory.  The only parameterised kind is then RY
+// (generator Y), whose gradient Im<lambda|Y|psi> is the real sum of
+// l1 p0 - l0 p1 over the pairs of its target bit.
+//
+// Storage order: amplitude x lives at swzr(x) = x ^ ((x >> 5) & 31), which
+// spreads the 32 amplitudes of a 128-byte row over the row by the next five
+// index bits (a bijection of [0, 2^n), linear over XOR).
+__device__ __forceinline__ int swzr(int x) { return x ^ ((x >> 5) & 31); }
+
+template <int K>
+__device__ void group_offsets_swzr(const BGroup& g, int (&off)[1 << K], int (&lm)[K]) {
+  off[0] = 0;
+#pragma unroll
+  for (int r = 1; r < (1 << K); ++r) off[r] = off[r & (r - 1)] ^ swzr(1 << g.bits[lowbit_b(r)]);
+#pragma unroll
+  for (int i = 0; i < K; ++i) lm[i] = (1 << g.bits[i]) - 1;
+}
+
+// (a, b) <- [[g0, g1], [g2, g3]] (a, b) on the pairs of group bit B (inside the
+// group-local control mask cm when CTRL); NEG: b <- -b
+template <int K, int B, bool NEG, bool CTRL>
+__device__ __forceinline__ void re_pairs(float g0, float g1, float g2, float g3, int cm,
+                                         float (&v)[1 << K]) {
+#pragma unroll
+  for (int r = 0; r < (1 << K); ++r) {
+    if (r & (1 << B)) continue;
+    if (CTRL && (r & cm) != cm) continue;
+    const int r1 = r | (1 << B);
+    if (NEG) {
+      v[r1] = -v[r1];
+    } else {
+      const float a = v[r], b = v[r1];
+      v[r] = g0 * a + g1 * b;
+      v[r1] = g2 * a + g3 * b;
+    }
+  }
+}
+
+// sign flip under a control mask fixed at compile time (CZ and its kin)
+template <int K, int B, int CM>
+__device__ __forceinline__ void re_neg_cm(float (&v)[1 << K]) {
+  if constexpr (!((CM >> B) & 1)) {
+#pragma unroll
+    for (int r = 0; r < (1 << K); ++r) {
+      if (r & (1 << B)) continue;
+      if ((r & CM) != CM) continue;
+      v[r | (1 << B)] = -v[r | (1 << B)];
+    }
+  }
+}
+
+template <int K, int B>
+__device__ __forceinline__ void re_neg(int cm, float (&v)[1 << K]) {
+#define SV_RE_CM(c)                                          \
+  case c:                                                    \
+    if constexpr (c < (1 << K)) re_neg_cm<K, B, c>(v);       \
+    break;
+  switch (cm) {
+    SV_RE_CM(0) SV_RE_CM(1) SV_RE_CM(2) SV_RE_CM(3) SV_RE_CM(4) SV_RE_CM(5) SV_RE_CM(6)
+    SV_RE_CM(7) SV_RE_CM(8) SV_RE_CM(9) SV_RE_CM(10) SV_RE_CM(11) SV_RE_CM(12) SV_RE_CM(13)
+    SV_RE_CM(14) SV_RE_CM(15) SV_RE_CM(16) SV_RE_CM(17) SV_RE_CM(18) SV_RE_CM(20)
+    SV_RE_CM(24)
+    default: re_pairs<K, B, true, true>(0.f, 0.f, 0.f, 0.f, cm, v); break;
+  }
+#undef SV_RE_CM
+}
+
+// operation (cls BC_REAL or BC_NEG) with matrix M (8 floats, re/im) or, when
+// DAG, its transpose
+template <int K, int B, bool DAG>
+__device__ __forceinline__ void re_apply(const BOp& op, const float* M, float (&v)[1 << K]) {
+  if (op.cls == BC_NEG) {
+    re_neg<K, B>(op.cm, v);
+    return;
+  }
+  const float g0 = M[0], g1 = DAG ? M[4] : M[2], g2 = DAG ? M[2] : M[4], g3 = M[6];
+  if (op.cm)
+    re_pairs<K, B, false, true>(g0, g1, g2, g3, op.cm, v);
+  else
+    re_pairs<K, B, false, false>(g0, g1, g2, g3, 0, v);
+}
+
+template <int K, int B>
+__device__ __forceinline__ float re_grad(int cm, const float (&p)[1 << K], const float (&l)[1 << K]) {
+  float acc = 0.f;
+#pragma unroll
+  for (int r = 0; r < (1 << K); ++r) {
+    if (r & (1 << B)) continue;
+    if ((r & cm) != cm) continue;
+    const int r1 = r | (1 << B);
+    acc = fmaf(l[r1], p[r], acc);
+    acc = fmaf(-l[r], p[r1], acc);
+  }
+  return acc;
+}
+
+#define SV_RE_BITS(B, CALL) \
+  switch (B) {              \
+    case 0: CALL(0); break; \
+    case 1: CALL(1); break; \
+    case 2: CALL(2); break; \
+    case 3: CALL(3); break; \
+    default: CALL(4); break; \
+  }
+
+template <int K>
+__device__ void group_fwd_re(float* psi, int n, const BGroup& g, const BOp* ops, const float* mats) {
+  int off[1 << K], lm[K];
+  group_offsets_swzr<K>(g, off, lm);
+  const int kk = g.k;
+  const int nsub = 1 << (n - kk);
+  const int width = 1 << kk;
+  for (int s = threadIdx.x; s < nsub; s += blockDim.x) {
+    const int b = swzr(sub_base<K>(s, lm, kk));
+    float v[1 << K];
+#pragma unroll
+    for (int r = 0; r < (1 << K); ++r) v[r] = r < width ? psi[b ^ off[r]] : 0.f;
+    for (int o = g.op0; o < g.op1; ++o) {
+      const BOp op = ops[o];
+      const float* M = mats + 8 * op.gi;
+#define SV_FWD_RE(BB) \
+  if constexpr (BB < K) re_apply<K, BB, false>(op, M, v)
+      SV_RE_BITS(op.b0, SV_FWD_RE)
+#undef SV_FWD_RE
+    }
+#pragma unroll
+    for (int r = 0; r < (1 << K); ++r)
+      if (r < width) psi[b ^ off[r]] = v[r];
+  }
+}
+
+template <int K>
+__device__ void group_bwd_re(float* psi, float* lam, int n, const BGroup& g, const BOp* ops,
+                             const float* mats, float2* wpart) {
+  int off[1 << K], lm[K];
+  group_offsets_swzr<K>(g, off, lm);
+  const int kk = g.k;
+  const int nsub = 1 << (n - kk);
+  const int width = 1 << kk;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // every lane of a warp runs the same number of iterations (warp sums)
+  const int iters = (nsub + blockDim.x - 1) / blockDim.x;
+  for (int it = 0; it < iters; ++it) {
+    const int s = threadIdx.x + it * blockDim.x;
+    const bool live = s < nsub;
+    const int b = live ? swzr(sub_base<K>(s, lm, kk)) : 0;
+    float p[1 << K], l[1 << K];
+#pragma unroll
+    for (int r = 0; r < (1 << K); ++r) {
+      const bool in = live && r < width;
+      p[r] = in ? psi[b ^ off[r]] : 0.f;
+      l[r] = in ? lam[b ^ off[r]] : 0.f;
+    }
+    for (int o = g.op1 - 1; o >= g.op0; --o) {
+      const BOp op = ops[o];
+      const float* M = mats + 8 * op.gi;
+      if (op.pauli) {  // RY: generator Y
+        float c = 0.f;
+#define SV_GRAD_RE(BB) \
+  if constexpr (BB < K) c = re_grad<K, BB>(op.cm, p, l)
+        SV_RE_BITS(op.b0, SV_GRAD_RE)
+#undef SV_GRAD_RE
+        c = warp_sum_f(c);
+        if (lane == 0) ksum_add(wpart[warp * kBMaxParams + op.param], c);
+      }
+#define SV_BWD_RE(BB)                        \
+  if constexpr (BB < K) {                    \
+    re_apply<K, BB, true>(op, M, p);         \
+    re_apply<K, BB, true>(op, M, l);         \
+  }
+      SV_RE_BITS(op.b0, SV_BWD_RE)
+#undef SV_BWD_RE
+    }
+    if (live) {
+#pragma unroll
+      for (int r = 0; r < (1 << K); ++r)
+        if (r < width) {
+          psi[b ^ off[r]] = p[r];
+          lam[b ^ off[r]] = l[r];
+        }
+    }
+  }
+}
+
+// Real states in shared memory: psi for items up to kBSmemQubits + 1 qubits,
+// lambda beside it up to kBSmemQubits; larger states in the block's global
+// workspace slot (read as 4 x 2^nmax floats).
+template <int K, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) kbatch_re(const BatchArgs A) {
+  __shared__ float mats[8 * kBMaxGates];
+  __shared__ float2 wpart[(MAXT / 32) * kBMaxParams];  // per warp and parameter: (sum, comp)
+  __shared__ double red[MAXT / 32];
+  __shared__ int s_item;
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  BOp* sops = reinterpret_cast<BOp*>(dyn_smem);
+  BGroup* sgrp = reinterpret_cast<BGroup*>(dyn_smem + kBOpsBytes);
+  int2* sterm = reinterpret_cast<int2*>(dyn_smem + kBOpsBytes + kBGroupBytes);
+  float* scoef = reinterpret_cast<float*>(dyn_smem + kBOpsBytes + kBGroupBytes + kBTermBytes);
+  float* dyn_state = reinterpret_cast<float*>(dyn_smem + kBCacheBytes);
+  constexpr int kSm = kBSmemQubits + 1;  // 2^15 floats = kBSmemStateBytes
+  const int nwarps = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float* const gpsi = reinterpret_cast<float*>(A.work + (size_t)blockIdx.x * (size_t(2) << A.nmax));
+  float* const glam = gpsi + (size_t(1) << A.nmax);
+  while (true) {
+    if (threadIdx.x == 0) s_item = atomicAdd(A.queue, 1);
+    __syncthreads();
+    const int slot = s_item;
+    if (slot >= A.n_items) break;
+    const int item = A.order[slot];
+    const BCirc C = A.circs[A.item_circ[item]];
+    const double* th = A.theta + A.theta_off[item];
+    const int dim = 1 << C.n;
+    float* psi = C.n <= kSm ? dyn_state : gpsi;
+    float* lam = C.n < kSm ? dyn_state + (1 << (kSm - 1)) : glam;
+    // gate matrices (fp64 trigonometry, rounded once): real kinds only
+    for (int gi = threadIdx.x; gi < C.ngates; gi += blockDim.x) {
+      const BGateDesc d = A.gates[C.gate0 + gi];
+      const double a = d.param >= 0 ? th[d.param] : d.angle;
+      double s, c;
+      sincos(0.5 * a, &s, &c);
+      double m[4] = {1, 0, 0, 1};
+      const double r2 = 0.70710678118654752440;
+      switch (d.kind) {
+        case SV_GATE_H: m[0] = r2; m[1] = r2; m[2] = r2; m[3] = -r2; break;
+        case SV_GATE_X: m[0] = 0; m[1] = 1; m[2] = 1; m[3] = 0; break;
+        case SV_GATE_Z: m[3] = -1; break;
+        default: m[0] = c; m[1] = -s; m[2] = s; m[3] = c; break;  // RY
+      }
+      for (int e = 0; e < 4; ++e) {
+        mats[8 * gi + 2 * e] = (float)m[e];
+        mats[8 * gi + 2 * e + 1] = 0.f;
+      }
+    }
+    for (int x = threadIdx.x; x < dim; x += blockDim.x) psi[x] = x == 0 ? 1.f : 0.f;
+    for (int i = threadIdx.x; i < nwarps * kBMaxParams; i += blockDim.x)
+      wpart[i] = make_float2(0.f, 0.f);
+    {
+      const int ng = C.ngroups;
+      const int op_base = ng ? A.groups[C.group0].op0 : 0;
+      const int nops = ng ? A.groups[C.group0 + ng - 1].op1 - op_base : 0;
+      for (int i = threadIdx.x; i < nops; i += blockDim.x) sops[i] = A.ops[op_base + i];
+      for (int i = threadIdx.x; i < ng; i += blockDim.x) {
+        BGroup G = A.groups[C.group0 + i];
+        G.op0 -= op_base;
+        G.op1 -= op_base;
+        sgrp[i] = G;
+      }
+      for (int t = threadIdx.x; t < C.nterms; t += blockDim.x) {
+        const BTerm T = A.terms[C.term0 + t];
+        const int xm = (int)T.xm, zm = (int)T.zm;
+        sterm[t] = make_int2(swzr(xm), (int)((unsigned)zm | ((unsigned)__popc(xm & zm) << 31)));
+        scoef[t] = (float)T.cre;  // a real batch has cim = 0
+      }
+    }
+    __syncthreads();
+    for (int gg = 0; gg < C.ngroups; ++gg) {
+      group_fwd_re<K>(psi, C.n, sgrp[gg], sops, mats);
+      __syncthreads();
+    }
+    // lambda = H psi, E = <psi|lambda>
+    float2 ek = make_float2(0.f, 0.f);
+    for (int x = threadIdx.x; x < dim; x += blockDim.x) {
+      const int px = swzr(x);
+      const float a = psi[px];
+      float d = 0.f;
+      for (int t = 0; t < C.ndiag; ++t) d += (__popc(x & sterm[t].y) & 1) ? -scoef[t] : scoef[t];
+      float o = d * a;
+      for (int t = C.ndiag; t < C.nterms; ++t) {
+        const int2 q = sterm[t];
+        const float sb = scoef[t] * psi[px ^ q.x];
+        o += ((__popc(x & q.y) + ((unsigned)q.y >> 31)) & 1) ? -sb : sb;
+      }
+      lam[px] = o;
+      ksum_add(ek, a * o);
+    }
+    double e = warp_sum_d(ksum_value(ek));
+    if (lane == 0) red[warp] = e;
+    __syncthreads();
+    for (int gg = C.ngroups - 1; gg >= 0; --gg) {
+      group_bwd_re<K>(psi, lam, C.n, sgrp[gg], sops, mats, wpart);
+      __syncthreads();
+    }
+    const int toff = A.theta_off[item];
+    for (int p = threadIdx.x; p < C.nparams; p += blockDim.x) {
+      double g = 0.0;
+      for (int w = 0; w < nwarps; ++w) g += ksum_value(wpart[w * kBMaxParams + p]);
+      A.grad[toff + p] = g;
+    }
+    if (threadIdx.x == 0) {
+      double E = 0.0;
+      for (int w = 0; w < nwarps; ++w) E += red[w];
+      A.energy[item] = E;
+    }
+    __syncthreads();
+  }
+}
+
 // ---- two-block clusters: each item's states split over the pair ----------------------
 // A cluster of two blocks (one per SM) runs one item at a time.  Block c
 // holds the amplitudes whose top bit (n - 1) is c, of both psi and lambda: in
@@ -945,6 +1250,8 @@ struct sv_batch_s {
   int k = 4, threads = 256, blocks = 0;  // chosen tile
   bool cluster = false;                  // two-block cluster kernel
   bool smem_states = false;              // single-block kernel with states in shared memory
+  bool real = false;                     // real-amplitude kernel (kbatch_re)
+  bool all_real = false;                 // every gate and term real: kbatch_re may run
   int sms = 152;
   // device buffers
   sv::BCirc* circs = nullptr;
@@ -1105,8 +1412,13 @@ BatchKernel kernel_for(int k, int threads, int per_sm) {
 // register groups of 2 or 3 qubits (4 would spill at 512 threads per block)
 BatchKernel cluster_kernel_for(int k) { return k == 2 ? kbatch_cl<2> : kbatch_cl<3>; }
 
+BatchKernel real_kernel_for(int k) {
+  return k <= 3 ? kbatch_re<3, 512, 1> : k == 4 ? kbatch_re<4, 512, 1> : kbatch_re<5, 512, 1>;
+}
+
 sv_status launch_batch(sv_batch b, const double* theta, double* energy, double* grad,
-                       cudaStream_t st, int k, int threads, int blocks, bool cl, bool sms) {
+                       cudaStream_t st, int k, int threads, int blocks, bool cl, bool sms,
+                       bool re) {
   BatchArgs A;
   A.circs = b->circs;
   A.gates = b->gates;
@@ -1124,6 +1436,19 @@ sv_status launch_batch(sv_batch b, const double* theta, double* energy, double* 
   A.work = b->work;
   A.queue = b->queue;
   SV_CUDA_TRY(cudaMemsetAsync(b->queue, 0, sizeof(int), st));
+  if (re) {
+    BatchKernel kern = real_kernel_for(k);
+    static bool attr[6] = {false, false, false, false, false, false};
+    if (!attr[k]) {
+      SV_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(kBCacheBytes + kBSmemStateBytes)));
+      attr[k] = true;
+    }
+    ProfScope prof(st, "kbatch_re");
+    kern<<<blocks, 512, kBCacheBytes + kBSmemStateBytes, st>>>(A);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return check_launch("batch kernel (real amplitudes)");
+  }
   if (cl) {
     BatchKernel kern = cluster_kernel_for(k);
     static bool attr[5] = {false, false, false, false, false};
@@ -1240,8 +1565,8 @@ sv_status sv_batch_plan(const sv_circuit* circuits, const sv_pauli_sum* hamilton
   int nmax = 0, width = 0;
   sv_status st = validate_batch("sv_batch_plan", circuits, hamiltonians, n_circuits, &nmax, &width);
   if (st) return st;
-  if (k < 2 || k > 4 || k < width || !groups_per_circuit) {
-    set_error("sv_batch_plan: group width %d must be in max(2, widest gate %d)..4", k, width);
+  if (k < 2 || k > 5 || k < width || !groups_per_circuit) {
+    set_error("sv_batch_plan: group width %d must be in max(2, widest gate %d)..5", k, width);
     return SV_ERR_INVALID;
   }
   HostPlan P;
@@ -1259,7 +1584,7 @@ sv_status sv_batch_plan(const sv_circuit* circuits, const sv_pauli_sum* hamilton
 sv_status sv_batch_create(const sv_circuit* circuits, const sv_pauli_sum* hamiltonians,
                           int n_circuits, const int32_t* item_circuit, int n_items, int tune,
                           sv_batch* out) {
-  if (!item_circuit || !out || n_items < 1 || tune < 0 || tune > 3) {
+  if (!item_circuit || !out || n_items < 1 || tune < 0 || tune > 4) {
     set_error("sv_batch_create: bad arguments");
     return SV_ERR_INVALID;
   }
@@ -1301,9 +1626,32 @@ sv_status sv_batch_create(const sv_circuit* circuits, const sv_pauli_sum* hamilt
     int k, threads, per_sm;
     bool cl;          // two-block clusters (per_sm = 1, threads = kClThreads)
     bool sms = false; // states in shared memory up to 14 qubits (512 threads, 1 per SM)
+    bool re = false;  // real amplitudes (kbatch_re, 512 threads, 1 per SM)
   };
+  // real batch: every gate real (H, X, Z, RY, with controls) and every term a
+  // real matrix (an even number of Y factors)
+  bool all_real = true;
+  for (int c = 0; c < n_circuits && all_real; ++c) {
+    for (int i = 0; i < circuits[c].n_gates; ++i) {
+      const int kd = circuits[c].gates[i].kind;
+      if (kd != SV_GATE_H && kd != SV_GATE_X && kd != SV_GATE_Z && kd != SV_GATE_RY) all_real = false;
+    }
+    for (int t = 0; t < hamiltonians[c].n_terms; ++t)
+      if (popc64(hamiltonians[c].xmask[t] & hamiltonians[c].zmask[t]) & 1) all_real = false;
+  }
+  b->all_real = all_real;
   std::vector<Cand> cands;
-  if (tune == 1) {
+  if (tune == 4) {
+    if (!all_real) {
+      set_error("sv_batch_create: tune = 4 (real amplitudes) needs every gate real (H X Z RY)"
+                " and every term with an even number of Y factors");
+      delete b;
+      return SV_ERR_INVALID;
+    }
+    cands.push_back({std::max(4, width), 512, 1, false, true, true});
+  } else if (tune == 1) {
+    if (all_real)
+      for (int kr = std::max(3, width); kr <= 5; ++kr) cands.push_back({kr, 512, 1, false, true, true});
     const Cand all[] = {{2, 512, 1, false, true}, {3, 512, 1, false, true}, {4, 512, 1, false, true},
                         {2, kClThreads, 1, true}, {3, kClThreads, 1, true},
                         {2, 512, 1, false}, {3, 512, 1, false}, {4, 512, 1, false},
@@ -1382,10 +1730,10 @@ sv_status sv_batch_create(const sv_circuit* circuits, const sv_pauli_sum* hamilt
         if (st) break;
       }
       const int blocks = c.cl ? 2 * (sms / 2) : sms * c.per_sm;
-      st = launch_batch(b, th, en, gr, 0, c.k, c.threads, blocks, c.cl, c.sms);  // warm-up
+      st = launch_batch(b, th, en, gr, 0, c.k, c.threads, blocks, c.cl, c.sms, c.re);  // warm-up
       if (st) break;
       cudaEventRecord(e0, 0);
-      st = launch_batch(b, th, en, gr, 0, c.k, c.threads, blocks, c.cl, c.sms);
+      st = launch_batch(b, th, en, gr, 0, c.k, c.threads, blocks, c.cl, c.sms, c.re);
       cudaEventRecord(e1, 0);
       if (cudaEventSynchronize(e1) != cudaSuccess) {
         set_error("sv_batch_create: tuning run failed: %s", cudaGetErrorString(cudaGetLastError()));
@@ -1401,6 +1749,7 @@ sv_status sv_batch_create(const sv_circuit* circuits, const sv_pauli_sum* hamilt
         b->blocks = blocks;
         b->cluster = c.cl;
         b->smem_states = c.sms;
+        b->real = c.re;
       }
     }
     cudaEventDestroy(e0);
@@ -1410,6 +1759,7 @@ sv_status sv_batch_create(const sv_circuit* circuits, const sv_pauli_sum* hamilt
     b->threads = cands[0].threads;
     b->cluster = cands[0].cl;
     b->smem_states = cands[0].sms;
+    b->real = cands[0].re;
     b->blocks = cands[0].cl ? 2 * (sms / 2) : sms * cands[0].per_sm;
   }
   if (th) cudaFree(th);
@@ -1444,13 +1794,14 @@ sv_status sv_batch_info(sv_batch b, int* k, int* threads, int* blocks, int* tota
   return SV_OK;
 }
 
-sv_status sv_batch_kernel(sv_batch b, int* cluster_size, int* smem_states) {
-  if (!b || !cluster_size || !smem_states) {
+sv_status sv_batch_kernel(sv_batch b, int* cluster_size, int* smem_states, int* real_states) {
+  if (!b || !cluster_size || !smem_states || !real_states) {
     set_error("sv_batch_kernel: bad arguments");
     return SV_ERR_INVALID;
   }
   *cluster_size = b->cluster ? 2 : 1;
-  *smem_states = (b->cluster || b->smem_states) ? 1 : 0;
+  *smem_states = (b->cluster || b->smem_states || b->real) ? 1 : 0;
+  *real_states = b->real ? 1 : 0;
   return SV_OK;
 }
 
@@ -1461,7 +1812,7 @@ sv_status sv_batch_run(sv_batch b, const double* dev_theta, double* dev_energy, 
     return SV_ERR_INVALID;
   }
   return launch_batch(b, dev_theta, dev_energy, dev_grad, (cudaStream_t)cuda_stream, b->k,
-                      b->threads, b->blocks, b->cluster, b->smem_states);
+                      b->threads, b->blocks, b->cluster, b->smem_states, b->real);
 }
 
 sv_status sv_batch_run_graph(sv_batch b, const double* dev_theta, double* dev_energy,
@@ -1484,7 +1835,7 @@ sv_status sv_batch_run_graph(sv_batch b, const double* dev_theta, double* dev_en
     sv_status s2 = SV_OK;
     if (e == cudaSuccess) {
       s2 = launch_batch(b, dev_theta, dev_energy, dev_grad, cap, b->k, b->threads, b->blocks,
-                        b->cluster, b->smem_states);
+                        b->cluster, b->smem_states, b->real);
       e = cudaStreamEndCapture(cap, &g);
     }
     if (e == cudaSuccess && s2 == SV_OK) e = cudaGraphInstantiate(&b->gexec, g, 0);

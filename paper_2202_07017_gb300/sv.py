@@ -115,7 +115,7 @@ def load(build: bool = True):
                             ctypes.c_int, P(c_vp)],
         "sv_batch_plan": [P(SvCircuit), P(SvPauliSum), ctypes.c_int, ctypes.c_int, P(c_i32)],
         "sv_batch_info": [c_vp, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int)],
-        "sv_batch_kernel": [c_vp, P(ctypes.c_int), P(ctypes.c_int)],
+        "sv_batch_kernel": [c_vp, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int)],
         "sv_batch_run": [c_vp, c_vp, c_vp, c_vp, c_vp],
         "sv_batch_run_graph": [c_vp, c_vp, c_vp, c_vp, c_vp],
         "sv_batch_grad": [P(SvCircuit), P(SvPauliSum), ctypes.c_int, P(c_i32), ctypes.c_int,
@@ -505,7 +505,8 @@ class PackedBatch:
 
 def sv_batch_create(circuits, hamiltonians, item_circuit, tune=False):
     """tune: False/0 default tile, True/1 autotune, 2 the two-block cluster kernel,
-    3 single blocks with states in shared memory."""
+    3 single blocks with states in shared memory, 4 the real-amplitude kernel
+    (every gate H, X, Z or RY, every term with an even number of Y factors)."""
     pb = PackedBatch(circuits, hamiltonians, item_circuit)
     h = c_vp()
     _check(load().sv_batch_create(pb.carr, pb.harr, len(pb.pcs),
@@ -531,10 +532,11 @@ def sv_batch_info(h: int):
 
 
 def sv_batch_kernel(h: int):
-    """(blocks per cluster, states in shared memory) of the chosen batch kernel."""
-    c, m = ctypes.c_int(), ctypes.c_int()
-    _check(load().sv_batch_kernel(c_vp(h), ctypes.byref(c), ctypes.byref(m)))
-    return c.value, bool(m.value)
+    """(blocks per cluster, states in shared memory, real states) of the chosen
+    batch kernel."""
+    c, m, r = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().sv_batch_kernel(c_vp(h), ctypes.byref(c), ctypes.byref(m), ctypes.byref(r)))
+    return c.value, bool(m.value), bool(r.value)
 
 
 def sv_batch_run(h: int, dev_theta: int, dev_energy: int, dev_grad: int, stream: int = 0) -> None:

@@ -12,9 +12,11 @@ ONEQ = ("H", "X", "Y", "Z", "RX", "RY", "RZ", "U1")
 
 def test_groups_for_each_width():
     hea, _ = W.hea(14, 10, 1)
-    g = {k: int(sv_batch_plan([hea], [W.tfim(14)], k)[0]) for k in (2, 3, 4)}
-    assert g[2] >= g[3] >= g[4] >= 1
+    g = {k: int(sv_batch_plan([hea], [W.tfim(14)], k)[0]) for k in (2, 3, 4, 5)}
+    assert g[2] >= g[3] >= g[4] >= g[5] >= 1
     assert g[4] < len(hea.gates)
+    with pytest.raises(SvError):  # 5 qubits is the widest register group
+        sv_batch_plan([hea], [W.tfim(14)], 6)
 
 
 def test_wide_gates_need_wide_groups():

@@ -155,3 +155,88 @@ def test_batch_kernel_choice_and_both_state_homes(mode, cl, sm):
                 err = np.max(np.abs(g[off:off + c.n_params][ps] - g_ref[ps]))
                 assert err <= 1e-5 * max(np.max(np.abs(g_ref[ps])), 0.05 * scale), (i, err)
             off += c.n_params
+
+
+REAL = ("H", "X", "Z", "RY")
+
+
+def _real_terms(n, count, seed):
+    """Random Pauli strings with an even number of Y factors (real matrices)."""
+    terms = [t for t in W.random_pauli_sum(n, 4 * count, seed)
+             if sum(1 for _, p in t[1] if p == "Y") % 2 == 0]
+    return terms[:count]
+
+
+def test_real_batch_against_oracle():
+    """The real-amplitude kernel (tune = 4): HEA items and random circuits of
+    real gates with up to 3 controls (H, X, Z, RY: CNOT, CZ, controlled RY
+    ...), Hamiltonians of real terms (XX, YY, ZZ, X, Z strings); items of
+    8..16 qubits put psi and lambda in shared memory (n <= 14), psi alone
+    (n = 15) or neither (n = 16).  Energies and gradients against the oracle;
+    graph replay repeats the launch bit for bit."""
+    from paper_2202_07017_gb300 import Batch
+    circuits, hams = [], []
+    for n in (1, 2, 5, 9, 14, 15, 16):
+        c, _ = W.hea(n, 3 if n < 15 else 2, 40 + n)
+        circuits.append(c)
+        hams.append(W.tfim(n) if n > 1 else [(1.0, ((0, "X"),)), (0.5, ((0, "Z"),))])
+    for n, seed in ((4, 1), (8, 2), (11, 3)):
+        c, _ = W.random_gates(n, 60, 300 + seed, max_tar=1, max_ctrl=3, kinds=REAL)
+        circuits.append(c)
+        hams.append(_real_terms(n, 10, seed))
+    items = list(range(len(circuits))) + [1, 3, 7]
+    rng = W.SplitMix64(78)
+    thetas = [np.array([rng.angle() for _ in range(circuits[ci].n_params)]) for ci in items]
+    b = Batch(circuits, hams, items, tune=4)
+    assert b.real and b.smem_states and b.cluster == 1
+    theta = torch.tensor(np.concatenate(thetas), dtype=torch.float64, device="cuda")
+    e, g = b.run(theta)
+    e2, g2 = b.run(theta, graph=True)
+    torch.cuda.synchronize()
+    e, g, e2, g2 = (t.cpu().numpy() for t in (e, g, e2, g2))
+    b.close()
+    assert np.array_equal(e, e2) and np.array_equal(g, g2)
+    off = 0
+    for i, ci in enumerate(items):
+        c, H, th = circuits[ci], hams[ci], thetas[i]
+        scale = sum(abs(t[0]) for t in H)
+        assert abs(e[i] - oracle.energy(c, th, H)) <= 1e-5 * scale, i
+        if c.n_params:
+            ps = (list(range(c.n_params)) if c.n_qubits <= 11
+                  else sorted({0, c.n_params // 3, c.n_params // 2, c.n_params - 1}))
+            ref = oracle.grad_param_shift(c, th, H, params=ps)
+            err = np.max(np.abs(g[off:off + c.n_params][ps] - ref[ps]))
+            assert err <= 1e-5 * max(np.max(np.abs(ref[ps])), 0.05 * scale), (i, err)
+        off += c.n_params
+
+
+def test_real_batch_matches_complex_kernel():
+    """The same real batch through the real-amplitude kernel and the complex
+    shared-memory kernel: energies and gradients agree to fp32 rounding."""
+    from paper_2202_07017_gb300 import Batch
+    mixed = W.mixed_batch(24, 99)
+    circuits = [m[0] for m in mixed]
+    hams = [m[2] for m in mixed]
+    theta = np.concatenate([m[1] for m in mixed])
+    items = list(range(len(circuits)))
+    out = {}
+    for tune in (3, 4):
+        b = Batch(circuits, hams, items, tune=tune)
+        assert b.real == (tune == 4)
+        e, g = b.run(torch.tensor(theta, dtype=torch.float64, device="cuda"))
+        torch.cuda.synchronize()
+        out[tune] = (e.cpu().numpy(), g.cpu().numpy())
+        b.close()
+    scale = max(sum(abs(t[0]) for t in H) for H in hams)
+    assert np.max(np.abs(out[3][0] - out[4][0])) <= 2e-6 * scale
+    assert np.max(np.abs(out[3][1] - out[4][1])) <= 2e-6 * scale
+
+
+def test_real_kernel_refuses_complex_batches():
+    from paper_2202_07017_gb300 import Batch, SvError
+    c, _ = W.hea(5, 2, 1)
+    with pytest.raises(SvError):  # a Y term is imaginary
+        Batch([c], [[(1.0, ((0, "Y"),))]], [0], tune=4)
+    c2, _ = W.random_gates(5, 20, 3, max_tar=1, max_ctrl=1, kinds=("RX", "RY"))
+    with pytest.raises(SvError):  # RX is complex
+        Batch([c2], [W.tfim(5)], [0], tune=4)

@@ -111,7 +111,7 @@ def _run_batch(b5, tune):
         b.close()
 
 
-@pytest.mark.parametrize("tune", [0, 1, 3], ids=["default", "tuned", "smem-states"])
+@pytest.mark.parametrize("tune", [0, 1, 3, 4], ids=["default", "tuned", "smem-states", "real"])
 def test_batch_every_energy(batch5120, tune):
     e, _ = _run_batch(batch5120, tune)
     err = np.abs(e - batch5120["e_ref"]) / batch5120["scale"]
@@ -119,9 +119,16 @@ def test_batch_every_energy(batch5120, tune):
     assert float(err.max()) <= TOL["c64"], int(np.argmax(err))
 
 
-def test_batch_full_gradients_for_every_qubit_count(batch5120):
+_GRAD_REFS = {}
+
+
+@pytest.mark.parametrize("tune", [1, 3], ids=["tuned", "smem-states"])
+def test_batch_full_gradients_for_every_qubit_count(batch5120, tune):
+    """Full gradients of 20 items (2 per qubit count) against the oracle: with
+    the autotuner's kernel (the batch is real: the real-amplitude kernel) and
+    with the complex shared-memory kernel."""
     b5 = batch5120
-    e, g = _run_batch(b5, 1)
+    e, g = _run_batch(b5, tune)
     items, circuits = b5["items"], b5["circuits"]
     offs = np.concatenate([[0], np.cumsum([circuits[ci].n_params for ci in items])])
     pick = [0, 4095]
@@ -130,7 +137,9 @@ def test_batch_full_gradients_for_every_qubit_count(batch5120):
     assert len(pick) == 20
     for i in pick:
         c, H, th = circuits[items[i]], b5["hams"][items[i]], b5["thetas"][i]
-        ref = oracle.grad_param_shift(c, th, H)
+        if i not in _GRAD_REFS:
+            _GRAD_REFS[i] = oracle.grad_param_shift(c, th, H)
+        ref = _GRAD_REFS[i]
         assert _rel(g[offs[i]:offs[i + 1]], ref) <= 1e-5, (i, c.n_qubits)
 
 
