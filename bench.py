@@ -1050,8 +1050,9 @@ def main():
                 "bound": "hbm", "achieved_gbs": rp["achieved_gbs"], "peak_gbs": peak,
                 "frac": rp["achieved_gbs"] / peak}
         if batch is not None:
-            rooflines["kbatch (C3)"] = {"bound": "shared memory (nominal)",
-                                        **batch["state_traffic"]}
+            kname = "kbatch_re" if batch["tile"].get("real_states") else "kbatch"
+            rooflines[f"{kname} (C3)"] = {"bound": "shared memory (nominal)",
+                                          **batch["state_traffic"]}
         for key in ("energy_sum_z", "energy_tfim"):
             r = red[key]
             if r.get("pass_gbs"):
