@@ -764,6 +764,34 @@ __device__ __forceinline__ void issue_load(const FusedParams<R>& P, uint32_t dst
 }
 
 template <typename R>
+__device__ __forceinline__ void issue_prefetch(const FusedParams<R>& P, const CUtensorMap* map,
+                                               const int* c) {
+  switch (P.rank) {
+    case 2: tma_prefetch<2>(map, c); break;
+    case 3: tma_prefetch<3>(map, c); break;
+    case 4: tma_prefetch<4>(map, c); break;
+    default: tma_prefetch<5>(map, c); break;
+  }
+}
+
+// The block's next slice (blk + gridDim.x) into L2 while this one is worked
+// on: its load then waits on L2 rather than HBM.  Warp 0; both views for
+// reverse sweeps.
+template <typename R>
+__device__ __forceinline__ void prefetch_next(const FusedParams<R>& P, uint64_t blk,
+                                              uint64_t n_blocks, int lane, bool two) {
+  const uint64_t nb = blk + gridDim.x;
+  if (nb >= n_blocks) return;
+  const uint64_t nbase = insert_zeros(nb, P.blk);
+  for (int k = lane; k < P.ncopies; k += 32) {
+    int c[5];
+    box_coords(P, nbase, k, c);
+    issue_prefetch(P, &P.tmap, c);
+    if (two) issue_prefetch(P, &P.tmap2, c);
+  }
+}
+
+template <typename R>
 __device__ __forceinline__ void issue_store(const FusedParams<R>& P, uint32_t src, const int* c) {
   switch (P.rank) {
     case 2: tma_store<2>(&P.tmap, c, src); break;
@@ -817,6 +845,7 @@ __global__ void __launch_bounds__(kFThreads, MINB)
         box_coords(P, base, k, c);
         issue_load(P, sbuf + (uint32_t)k * P.box_bytes, c, barp);
       }
+      prefetch_next(P, blk, n_blocks, lane, false);
     }
     const bool ok = mbar_wait_bounded(barp, parity);
     parity ^= 1;
@@ -1177,6 +1206,7 @@ __global__ void __launch_bounds__(kFThreads, MINB)
           default: load_pair<5>(sbuf + off, sbuf2 + off, &P.tmap, &P.tmap2, c, barp); break;
         }
       }
+      prefetch_next(P, blk, n_blocks, lane, true);
     }
     const bool ok = mbar_wait_bounded(barp, parity);
     parity ^= 1;

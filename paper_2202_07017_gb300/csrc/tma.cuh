@@ -99,6 +99,25 @@ __device__ __forceinline__ void tma_load(uint32_t dst, const CUtensorMap* map, c
         : "memory");
 }
 
+// global -> L2 only, rank 2..5: a hint that brings a box into L2 ahead of
+// its load (no completion to wait for)
+template <int RANK>
+__device__ __forceinline__ void tma_prefetch(const CUtensorMap* map, const int* c) {
+  const uint64_t m = reinterpret_cast<uint64_t>(map);
+  if constexpr (RANK == 2)
+    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];"
+                 ::"l"(m), "r"(c[0]), "r"(c[1]) : "memory");
+  else if constexpr (RANK == 3)
+    asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];"
+                 ::"l"(m), "r"(c[0]), "r"(c[1]), "r"(c[2]) : "memory");
+  else if constexpr (RANK == 4)
+    asm volatile("cp.async.bulk.prefetch.tensor.4d.L2.global.tile [%0, {%1, %2, %3, %4}];"
+                 ::"l"(m), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]) : "memory");
+  else
+    asm volatile("cp.async.bulk.prefetch.tensor.5d.L2.global.tile [%0, {%1, %2, %3, %4, %5}];"
+                 ::"l"(m), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4]) : "memory");
+}
+
 // shared -> global, rank 2..5, tracked in the calling thread's bulk group
 template <int RANK>
 __device__ __forceinline__ void tma_store(const CUtensorMap* map, const int* c, uint32_t src) {
