@@ -56,3 +56,16 @@ def test_mixed_batch_recipe():
     # roughly uniform: every qubit count within 40 % of 1024 / 9
     counts = np.bincount(ns, minlength=17)[8:]
     assert counts.min() > 0.6 * 1024 / 9 and counts.max() < 1.4 * 1024 / 9
+
+
+def test_real_amplitude_kernel_needs_real_gates_and_terms():
+    """tune = 4 (the real-amplitude batch kernel) is refused on the host, before
+    any device work, for a Y term (an odd number of Y factors is an imaginary
+    matrix) or a complex gate (RX)."""
+    from paper_2202_07017_gb300 import sv_batch_create
+    hea, _ = W.hea(5, 2, 1)
+    with pytest.raises(SvError, match="real amplitudes"):
+        sv_batch_create([hea], [[(1.0, ((0, "Y"),))]], [0], 4)
+    c, _ = W.random_gates(5, 20, 3, max_tar=1, max_ctrl=1, kinds=("RX", "RY"))
+    with pytest.raises(SvError, match="real amplitudes"):
+        sv_batch_create([c], [W.tfim(5)], [0], 4)
